@@ -1,0 +1,332 @@
+#!/usr/bin/env python3
+"""Benchmark: Clifford & Clifford boson sampling, n = 30 photons in m = 60
+modes (seeded Haar-random interferometer, inputs in modes 0..29), through the
+library's C ABI.
+
+One step = one batch of ``--samples`` (default 200) samples drawn with every
+hot-path stage on the GPU: per-chain planning, Gray decode / re-seed, the
+incremental column-sum walk, the per-addend products, the fused Laplace
+minors, compensated accumulation and the weighted draw.
+
+  value     samples/s with U resident on the device (bs_sample_dev), CUDA
+            events around every step, L2 flushed (256 MiB write) between steps
+  e2e       samples/s through bs_sample with host U / host counts (copies
+            inside the timed region)
+  roofline  the fused-minors walk kernel: algorithmic flops (per-addend count
+            22K - 22, K columns) / summed kernel time (CUDA events on the
+            launching stream) vs 2 x the FP32 FMA rate measured on this GPU
+  cpu_baseline  the oracle (single-threaded double-double C) on a bounded
+            prefix of one chain, scaled to samples/s by its own operation count
+
+``--impl reference`` runs the oracle as the reference arm (CPU only).
+Multi-GPU: samples are independent, so ranks draw disjoint sample sets
+(weak scaling, no collective on the data path).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "Gray-code addends/s vs FP64 peak; C&C samples/s & p99 latency, n=30 m=60"
+UNIT = "samples/s"
+N_PHOTONS, M_MODES, SEED = 30, 60, 3
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="mine", choices=["mine", "reference"])
+    ap.add_argument("--samples", type=int, default=200)
+    ap.add_argument("--mode", default="mixed", choices=["mixed", "fp64"])
+    ap.add_argument("--fp64-samples", type=int, default=20, help="samples of the plain FP64 form (0: skip)")
+    ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    return ap.parse_args()
+
+
+# ---------------------------------------------------------------- clocks
+CLOCK_FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+                "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+                "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+
+def start_clocks(device):
+    path = tempfile.mktemp(prefix="bs_clocks_", suffix=".csv")
+    try:
+        f = open(path, "w")
+        p = subprocess.Popen(["nvidia-smi", "-i", str(device), "--query-gpu=" + CLOCK_FIELDS,
+                              "--format=csv,noheader,nounits", "-lms", "200"], stdout=f, stderr=subprocess.DEVNULL)
+        return p, f, path
+    except (OSError, FileNotFoundError):
+        return None, None, path
+
+
+def stop_clocks(handle):
+    p, f, path = handle
+    if p is None:
+        return None
+    p.terminate()
+    try:
+        p.wait(timeout=5)
+    except subprocess.TimeoutExpired:
+        p.kill()
+    f.close()
+    sm, mx, reasons = [], [], set()
+    names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+    with open(path) as fh:
+        for line in fh:
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx.append(float(parts[2]))
+            except ValueError:
+                continue
+            for name, val in zip(names, parts[5:9]):
+                if val.lower().startswith("active"):
+                    reasons.add(name)
+    os.unlink(path)
+    if not sm:
+        return None
+    return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+            "samples": len(sm)}
+
+
+# ---------------------------------------------------------------- oracle baseline
+def full_sample_ops(n):
+    # operations the oracle's sampler spends on a collision-free sample:
+    # step k computes k minors, each a (k-1)x(k-1) Gray walk of 2^(k-2)
+    # addends over k-1 columns
+    return sum(k * (k - 1) * 2.0 ** (k - 2) for k in range(2, n + 1))
+
+
+def oracle_baseline(budget_s):
+    """Time the oracle on a growing prefix of chain 0 until one run takes
+    ~budget_s / 3; report samples/s = (ops/s) / (ops of a full sample)."""
+    import oracle
+    import synthetic as S
+    u, occ = S.config_cc(N_PHOTONS, M_MODES, SEED)
+    steps, total_t, total_ops, last = 12, 0.0, 0.0, None
+    while steps <= N_PHOTONS:
+        t0 = time.perf_counter()
+        _, _, ops = oracle.cc_sample(u, occ, 1, seed=7, max_steps=steps)
+        dt = time.perf_counter() - t0
+        total_t += dt
+        total_ops += ops
+        last = (steps, dt, ops)
+        if dt > budget_s / 3 or total_t > budget_s:
+            break
+        steps += 1
+    rate = last[2] / last[1]
+    value = rate / full_sample_ops(N_PHOTONS)
+    return {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": (f"steps 1..{last[0]} of one n=30 m=60 chain (double-double C oracle, minors by direct "
+                       f"Gray BB/FG permanents) in {last[1]:.2f} s = {last[2]:.3g} addend-column ops; scaled by "
+                       f"the {full_sample_ops(N_PHOTONS):.3g} ops of a full collision-free sample")}
+
+
+def run_reference(args):
+    """Reference arm: the oracle on the host cores.  Warm-up calibrates a chain
+    prefix that takes about --cpu-seconds / 4; each timed step reruns it."""
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    import oracle
+    import synthetic as S
+    u, occ = S.config_cc(N_PHOTONS, M_MODES, SEED)
+    steps = 12
+    while steps < N_PHOTONS:
+        t0 = time.perf_counter()
+        oracle.cc_sample(u, occ, 1, seed=7, max_steps=steps)
+        if time.perf_counter() - t0 > max(args.cpu_seconds, 2.0) / 4:
+            break
+        steps += 1
+    times, ops = [], 0.0
+    for i in range(max(args.steps, 1)):
+        t0 = time.perf_counter()
+        _, _, ops = oracle.cc_sample(u, occ, 1, seed=7, max_steps=steps)
+        times.append(time.perf_counter() - t0)
+    value = (ops / statistics.mean(times)) / full_sample_ops(N_PHOTONS)
+    cb = {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+          "sample": (f"steps 1..{steps} of one n=30 m=60 chain per step ({ops:.3g} addend-column ops), scaled by "
+                     f"the {full_sample_ops(N_PHOTONS):.3g} ops of a full collision-free sample")}
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000 * statistics.mean(times),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64x2 (double-double)",
+            "data": "synthetic (seeded Haar-random 60-mode unitary)",
+            "config": {"workload": "cc_sampling_n30_m60", "n": N_PHOTONS, "m": M_MODES,
+                       "samples_per_step": "bounded chain prefix on the host (oracle)"},
+            "cpu_baseline": cb,
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ---------------------------------------------------------------- GPU arm
+def run_mine(args):
+    import numpy as np
+    import torch
+
+    import paper_2309_07027_gb300 as bs
+    import synthetic as S
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+
+    mode = bs.BS_MIXED if args.mode == "mixed" else bs.BS_FP64
+    u, occ = S.config_cc(N_PHOTONS, M_MODES, SEED)
+    ctx = bs.Context(local)
+    stream = torch.cuda.current_stream()
+    ctx.set_stream(stream)
+    fp64_rate, fp32_rate = ctx.measure_fma_rates()
+    u_dev = torch.from_numpy(u).to("cuda")
+    S_ = args.samples
+    out_dev = torch.zeros((S_, M_MODES), dtype=torch.int32, device="cuda")
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+    seed_base = 1000003 * (rank + 1)
+
+    for w in range(args.warmup):
+        ctx.sample_dev(u_dev, occ, S_, seed_base + w, out_dev, mode=mode)
+        ctx.sync()
+    ctx.reset_stats()
+    ctx.set_profiling(True)
+    clocks = start_clocks(local)
+    barrier()
+    torch.cuda.synchronize()
+    evs = []
+    wall0 = time.perf_counter()
+    for i in range(args.steps):
+        flush.zero_()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        ctx.sample_dev(u_dev, occ, S_, seed_base + 100 + i, out_dev, mode=mode)
+        e1.record(stream)
+        evs.append((e0, e1))
+    torch.cuda.synchronize()
+    barrier()
+    wall = time.perf_counter() - wall0
+    clk = stop_clocks(clocks)
+    ctx.sync()
+    st = ctx.stats()
+    ctx.set_profiling(False)
+    step_ms = [a.elapsed_time(b) for a, b in evs]
+    counts = out_dev.cpu().numpy()
+    assert np.all(counts.sum(axis=1) == N_PHOTONS), "sampler returned a wrong photon count"
+    t_max = sum(step_ms) / 1000.0
+    if dist is not None:
+        t = torch.tensor([t_max], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        t_max = float(t.item())
+    value = world * S_ * args.steps / t_max
+    launches = int(st["kernel_launches"])
+
+    # roofline of the dominant walk kernel (fused minors in the run's
+    # precision; MIXED sends heavy-collision chains to the FP64 kernel, whose
+    # time and work are reported beside)
+    p = 1 if mode == bs.BS_MIXED else 0
+    walk_s = st["walk_ms"][p] / 1000.0
+    fl = st["addend_flops"][p]
+    peak = 2.0 * (fp32_rate if p == 1 else fp64_rate) / 1e12
+    achieved = fl / walk_s / 1e12 if walk_s > 0 else 0.0
+    roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+            "frac": achieved / peak if peak else None, "traffic": None,
+            "kernel": "walk_fp32_minors_kernel" if p == 1 else "walk_fp64_minors_kernel",
+            "peak_source": "measured on this GPU by bs_measure_fma_rates (2 flops per lane-FMA)",
+            "walk_ms_per_step": st["walk_ms"][p] / args.steps, "walk_launches": int(st["timed_launches"][p]),
+            "addends_per_s": st["addends"][p] / walk_s if walk_s > 0 else 0.0,
+            "other_precision": {"walk_ms_per_step": st["walk_ms"][1 - p] / args.steps,
+                                "addends": st["addends"][1 - p]}}
+
+    # end to end through the host API (U from pinned-able host memory, counts back)
+    e2e = None
+    if not args.no_e2e:
+        ctx.set_stream(None)
+        t0 = time.perf_counter()
+        for i in range(args.steps):
+            ctx.sample(u, occ, S_, seed_base + 200 + i, mode=mode)
+        e2e_t = time.perf_counter() - t0
+        e2e = {"value": world * S_ * args.steps / e2e_t, "unit": UNIT, "h2d_bytes_per_step": int(u.nbytes),
+               "d2h_bytes_per_step": int(S_ * M_MODES * 4)}
+        ctx.set_stream(stream)
+
+    # the plain FP64 form on a smaller sample set, same API
+    fp64_form = None
+    if args.fp64_samples > 0 and mode == bs.BS_MIXED:
+        out64 = torch.zeros((args.fp64_samples, M_MODES), dtype=torch.int32, device="cuda")
+        ctx.sample_dev(u_dev, occ, 2, seed_base + 299, out64, mode=bs.BS_FP64)
+        ctx.sync()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        ctx.sample_dev(u_dev, occ, args.fp64_samples, seed_base + 300, out64, mode=bs.BS_FP64)
+        e1.record(stream)
+        ctx.sync()
+        ms = e0.elapsed_time(e1)
+        fp64_form = {"samples_per_s": args.fp64_samples / (ms / 1000.0), "samples": args.fp64_samples,
+                     "fp64_fma_per_s_measured": fp64_rate}
+
+    if rank != 0:
+        ctx.close()
+        if dist is not None:
+            dist.destroy_process_group()
+        return 0
+    cpu = None
+    if world == 1 and not args.no_cpu_baseline:
+        cpu = oracle_baseline(args.cpu_seconds)
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": statistics.mean(step_ms), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32 products / f64 accumulation" if mode == bs.BS_MIXED else "f64",
+        "data": "synthetic (seeded Haar-random 60-mode unitary)",
+        "config": {"workload": "cc_sampling_n30_m60", "n": N_PHOTONS, "m": M_MODES, "samples_per_step": S_,
+                   "mode": args.mode, "l2": "flushed between steps (256 MiB write)",
+                   "parallelism": f"replicas x{world} (independent samples)"},
+        "latency_ms": {"p50": statistics.median(step_ms), "p99": sorted(step_ms)[max(0, int(0.99 * len(step_ms)) - 1)],
+                       "what": "per batch of samples (all chains of a batch finish together)"},
+        "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
+        "clocks": clk, "fp64_form": fp64_form, "wall_s": wall,
+        "fma_rates_measured": {"fp64_per_s": fp64_rate, "fp32_per_s": fp32_rate},
+    }
+    print(json.dumps(line), flush=True)
+    ctx.close()
+    if dist is not None:
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return run_reference(args)
+    from paper_2309_07027_gb300 import _build
+    _build.build()
+    return run_mine(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

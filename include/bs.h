@@ -1,0 +1,229 @@
+/*
+ * bs.h -- C ABI of the GB300 boson-sampling permanent library (libbs.so).
+ *
+ * Hot path of "High performance Boson Sampling simulation via data-flow
+ * engines" (Morse et al., arXiv 2309.07027): the generalized
+ * Balasubramanian-Bax-Franklin-Glynn permanent with row and column
+ * multiplicities (Sec. 2.2, Eq. bbfgrepeated) walked in n-ary reflected Gray
+ * order, its Laplace minors, and Clifford & Clifford sampling built on them
+ * (Sec. 4).  All arithmetic runs in CUDA kernels for sm_103a; there is no CPU
+ * fallback: without a usable GPU every compute call returns BS_ENODEV.
+ *
+ * Conventions
+ *   - Complex numbers are bs_c128 {re, im} (two IEEE doubles).
+ *   - Matrices are row-major with a leading dimension `ld` counted in complex
+ *     elements (ld >= cols).  Rows are output modes, columns input modes
+ *     (Sec. 2: column sums of the unitary, rows carry the output
+ *     multiplicities).
+ *   - Host-pointer calls are synchronous: inputs are copied in, outputs are
+ *     written to caller memory before the call returns.  The caller owns every
+ *     buffer it passes; the library never keeps a caller pointer.
+ *   - `*_dev` calls take device pointers, enqueue work on the context's stream
+ *     and return without waiting; bs_ctx_sync() waits and reports kernel
+ *     status (for example a deadline that expired).
+ *   - Return value: BS_OK (0) or a negative BS_E* code; bs_last_error() gives a
+ *     message for the calling thread.
+ *   - Limits: n = sum of multiplicities <= BS_MAX_N (48); weights
+ *     prod C(M_k, Delta_k) < 2^48 are exact in FP64.
+ */
+#ifndef BS_H
+#define BS_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define BS_MAX_N 48
+
+enum {
+    BS_OK = 0,
+    BS_EINVAL = -1,    /* bad argument (sizes, multiplicities, sums, limits) */
+    BS_ENOMEM = -2,    /* device memory budget or allocation exhausted */
+    BS_ECUDA = -3,     /* CUDA runtime error (message in bs_last_error) */
+    BS_ETIMEOUT = -4,  /* a kernel deadline expired (status word) */
+    BS_ENODEV = -5     /* no usable CUDA device */
+};
+
+typedef struct {
+    double re, im;
+} bs_c128;
+
+/* Arithmetic of the walk.
+ *   BS_FP64:  column sums, products, weights and sums in double precision;
+ *             partial sums combined in double-double.
+ *   BS_MIXED: column sums and products in single precision (column sums
+ *             re-seeded from the matrix every chunk, columns scaled by powers
+ *             of two), addends summed in float-float runs, partial sums in
+ *             double-double (Sec. 3.2 discusses the accuracy trade-off). */
+typedef enum { BS_FP64 = 0, BS_MIXED = 1 } bs_mode;
+
+typedef struct bs_ctx bs_ctx;
+
+/* Create a context on CUDA device `device`.  mem_budget_bytes caps the
+ * device memory the context may allocate (0 = no cap).  On success *out owns
+ * a stream and grow-only device buffers; release with bs_ctx_destroy.
+ * Errors: BS_EINVAL (out == NULL), BS_ENODEV, BS_ECUDA. */
+int bs_ctx_create(bs_ctx** out, int device, size_t mem_budget_bytes);
+
+/* Free every resource of the context (NULL is accepted). */
+void bs_ctx_destroy(bs_ctx* ctx);
+
+/* Message of the last failed call made by this thread (never NULL). */
+const char* bs_last_error(const bs_ctx* ctx);
+
+/* Use an external cudaStream_t (passed as void*) for all later work; any
+ * handle is taken as is, 0 meaning the legacy default stream.  The caller
+ * keeps the stream alive.  bs_ctx_use_own_stream() returns to the context's
+ * own stream. */
+int bs_ctx_set_stream(bs_ctx* ctx, void* stream);
+int bs_ctx_use_own_stream(bs_ctx* ctx);
+
+/* Wait for all work enqueued on the context's stream and report the kernel
+ * status word: BS_OK or BS_ETIMEOUT (a deadline expired), or BS_ECUDA. */
+int bs_ctx_sync(bs_ctx* ctx);
+
+/* Relative deadline (seconds) for every later walk launch: warps stop taking
+ * work once the device clock passes launch time + seconds, and the call
+ * returns BS_ETIMEOUT.  0 disables the deadline. */
+int bs_ctx_set_deadline(bs_ctx* ctx, double seconds);
+
+/* Chunk-length knob: log2_chunk_max caps the chunk length (= the re-seed
+ * interval of the column sums) of the given mode (default 12); values
+ * outside [4, 20] are rejected with BS_EINVAL. */
+int bs_ctx_set_chunk_log2(bs_ctx* ctx, bs_mode mode, int log2_chunk_max);
+int bs_ctx_get_chunk_log2(const bs_ctx* ctx, bs_mode mode);
+
+/* ------------------------------------------------------------------ */
+/* Permanents                                                          */
+/* ------------------------------------------------------------------ */
+
+/* perm(A, M, N) of Eq. bbfgrepeated (Sec. 2.2): the permanent of the
+ * n x n matrix obtained by repeating row r row_mult[r] times and column c
+ * col_mult[c] times, n = sum(row_mult) = sum(col_mult) (Sec. 4, U_ST).
+ *   A        rows x cols, row-major, leading dimension ld (host memory).
+ *   row_mult rows non-negative ints; col_mult cols non-negative ints.
+ *   out      result rounded to double; out_lo (nullable) receives the low
+ *            part of the double-double sum (out + out_lo ~ 106 bits of the
+ *            computed value).
+ * n = 0 gives 1 (the empty permanent).  The orientation (A or A^T) with
+ * fewer addends is chosen automatically (perm(A) = perm(A^T)).
+ * Errors: BS_EINVAL (negative multiplicity, sums differ, n > BS_MAX_N,
+ * ld < cols, NULL pointers), BS_ENOMEM, BS_ECUDA, BS_ETIMEOUT. */
+int bs_perm(bs_ctx* ctx, const bs_c128* A, int rows, int cols, int ld, const int* row_mult,
+            const int* col_mult, bs_mode mode, bs_c128* out, bs_c128* out_lo);
+
+/* Batch of `count` independent permanents of uneven sizes in one persistent
+ * launch per column bucket (Appendix A.4 batches equal-size matrices; here
+ * sizes may differ).  Item b: matrix rows[b] x cols[b], row-major with
+ * ld = cols[b], at A_packed + a_offset[b]; multiplicities at
+ * mult_packed + row_mult_off[b] (rows[b] ints) and + col_mult_off[b]
+ * (cols[b] ints).  out[b] receives item b (host memory).  An invalid item
+ * fails the whole call with BS_EINVAL before any work is queued. */
+int bs_perm_batch(bs_ctx* ctx, int count, const bs_c128* A_packed, const int64_t* a_offset, const int* rows,
+                  const int* cols, const int* mult_packed, const int64_t* row_mult_off,
+                  const int64_t* col_mult_off, bs_mode mode, bs_c128* out);
+
+/* Device-pointer batch: A_packed_dev and out_dev are device pointers; the
+ * offsets, sizes and multiplicities are host arrays (they drive the host
+ * plan).  Enqueued on the context stream; out_dev is valid after
+ * bs_ctx_sync().  A_packed_dev must stay valid until then. */
+int bs_perm_batch_dev(bs_ctx* ctx, int count, const bs_c128* A_packed_dev, const int64_t* a_offset,
+                      const int* rows, const int* cols, const int* mult_packed, const int64_t* row_mult_off,
+                      const int64_t* col_mult_off, bs_mode mode, bs_c128* out_dev);
+
+/* Laplace minors used by a Clifford & Clifford step (Sec. 4, Clifford &
+ * Clifford's algorithm; the paper batches such permanents "with identical
+ * row selections but different column selections", Appendix A.4).
+ * Requires sum(row_mult) = sum(col_mult) - 1.  minors[c] (cols entries) is
+ * the permanent of the expanded matrix with one copy of column c removed,
+ * 0 when col_mult[c] == 0.  All minors come from one shared Gray walk over
+ * the rows.  For any row vector v,  sum_c col_mult[c] v[c] minors[c] is the
+ * permanent of A with v appended as one more row.
+ * Errors as bs_perm. */
+int bs_laplace_minors(bs_ctx* ctx, const bs_c128* A, int rows, int cols, int ld, const int* row_mult,
+                      const int* col_mult, bs_mode mode, bs_c128* minors);
+
+/* ------------------------------------------------------------------ */
+/* Clifford & Clifford sampling (Sec. 4)                               */
+/* ------------------------------------------------------------------ */
+
+/* Draw n_samples output patterns of ideal boson sampling with interferometer
+ * U (m x m, row-major, host) and input occupation input_occupation[m]
+ * (n = sum <= BS_MAX_N photons), Clifford & Clifford's algorithm: a random
+ * permutation of the input photons, then for k = 1..n the row r_k drawn with
+ * probability proportional to |sum_l U[r, col_l] minor_l|^2 using the minors
+ * of the (k-1) x k matrix of rows drawn so far (Eq. bs_p gives the output
+ * distribution).  Random numbers: Philox4x32-10 (Salmon et al., SC'11) keyed
+ * by (seed low, seed high) with counter (sample low, sample high, purpose,
+ * index): purpose 0 / index j drives the Fisher-Yates swap of position j
+ * (j = n-1..1) with position floor(w0 (j+1) / 2^32); purpose 1 / index k gives
+ * u = ((w0 << 32 | w1) >> 11) 2^-53 for step k, and r_k is the first row whose
+ * running FP64 weight sum (row order) exceeds u times the total.  Sample s of a
+ * seed does not depend on n_samples.
+ * out: n_samples x m occupation counts (host).  All samples advance together,
+ * one batched minors launch per step. */
+int bs_sample(bs_ctx* ctx, const bs_c128* U, int m, const int* input_occupation, int n_samples, uint64_t seed,
+              bs_mode mode, int* out);
+
+/* General form: U is m_rows x m_cols (row-major, leading dimension ld), one
+ * input occupation per column, and only output rows < m_detected are counted
+ * in out (n_samples x m_detected); rows >= m_detected model loss modes (Sec. 4,
+ * lossy simulation by extra modes).  m_detected <= 0 means m_rows. */
+int bs_sample_ex(bs_ctx* ctx, const bs_c128* U, int m_rows, int m_cols, int ld, const int* input_occupation,
+                 int n_samples, uint64_t seed, int m_detected, bs_mode mode, int* out);
+
+/* Device-pointer form of bs_sample_ex: U_dev and out_dev on the device,
+ * input_occupation on the host.  Enqueued; valid after bs_ctx_sync(). */
+int bs_sample_dev(bs_ctx* ctx, const bs_c128* U_dev, int m_rows, int m_cols, int ld, const int* input_occupation,
+                  int n_samples, uint64_t seed, int m_detected, bs_mode mode, int* out_dev);
+
+/* ------------------------------------------------------------------ */
+/* Measurement and diagnostics                                         */
+/* ------------------------------------------------------------------ */
+
+typedef struct {
+    uint64_t walk_launches;     /* walk kernels launched */
+    uint64_t kernel_launches;   /* all kernels this context launched */
+    uint64_t addends[2];        /* Gray-walk addends evaluated: [FP64 kernels, FP32 kernels] */
+    uint64_t addend_flops[2];   /* algorithmic flops of those addends */
+    double walk_ms[2];          /* summed walk-kernel time (profiling on) */
+    uint64_t timed_launches[2]; /* walk launches included in walk_ms */
+} bs_stats;
+
+/* Record CUDA events around every walk launch (on its stream) when on != 0;
+ * bs_ctx_get_stats() then reports their summed durations. */
+int bs_ctx_set_profiling(bs_ctx* ctx, int on);
+
+/* Durations (ms) of the walk launches timed since the last call, oldest
+ * first; at most max_entries are written, the number available is returned
+ * (or a negative error).  Waits for the context's stream. */
+int bs_ctx_get_walk_times(bs_ctx* ctx, double* ms_out, int max_entries);
+int bs_ctx_get_stats(bs_ctx* ctx, bs_stats* out);
+int bs_ctx_reset_stats(bs_ctx* ctx);
+
+/* Measured lane-FMA issue rates of the FP64 and FP32 pipes of this device
+ * (operations per second, 1 FMA = 2 flops), from a timed microbenchmark. */
+int bs_measure_fma_rates(bs_ctx* ctx, double* fp64_fma_per_s, double* fp32_fma_per_s);
+
+/* Host-only check of the n-ary reflected Gray counter the kernels use: walks
+ * `steps` moves from index `start` over digits with the given radices (the
+ * first nbin must be 2) and writes the Delta vector after every move to
+ * deltas (steps x ndigits), the moved digit to moved (steps), and the binomial
+ * weight to weights (steps).  Returns BS_EINVAL on bad radices. */
+int bs_debug_gray_walk(int ndigits, int nbin, const int* radix, uint64_t start, int steps, int* deltas,
+                       int* moved, uint64_t* weights);
+
+/* Host-only planner summary for a permanent (kind 0) or minors (kind 1)
+ * problem: info[0] = addends C, info[1] = digit rows, info[2] = binary digits,
+ * info[3] = product columns, info[4] = 1 if transposed, info[5] = pinned source
+ * row.  Returns BS_EINVAL on invalid multiplicities. */
+int bs_debug_plan(int rows, int cols, const int* row_mult, const int* col_mult, int kind, int64_t* info);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* BS_H */

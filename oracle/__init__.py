@@ -30,7 +30,8 @@ def lib():
             getattr(L, name).argtypes = [C.c_int, dp, C.c_int, dp]
         for name in ("orc_bbfg_gray", "orc_bbfg_direct"):
             getattr(L, name).argtypes = [C.c_int, C.c_int, dp, C.c_int, dp]
-        for name in ("orc_perm_mult", "orc_perm_expanded", "orc_minors", "orc_bbfg_mult_extremes"):
+        for name in ("orc_perm_mult", "orc_perm_expanded", "orc_minors", "orc_bbfg_mult_extremes",
+                     "orc_perm_mult_abs"):
             getattr(L, name).argtypes = [C.c_int, C.c_int, dp, C.c_int, ip, ip, dp]
         L.orc_gray_sequence.argtypes = [C.c_int, C.POINTER(C.c_uint64)]
         L.orc_ryser_exact_gauss.argtypes = [C.c_int, C.POINTER(C.c_int64), C.POINTER(C.c_int64)]
@@ -166,6 +167,11 @@ def minors(a, row_mult, col_mult):
     val = out[:, 0] + 1j * out[:, 2]
     tail = out[:, 1] + 1j * out[:, 3]
     return val, tail
+
+
+def perm_mult_abs(a, row_mult, col_mult):
+    """Modulus-sum S_abs of the addends of Eq. (bbfgrepeated) (with 2^(1-n))."""
+    return float(_mult_call("orc_perm_mult_abs", a, row_mult, col_mult, 1)[0])
 
 
 def mult_extremes(a, row_mult, col_mult):

@@ -33,6 +33,7 @@
  *                         orc_bbfg_gray on the expanded matrix
  *   orc_minors            Laplace minors: per(expanded A with one copy of
  *                         distinct column l removed), each by orc_bbfg_gray
+ *   orc_perm_mult_abs     modulus-sum of the addends of Eq. (bbfgrepeated)
  *   orc_bbfg_mult_extremes  sums of the positive and the negative real
  *                         addends of Eq. (bbfgrepeated) (Appendix A.5)
  *   orc_philox4x32_10     counter-based generator (Salmon et al., SC'11)
@@ -357,6 +358,39 @@ int orc_perm_mult(int R, int K, const double* A, int ld, const int* M, const int
         D[k]++;
     }
     z_store(z_ldexp(acc, 1 - p.n), out);
+    return 0;
+}
+
+/* S_abs = 2^(1-n) sum over Delta of prod_k C(M_k, Delta_k) |prod_j c_j^N_j|,
+ * the modulus-sum of the addends of Eq. (bbfgrepeated): the scale of the
+ * rounding error of any evaluation of the sum (each addend carries a
+ * relative error, so |error| <= rel * S_abs).  out[0] = S_abs. */
+int orc_perm_mult_abs(int R, int K, const double* A, int ld, const int* M, const int* N, double* out) {
+    mult_problem p;
+    int rc = mult_setup(R, K, M, N, &p);
+    if (rc) return rc;
+    if (p.n == 0) { out[0] = 1.0; return 0; }
+    int D[64];
+    memset(D, 0, sizeof(D));
+    dd acc = dd_make(0.0);
+    for (;;) {
+        dd w = dd_make(1.0);
+        for (int k = 1; k < p.R; ++k) w = dd_mul_d(w, binom_exact(p.M[k], D[k]));
+        double mag = 1.0;
+        for (int j = 0; j < p.K; ++j) {
+            zdd s = z_zero();
+            for (int k = 0; k < p.R; ++k)
+                s = z_add(s, z_mul_d(z_elem(A, ld, p.rows[k], p.cols[j]), (double)(p.M[k] - 2 * D[k])));
+            double m = hypot(s.re.hi + s.re.lo, s.im.hi + s.im.lo);
+            for (int e = 0; e < p.N[j]; ++e) mag *= m;
+        }
+        acc = dd_add(acc, dd_mul_d(w, mag));
+        int k = 1;
+        while (k < p.R && D[k] == p.M[k]) { D[k] = 0; ++k; }
+        if (k >= p.R) break;
+        D[k]++;
+    }
+    out[0] = ldexp(acc.hi + acc.lo, 1 - p.n);
     return 0;
 }
 

@@ -1,0 +1,1070 @@
+// Host side of libbs: contexts, device buffers under a memory budget, the
+// integer planner (canonicalisation of a permanent / minors problem), launch
+// sequencing on the context stream, the Clifford & Clifford driver loop, and
+// the C ABI declared in include/bs.h.
+//
+// Canonicalisation (Sec. 2.2, Eq. bbfgrepeated):
+//   * rows / columns with multiplicity 0 are dropped; sum(M) = sum(N) = n is
+//     checked (minors: sum(M) = sum(N) - 1);
+//   * permanents are evaluated in the orientation (A or A^T, perm(A) =
+//     perm(A^T)) whose row multiplicities give fewer addends;
+//   * the pinned row (delta = +1, "always treated with a multiplicity of 1")
+//     is a row of smallest multiplicity; if that multiplicity is M_p > 1 its
+//     other M_p - 1 copies become a digit of radix M_p (the paper suggests
+//     moving a non-repeated row to the top; any choice gives the same sum);
+//   * digits: multiplicity-1 rows first (binary, fastest), then repeated rows
+//     by increasing multiplicity;
+//   * repeated columns are expanded, so every product column has
+//     multiplicity 1 and the product length is n (minors: n + 1).
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include "bs.h"
+#include "bs_job.h"
+#include "gray.h"
+#include "kernels.h"
+#include "sample.h"
+
+namespace {
+
+thread_local std::string g_err = "no error";
+
+int fail(int code, const char* fmt, ...) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof(buf), fmt, ap);
+    va_end(ap);
+    g_err = buf;
+    return code;
+}
+
+#define BS_CUDA(call)                                                                                  \
+    do {                                                                                               \
+        cudaError_t e_ = (call);                                                                       \
+        if (e_ != cudaSuccess) return fail(BS_ECUDA, "%s: %s (%s:%d)", #call, cudaGetErrorString(e_), \
+                                           __FILE__, __LINE__);                                        \
+    } while (0)
+
+struct DevBuf {
+    void* p = nullptr;
+    size_t n = 0;
+};
+
+// control block layout (unsigned long long slots)
+constexpr int kMaxGroups = 64;
+constexpr int kCtlStatus = kMaxGroups;       // int status word (in a 64-bit slot)
+constexpr int kCtlTotal = kMaxGroups + 1;    // sampler task totals [FP64, FP32]
+constexpr int kCtlCounter = kMaxGroups + 3;  // sampler work counters [FP64, FP32]
+constexpr int kCtlStats = kMaxGroups + 5;    // [addends64, flops64, addends32, flops32]
+constexpr int kCtlListLen = kMaxGroups + 9;  // two ints: sampler list lengths
+constexpr int kCtlSlots = kMaxGroups + 16;
+
+struct Timed {
+    cudaEvent_t e0, e1;
+    int fp32;
+};
+
+}  // namespace
+
+struct bs_ctx {
+    int device = 0;
+    cudaStream_t own = nullptr;
+    cudaStream_t stream = nullptr;
+    size_t budget = 0, used = 0;
+    DevBuf src, jobs, meta, data64, data32, partials, out, out_lo, ctl;
+    DevBuf cc_inputs, cc_cols, cc_rows, cc_jobs, cc_meta, cc_data, cc_partials, cc_minors, cc_out, cc_U, cc_lists;
+    void* h_stage = nullptr;
+    size_t h_stage_n = 0;
+    cudaEvent_t stage_ev = nullptr;
+    double deadline_s = 0.0;
+    int log2max[2] = {12, 12};
+    bool profiling = false;
+    std::vector<Timed> timed;
+    std::vector<double> walk_log;  // per-launch walk durations not yet read
+    bs_stats stats{};
+    std::mutex mu;
+};
+
+namespace {
+
+int ensure(bs_ctx* c, DevBuf& b, size_t bytes) {
+    if (bytes == 0) bytes = 16;
+    if (b.n >= bytes) return BS_OK;
+    size_t want = std::max(bytes, b.n + b.n / 4);
+    if (c->budget && c->used - b.n + want > c->budget) {
+        want = bytes;
+        if (c->used - b.n + want > c->budget)
+            return fail(BS_ENOMEM, "device memory budget exceeded: need %zu more bytes (budget %zu, in use %zu)",
+                        want - b.n, c->budget, c->used);
+    }
+    if (b.p) {
+        cudaFree(b.p);
+        c->used -= b.n;
+        b.p = nullptr;
+        b.n = 0;
+    }
+    cudaError_t e = cudaMalloc(&b.p, want);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return fail(BS_ENOMEM, "cudaMalloc(%zu) failed: %s", want, cudaGetErrorString(e));
+    }
+    b.n = want;
+    c->used += want;
+    return BS_OK;
+}
+
+void release(bs_ctx* c, DevBuf& b) {
+    if (b.p) cudaFree(b.p);
+    c->used -= b.n;
+    b.p = nullptr;
+    b.n = 0;
+}
+
+// Pinned staging buffer; waits for the previous upload from it first.
+void* stage(bs_ctx* c, size_t bytes) {
+    if (c->stage_ev) cudaEventSynchronize(c->stage_ev);
+    if (c->h_stage_n < bytes) {
+        if (c->h_stage) cudaFreeHost(c->h_stage);
+        size_t want = std::max(bytes, c->h_stage_n * 2);
+        if (cudaHostAlloc(&c->h_stage, want, cudaHostAllocDefault) != cudaSuccess) {
+            cudaGetLastError();
+            c->h_stage = nullptr;
+            c->h_stage_n = 0;
+            return nullptr;
+        }
+        c->h_stage_n = want;
+    }
+    return c->h_stage;
+}
+
+// ------------------------------------------------------------------ planner
+struct IntPlan {
+    int kind = BS_KIND_PERM;
+    bool trivial = false;  // result known without a walk
+    int n = 0;             // photons of the formula
+    int K = 0, nrows = 0, nbin = 0;
+    uint64_t C = 1;
+    bool trans = false;
+    int pinned_src = 0;
+    int radix[BS_MAX_DIGITS];
+    int digit_src[BS_MAX_DIGITS];
+    int col_src[BS_MAX_COLS];
+};
+
+// Addends of the orientation whose row multiplicities are m[0..cnt): the
+// smallest one is pinned (its other copies form a digit of radix m_p).
+uint64_t pin_cost(const int* m, int cnt) {
+    if (cnt <= 0) return 1;
+    int p = 0;
+    for (int i = 1; i < cnt; ++i)
+        if (m[i] < m[p]) p = i;
+    uint64_t c = (uint64_t)m[p];
+    for (int i = 0; i < cnt; ++i)
+        if (i != p) c *= (uint64_t)(m[i] + 1);
+    return c;
+}
+
+// Canonicalisation without heap allocation (fixed capacities: at most
+// BS_MAX_N photons, so at most BS_MAX_N occupied rows or columns).
+int plan_job(int rows, int cols, const int* M, const int* N, int kind, IntPlan& p) {
+    if (rows < 0 || cols < 0) return fail(BS_EINVAL, "negative matrix size %d x %d", rows, cols);
+    if ((rows > 0 && !M) || (cols > 0 && !N)) return fail(BS_EINVAL, "multiplicity array is NULL");
+    long sm = 0, sn = 0;
+    for (int r = 0; r < rows; ++r) {
+        if (M[r] < 0) return fail(BS_EINVAL, "row multiplicity %d of row %d is negative", M[r], r);
+        sm += M[r];
+    }
+    for (int j = 0; j < cols; ++j) {
+        if (N[j] < 0) return fail(BS_EINVAL, "column multiplicity %d of column %d is negative", N[j], j);
+        sn += N[j];
+    }
+    p = IntPlan();
+    p.kind = kind;
+    if (kind == BS_KIND_PERM) {
+        if (sm != sn) return fail(BS_EINVAL, "sum of row multiplicities %ld != sum of column multiplicities %ld", sm, sn);
+        if (sm > BS_MAX_N) return fail(BS_EINVAL, "n = %ld photons exceeds the limit %d", sm, BS_MAX_N);
+    } else {
+        if (sm != sn - 1)
+            return fail(BS_EINVAL, "minors need sum(row_mult) = sum(col_mult) - 1, got %ld and %ld", sm, sn);
+        if (sn > BS_MAX_N) return fail(BS_EINVAL, "n + 1 = %ld columns exceeds the limit %d", sn, BS_MAX_N);
+    }
+    p.n = (int)sm;
+    if (p.n == 0) {
+        p.trivial = true;  // per(0 x 0) = 1 (minors: the single column with N = 1)
+        return BS_OK;
+    }
+    int rsrc[BS_MAX_N], rmul[BS_MAX_N], csrc[BS_MAX_N + 1], cmul[BS_MAX_N + 1];
+    int nr = 0, nc = 0;
+    for (int r = 0; r < rows; ++r)
+        if (M[r] > 0) {
+            rsrc[nr] = r;
+            rmul[nr++] = M[r];
+        }
+    for (int j = 0; j < cols; ++j)
+        if (N[j] > 0) {
+            csrc[nc] = j;
+            cmul[nc++] = N[j];
+        }
+    const int* Rs = rsrc;
+    const int* Rm = rmul;
+    const int* Cs = csrc;
+    const int* Cm = cmul;
+    int nR = nr, nC = nc;
+    if (kind == BS_KIND_PERM && pin_cost(cmul, nc) < pin_cost(rmul, nr)) {
+        p.trans = true;
+        Rs = csrc;
+        Rm = cmul;
+        nR = nc;
+        Cs = rsrc;
+        Cm = rmul;
+        nC = nr;
+    }
+    int pin = 0;
+    for (int i = 1; i < nR; ++i)
+        if (Rm[i] < Rm[pin]) pin = i;
+    p.pinned_src = Rs[pin];
+    // digits: binary first (order of appearance, then a split pinned row of
+    // multiplicity 2), then repeated rows by increasing multiplicity
+    int dm[BS_MAX_DIGITS], ds[BS_MAX_DIGITS], nd = 0;
+    for (int i = 0; i < nR; ++i)
+        if (i != pin && Rm[i] == 1) {
+            dm[nd] = 1;
+            ds[nd++] = Rs[i];
+        }
+    if (Rm[pin] == 2) {
+        dm[nd] = 1;
+        ds[nd++] = Rs[pin];
+    }
+    p.nbin = nd;
+    for (int i = 0; i <= nR; ++i) {
+        int m, s;
+        if (i < nR) {
+            if (i == pin || Rm[i] == 1) continue;
+            m = Rm[i];
+            s = Rs[i];
+        } else {
+            if (Rm[pin] <= 2) continue;
+            m = Rm[pin] - 1;
+            s = Rs[pin];
+        }
+        int pos = nd;
+        while (pos > p.nbin && dm[pos - 1] > m) {  // stable insertion sort
+            dm[pos] = dm[pos - 1];
+            ds[pos] = ds[pos - 1];
+            --pos;
+        }
+        dm[pos] = m;
+        ds[pos] = s;
+        ++nd;
+    }
+    p.nrows = nd;
+    p.C = 1;
+    for (int d = 0; d < nd; ++d) {
+        p.radix[d] = dm[d] + 1;
+        p.digit_src[d] = ds[d];
+        p.C *= (uint64_t)(dm[d] + 1);
+    }
+    p.K = 0;
+    for (int j = 0; j < nC; ++j)
+        for (int t = 0; t < Cm[j]; ++t) p.col_src[p.K++] = Cs[j];
+    return BS_OK;
+}
+
+// Product column of the first copy of source column c in a minors plan
+// (columns expanded in source order); -1 when col_mult[c] == 0.
+int first_product_col(const int* N, int c) {
+    if (N[c] <= 0) return -1;
+    int at = 0;
+    for (int j = 0; j < c; ++j) at += N[j] > 0 ? N[j] : 0;
+    return at;
+}
+
+// ------------------------------------------------------------------ launcher
+struct JobIn {
+    const IntPlan* p;
+    int64_t src_off;
+    int src_ld;
+    int out_index;
+};
+
+int record_walk_start(bs_ctx* c, cudaEvent_t* e0) {
+    *e0 = nullptr;
+    if (!c->profiling) return BS_OK;
+    BS_CUDA(cudaEventCreate(e0));
+    BS_CUDA(cudaEventRecord(*e0, c->stream));
+    return BS_OK;
+}
+
+int record_walk_end(bs_ctx* c, cudaEvent_t e0, bool fp32) {
+    if (!c->profiling || !e0) return BS_OK;
+    cudaEvent_t e1;
+    BS_CUDA(cudaEventCreate(&e1));
+    BS_CUDA(cudaEventRecord(e1, c->stream));
+    c->timed.push_back({e0, e1, fp32 ? 1 : 0});
+    return BS_OK;
+}
+
+int launch_walk(bs_ctx* c, const bs::WalkArgs& a, bool fp32, int kind) {
+    cudaEvent_t e0;
+    int rc = record_walk_start(c, &e0);
+    if (rc) return rc;
+    cudaError_t e;
+    if (fp32)
+        e = kind == BS_KIND_PERM ? bs::launch_walk_fp32_perm(a, c->stream) : bs::launch_walk_fp32_minors(a, c->stream);
+    else
+        e = kind == BS_KIND_PERM ? bs::launch_walk_fp64_perm(a, c->stream) : bs::launch_walk_fp64_minors(a, c->stream);
+    if (e != cudaSuccess) return fail(BS_ECUDA, "walk launch failed: %s", cudaGetErrorString(e));
+    c->stats.walk_launches++;
+    c->stats.kernel_launches++;
+    return record_walk_end(c, e0, fp32);
+}
+
+int run_jobs(bs_ctx* c, std::vector<JobIn>& ins, const double2* d_src, bs_mode mode, double2* d_out,
+             double2* d_out_lo) {
+    struct Row {
+        JobIn in;
+        int fp32, kind, bucket, log2L, cpt, ncols;
+        uint32_t ntasks;
+    };
+    std::vector<Row> rows;
+    for (auto& in : ins) {
+        if (in.p->trivial) continue;
+        Row r;
+        r.in = in;
+        r.fp32 = (mode == BS_MIXED && bs_mixed_uses_fp32(in.p->radix, in.p->nrows, in.p->K, in.p->n)) ? 1 : 0;
+        r.kind = in.p->kind;
+        r.bucket = (in.p->K + 3) >> 2;
+        r.cpt = (r.fp32 && r.kind == BS_KIND_MINORS) ? 16 : 32;
+        r.log2L = bs_choose_log2L(in.p->C, r.cpt, c->log2max[r.fp32]);
+        uint64_t per = (uint64_t)r.cpt << r.log2L;
+        r.ntasks = (uint32_t)((in.p->C + per - 1) / per);
+        r.ncols = r.kind == BS_KIND_PERM ? 1 : in.p->K;
+        rows.push_back(r);
+    }
+    if (rows.empty()) return BS_OK;
+    // groups of equal (precision, kind, bucket); largest jobs first inside
+    std::stable_sort(rows.begin(), rows.end(), [](const Row& a, const Row& b) {
+        if (a.fp32 != b.fp32) return a.fp32 < b.fp32;
+        if (a.kind != b.kind) return a.kind < b.kind;
+        if (a.bucket != b.bucket) return a.bucket < b.bucket;
+        return a.in.p->C > b.in.p->C;
+    });
+    std::vector<std::pair<size_t, size_t>> groups;
+    for (size_t i = 0; i < rows.size();) {
+        size_t j = i;
+        while (j < rows.size() && rows[j].fp32 == rows[i].fp32 && rows[j].kind == rows[i].kind &&
+               rows[j].bucket == rows[i].bucket)
+            ++j;
+        groups.push_back({i, j});
+        i = j;
+    }
+    if ((int)groups.size() > kMaxGroups) return fail(BS_EINVAL, "too many kernel groups");
+    std::vector<bs_job> jobs(rows.size());
+    std::vector<int> meta;
+    int64_t data_off[2] = {0, 0}, part_off = 0;
+    int max_cols = 1;
+    uint64_t adds[2] = {0, 0}, flops[2] = {0, 0};
+    for (auto& g : groups) {
+        uint64_t tb = 0;
+        for (size_t i = g.first; i < g.second; ++i) {
+            const Row& r = rows[i];
+            const IntPlan& p = *r.in.p;
+            bs_job& jb = jobs[i];
+            std::memset(&jb, 0, sizeof(jb));
+            jb.C = p.C;
+            jb.task_begin = tb;
+            jb.ntasks = r.ntasks;
+            jb.K = p.K;
+            jb.nrows = p.nrows;
+            jb.nbin = p.nbin;
+            jb.kind = r.kind;
+            jb.log2L = r.log2L;
+            jb.out_index = r.in.out_index;
+            jb.n = p.n;
+            jb.normalize = r.fp32;
+            jb.fp32 = r.fp32;
+            jb.data_off = data_off[r.fp32];
+            jb.meta_off = (int64_t)meta.size();
+            jb.partial_off = part_off;
+            jb.src_off = r.in.src_off;
+            jb.src_ld = r.in.src_ld;
+            jb.src_trans = p.trans ? 1 : 0;
+            meta.insert(meta.end(), p.radix, p.radix + p.nrows);
+            meta.insert(meta.end(), p.digit_src, p.digit_src + p.nrows);
+            meta.insert(meta.end(), p.col_src, p.col_src + p.K);
+            meta.insert(meta.end(), (size_t)p.K, 0);
+            meta.push_back(p.pinned_src);
+            data_off[r.fp32] += (int64_t)(1 + p.nrows) * BS_ROW_STRIDE(p.K);
+            part_off += (int64_t)r.ntasks * r.ncols;
+            tb += r.ntasks;
+            max_cols = std::max(max_cols, r.ncols);
+            adds[r.fp32] += p.C;
+            flops[r.fp32] += p.C * (uint64_t)bs_flops_per_addend(p.K, r.kind);
+        }
+    }
+    const size_t jobs_b = jobs.size() * sizeof(bs_job), meta_b = meta.size() * sizeof(int);
+    int rc;
+    if ((rc = ensure(c, c->jobs, jobs_b))) return rc;
+    if ((rc = ensure(c, c->meta, meta_b))) return rc;
+    if ((rc = ensure(c, c->data64, (size_t)data_off[0] * 16))) return rc;
+    if ((rc = ensure(c, c->data32, (size_t)data_off[1] * 8))) return rc;
+    if ((rc = ensure(c, c->partials, (size_t)part_off * sizeof(bs_zdd)))) return rc;
+    if ((rc = ensure(c, c->ctl, kCtlSlots * 8))) return rc;
+    char* h = static_cast<char*>(stage(c, jobs_b + meta_b));
+    if (!h) return fail(BS_ENOMEM, "pinned host staging allocation failed");
+    std::memcpy(h, jobs.data(), jobs_b);
+    std::memcpy(h + jobs_b, meta.data(), meta_b);
+    BS_CUDA(cudaMemcpyAsync(c->jobs.p, h, jobs_b, cudaMemcpyHostToDevice, c->stream));
+    BS_CUDA(cudaMemcpyAsync(c->meta.p, h + jobs_b, meta_b, cudaMemcpyHostToDevice, c->stream));
+    BS_CUDA(cudaEventRecord(c->stage_ev, c->stream));
+    BS_CUDA(cudaMemsetAsync(c->ctl.p, 0, kCtlSlots * 8, c->stream));
+    const bs_job* djobs = static_cast<const bs_job*>(c->jobs.p);
+    // FP64 jobs come first (sorted by precision), then FP32 jobs
+    size_t n64 = 0;
+    while (n64 < rows.size() && !rows[n64].fp32) ++n64;
+    for (int prec = 0; prec < 2; ++prec) {
+        const size_t lo = prec ? n64 : 0, hi = prec ? rows.size() : n64;
+        if (hi == lo) continue;
+        cudaError_t e = bs::launch_pack(djobs + lo, (int)(hi - lo), d_src, static_cast<int*>(c->meta.p),
+                                        prec ? c->data32.p : c->data64.p, prec, c->stream);
+        if (e != cudaSuccess) return fail(BS_ECUDA, "pack launch failed: %s", cudaGetErrorString(e));
+        c->stats.kernel_launches++;
+    }
+    unsigned long long* ctl = static_cast<unsigned long long*>(c->ctl.p);
+    for (size_t gi = 0; gi < groups.size(); ++gi) {
+        auto& g = groups[gi];
+        const int fp32 = rows[g.first].fp32;
+        bs::WalkArgs w;
+        std::memset(&w, 0, sizeof(w));
+        w.jobs = djobs + g.first;
+        w.njobs = (int)(g.second - g.first);
+        w.data = fp32 ? c->data32.p : c->data64.p;
+        w.meta = static_cast<const int*>(c->meta.p);
+        w.partials = static_cast<bs_zdd*>(c->partials.p);
+        unsigned long long tot = 0;
+        int kmax = 0;
+        for (size_t i = g.first; i < g.second; ++i) {
+            tot += rows[i].ntasks;
+            kmax = std::max(kmax, rows[i].in.p->K);
+        }
+        w.total_tasks = tot;
+        w.counter = ctl + gi;
+        w.status = reinterpret_cast<int*>(ctl + kCtlStatus);
+        w.deadline_rel_ns = c->deadline_s > 0 ? (unsigned long long)(c->deadline_s * 1e9) : 0ull;
+        w.max_K = kmax;
+        if ((rc = launch_walk(c, w, fp32 != 0, rows[g.first].kind))) return rc;
+    }
+    {
+        cudaError_t e = bs::launch_reduce(djobs, (int)jobs.size(), static_cast<const bs_zdd*>(c->partials.p),
+                                          static_cast<const int*>(c->meta.p), d_out, d_out_lo, max_cols, c->stream);
+        if (e != cudaSuccess) return fail(BS_ECUDA, "reduce launch failed: %s", cudaGetErrorString(e));
+        c->stats.kernel_launches++;
+    }
+    for (int p = 0; p < 2; ++p) {
+        c->stats.addends[p] += adds[p];
+        c->stats.addend_flops[p] += flops[p];
+    }
+    return BS_OK;
+}
+
+int check_status(bs_ctx* c) {
+    if (!c->ctl.p) return BS_OK;
+    int st = 0;
+    BS_CUDA(cudaMemcpy(&st, static_cast<unsigned long long*>(c->ctl.p) + kCtlStatus, sizeof(int),
+                       cudaMemcpyDeviceToHost));
+    if (st == BS_STATUS_TIMEOUT) return fail(BS_ETIMEOUT, "a walk kernel passed its deadline");
+    if (st == BS_STATUS_BADJOB) return fail(BS_ECUDA, "a walk kernel received a job of the wrong bucket");
+    return BS_OK;
+}
+
+int sync_and_check(bs_ctx* c) {
+    cudaError_t e = cudaStreamSynchronize(c->stream);
+    if (e != cudaSuccess) return fail(BS_ECUDA, "stream synchronize: %s", cudaGetErrorString(e));
+    return check_status(c);
+}
+
+bool ok_ctx(bs_ctx* c) {
+    if (!c) {
+        fail(BS_EINVAL, "context is NULL");
+        return false;
+    }
+    return true;
+}
+
+// Copies rows x cols of A (leading dimension ld) to the staging buffer at
+// offset `at` (in complex elements), contiguous.
+void copy_matrix(bs_c128* dst, const bs_c128* A, int rows, int cols, int ld) {
+    for (int r = 0; r < rows; ++r) std::memcpy(dst + (size_t)r * cols, A + (size_t)r * ld, sizeof(bs_c128) * cols);
+}
+
+int single_job(bs_ctx* c, const bs_c128* A, int rows, int cols, int ld, const int* M, const int* N, int kind,
+               bs_mode mode, IntPlan& p, std::vector<double2>& hi, std::vector<double2>& lo) {
+    if (!ok_ctx(c)) return BS_EINVAL;
+    if (mode != BS_FP64 && mode != BS_MIXED) return fail(BS_EINVAL, "unknown mode %d", (int)mode);
+    int rc = plan_job(rows, cols, M, N, kind, p);
+    if (rc) return rc;
+    const int nout = kind == BS_KIND_PERM ? 1 : std::max(p.K, 1);
+    hi.assign(nout, make_double2(0, 0));
+    lo.assign(nout, make_double2(0, 0));
+    if (p.trivial) {
+        hi[0] = make_double2(1.0, 0.0);
+        return BS_OK;
+    }
+    if (!A) return fail(BS_EINVAL, "matrix pointer is NULL");
+    if (ld < cols) return fail(BS_EINVAL, "leading dimension %d < columns %d", ld, cols);
+    std::lock_guard<std::mutex> lk(c->mu);
+    BS_CUDA(cudaSetDevice(c->device));
+    const size_t mat_b = (size_t)rows * cols * sizeof(bs_c128);
+    if ((rc = ensure(c, c->src, mat_b))) return rc;
+    if ((rc = ensure(c, c->out, nout * sizeof(double2)))) return rc;
+    if ((rc = ensure(c, c->out_lo, nout * sizeof(double2)))) return rc;
+    bs_c128* h = static_cast<bs_c128*>(stage(c, mat_b));
+    if (!h) return fail(BS_ENOMEM, "pinned host staging allocation failed");
+    copy_matrix(h, A, rows, cols, ld);
+    BS_CUDA(cudaMemcpyAsync(c->src.p, h, mat_b, cudaMemcpyHostToDevice, c->stream));
+    BS_CUDA(cudaEventRecord(c->stage_ev, c->stream));
+    std::vector<JobIn> ins = {{&p, 0, cols, 0}};
+    rc = run_jobs(c, ins, static_cast<const double2*>(c->src.p), mode, static_cast<double2*>(c->out.p),
+                  static_cast<double2*>(c->out_lo.p));
+    if (rc) return rc;
+    BS_CUDA(cudaMemcpyAsync(hi.data(), c->out.p, nout * sizeof(double2), cudaMemcpyDeviceToHost, c->stream));
+    BS_CUDA(cudaMemcpyAsync(lo.data(), c->out_lo.p, nout * sizeof(double2), cudaMemcpyDeviceToHost, c->stream));
+    return sync_and_check(c);
+}
+
+// ------------------------------------------------------------------ sampler
+int sample_dev(bs_ctx* c, const double2* dU, int m_rows, int m_cols, int ld, const int* occ, int n_samples,
+               uint64_t seed, int m_det, bs_mode mode, int* dout) {
+    if (m_rows <= 0 || m_cols <= 0) return fail(BS_EINVAL, "bad interferometer size %d x %d", m_rows, m_cols);
+    if (ld < m_cols) return fail(BS_EINVAL, "leading dimension %d < columns %d", ld, m_cols);
+    if (m_rows > 8192) return fail(BS_EINVAL, "at most 8192 output modes are supported");
+    if (!occ) return fail(BS_EINVAL, "input occupation is NULL");
+    if (n_samples < 0) return fail(BS_EINVAL, "negative sample count");
+    if (m_det <= 0 || m_det > m_rows) m_det = m_rows;
+    std::vector<int> inputs;
+    for (int i = 0; i < m_cols; ++i) {
+        if (occ[i] < 0) return fail(BS_EINVAL, "negative occupation in mode %d", i);
+        for (int t = 0; t < occ[i]; ++t) inputs.push_back(i);
+    }
+    const int n = (int)inputs.size();
+    if (n > BS_MAX_N) return fail(BS_EINVAL, "n = %d photons exceeds the limit %d", n, BS_MAX_N);
+    if (n_samples == 0) return BS_OK;
+    if (n == 0) {
+        BS_CUDA(cudaMemsetAsync(dout, 0, (size_t)n_samples * m_det * sizeof(int), c->stream));
+        return BS_OK;
+    }
+    const bool mixed = mode == BS_MIXED;
+    // worst-case tasks of one chain at the last step (C <= 2^(n-2)), over
+    // both kernels a chain may be given
+    uint64_t cmax = n >= 2 ? (1ull << (n - 2)) : 1ull;
+    uint64_t tasks_stride = 8193;
+    tasks_stride = std::max<uint64_t>(tasks_stride, cmax / (32ull << c->log2max[0]) + 2);
+    if (mixed) tasks_stride = std::max<uint64_t>(tasks_stride, cmax / (16ull << c->log2max[1]) + 2);
+    // a step-k job has <= k - 1 digit rows and K = k <= n columns
+    const int64_t meta_stride = 4 * n + 1, data_stride = (int64_t)n * BS_ROW_STRIDE(n);
+    // chains per pass: bounded by the budget (or 2 GiB of partials per pass)
+    const size_t per_chain = (size_t)tasks_stride * n * sizeof(bs_zdd) + (size_t)data_stride * 16 +
+                             meta_stride * 4 + sizeof(bs_job) + (size_t)n * (8 + 16) + 8 + 64;
+    size_t cap_bytes = (size_t)2 << 30;
+    if (c->budget) {
+        size_t free_b = c->budget > c->used ? c->budget - c->used : 0;
+        cap_bytes = std::min(cap_bytes, free_b / 2 + c->cc_partials.n);
+    }
+    int S_max = (int)std::max<size_t>(1, std::min<size_t>((size_t)n_samples, cap_bytes / per_chain));
+    int rc;
+    const int S0 = std::min(S_max, n_samples);
+    if ((rc = ensure(c, c->cc_inputs, n * sizeof(int)))) return rc;
+    if ((rc = ensure(c, c->cc_cols, (size_t)S0 * n * sizeof(int)))) return rc;
+    if ((rc = ensure(c, c->cc_rows, (size_t)S0 * n * sizeof(int)))) return rc;
+    if ((rc = ensure(c, c->cc_jobs, (size_t)S0 * sizeof(bs_job)))) return rc;
+    if ((rc = ensure(c, c->cc_meta, (size_t)S0 * meta_stride * sizeof(int)))) return rc;
+    if ((rc = ensure(c, c->cc_data, (size_t)S0 * data_stride * 16))) return rc;
+    if ((rc = ensure(c, c->cc_lists, (size_t)S0 * 2 * sizeof(int)))) return rc;
+    if ((rc = ensure(c, c->cc_partials, (size_t)S0 * tasks_stride * n * sizeof(bs_zdd)))) return rc;
+    if ((rc = ensure(c, c->cc_minors, (size_t)S0 * n * sizeof(double2)))) return rc;
+    if ((rc = ensure(c, c->ctl, kCtlSlots * 8))) return rc;
+    int* h = static_cast<int*>(stage(c, n * sizeof(int)));
+    if (!h) return fail(BS_ENOMEM, "pinned host staging allocation failed");
+    std::memcpy(h, inputs.data(), n * sizeof(int));
+    BS_CUDA(cudaMemcpyAsync(c->cc_inputs.p, h, n * sizeof(int), cudaMemcpyHostToDevice, c->stream));
+    BS_CUDA(cudaEventRecord(c->stage_ev, c->stream));
+    BS_CUDA(cudaMemsetAsync(c->ctl.p, 0, kCtlSlots * 8, c->stream));
+    unsigned long long* ctl = static_cast<unsigned long long*>(c->ctl.p);
+    for (int base = 0; base < n_samples; base += S_max) {
+        bs::CcArgs a;
+        std::memset(&a, 0, sizeof(a));
+        a.S = std::min(S_max, n_samples - base);
+        a.n = n;
+        a.m_rows = m_rows;
+        a.m_det = m_det;
+        a.ld = ld;
+        a.seed = seed;
+        a.sample_base = (uint64_t)base;
+        a.U = dU;
+        a.inputs = static_cast<const int*>(c->cc_inputs.p);
+        a.cols = static_cast<int*>(c->cc_cols.p);
+        a.rows = static_cast<int*>(c->cc_rows.p);
+        a.jobs = static_cast<bs_job*>(c->cc_jobs.p);
+        a.meta = static_cast<int*>(c->cc_meta.p);
+        a.data = c->cc_data.p;
+        a.partials = static_cast<bs_zdd*>(c->cc_partials.p);
+        a.minors = static_cast<double2*>(c->cc_minors.p);
+        a.total = ctl + kCtlTotal;
+        a.counter = ctl + kCtlCounter;
+        a.stats = ctl + kCtlStats;
+        a.lists = static_cast<int*>(c->cc_lists.p);
+        a.list_len = reinterpret_cast<int*>(ctl + kCtlListLen);
+        a.out = dout + (size_t)base * m_det;
+        a.meta_stride = meta_stride;
+        a.data_stride = data_stride;
+        a.tasks_stride = (int64_t)tasks_stride;
+        a.mixed = mixed ? 1 : 0;
+        a.log2max64 = c->log2max[0];
+        a.log2max32 = c->log2max[1];
+        cudaError_t e = bs::launch_cc_init(a, c->stream);
+        if (e != cudaSuccess) return fail(BS_ECUDA, "sampler init: %s", cudaGetErrorString(e));
+        c->stats.kernel_launches++;
+        for (int k = 1; k <= n; ++k) {
+            if (k >= 2) {
+                if ((e = bs::launch_cc_plan(a, k, c->stream)) != cudaSuccess)
+                    return fail(BS_ECUDA, "sampler plan: %s", cudaGetErrorString(e));
+                if ((e = bs::launch_cc_scan(a, k, c->stream)) != cudaSuccess)
+                    return fail(BS_ECUDA, "sampler scan: %s", cudaGetErrorString(e));
+                for (int prec = mixed ? 1 : 0; prec >= 0; --prec) {
+                    bs::WalkArgs w;
+                    std::memset(&w, 0, sizeof(w));
+                    w.jobs = a.jobs;
+                    w.njobs = a.S;
+                    w.job_list = a.lists + prec * a.S;
+                    w.njobs_dev = a.list_len + prec;
+                    w.data = a.data;
+                    w.meta = a.meta;
+                    w.partials = a.partials;
+                    w.total_tasks = 0;
+                    w.total_dev = a.total + prec;
+                    w.counter = a.counter + prec;
+                    w.status = reinterpret_cast<int*>(ctl + kCtlStatus);
+                    w.deadline_rel_ns = c->deadline_s > 0 ? (unsigned long long)(c->deadline_s * 1e9) : 0ull;
+                    w.max_K = k;
+                    if ((rc = launch_walk(c, w, prec == 1, BS_KIND_MINORS))) return rc;
+                }
+                if ((e = bs::launch_reduce(a.jobs, a.S, a.partials, a.meta, a.minors, nullptr, k, c->stream)) !=
+                    cudaSuccess)
+                    return fail(BS_ECUDA, "sampler reduce: %s", cudaGetErrorString(e));
+                c->stats.kernel_launches += 3;
+            }
+            if ((e = bs::launch_cc_draw(a, k, c->stream)) != cudaSuccess)
+                return fail(BS_ECUDA, "sampler draw: %s", cudaGetErrorString(e));
+            c->stats.kernel_launches++;
+        }
+        if ((e = bs::launch_cc_counts(a, c->stream)) != cudaSuccess)
+            return fail(BS_ECUDA, "sampler counts: %s", cudaGetErrorString(e));
+        c->stats.kernel_launches++;
+    }
+    return BS_OK;
+}
+
+uint64_t read_device_stat(bs_ctx* c, int which) {
+    if (!c->ctl.p) return 0;
+    unsigned long long v = 0;
+    cudaMemcpy(&v, static_cast<unsigned long long*>(c->ctl.p) + kCtlStats + which, 8, cudaMemcpyDeviceToHost);
+    return v;
+}
+
+}  // namespace
+
+// ====================================================================== C ABI
+#pragma GCC visibility push(default)
+extern "C" {
+
+int bs_ctx_create(bs_ctx** out, int device, size_t mem_budget_bytes) {
+    if (!out) return fail(BS_EINVAL, "out is NULL");
+    *out = nullptr;
+    int count = 0;
+    cudaError_t e = cudaGetDeviceCount(&count);
+    if (e != cudaSuccess || count <= 0) {
+        cudaGetLastError();
+        return fail(BS_ENODEV, "no CUDA device available (%s)", cudaGetErrorString(e));
+    }
+    if (device < 0 || device >= count) return fail(BS_EINVAL, "device %d out of range [0, %d)", device, count);
+    bs_ctx* c = new bs_ctx();
+    c->device = device;
+    c->budget = mem_budget_bytes;
+    e = cudaSetDevice(device);
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&c->own, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&c->stage_ev, cudaEventDisableTiming);
+    if (e != cudaSuccess) {
+        delete c;
+        return fail(BS_ECUDA, "context setup: %s", cudaGetErrorString(e));
+    }
+    c->stream = c->own;
+    *out = c;
+    return BS_OK;
+}
+
+void bs_ctx_destroy(bs_ctx* c) {
+    if (!c) return;
+    cudaSetDevice(c->device);
+    cudaStreamSynchronize(c->stream);
+    for (auto& t : c->timed) {
+        cudaEventDestroy(t.e0);
+        cudaEventDestroy(t.e1);
+    }
+    DevBuf* bufs[] = {&c->src,       &c->jobs,     &c->meta,     &c->data64,  &c->data32,      &c->partials,
+                      &c->out,       &c->out_lo,   &c->ctl,      &c->cc_inputs, &c->cc_cols,   &c->cc_rows,
+                      &c->cc_jobs,   &c->cc_meta,  &c->cc_data,  &c->cc_partials, &c->cc_minors, &c->cc_out,
+                      &c->cc_U, &c->cc_lists};
+    for (DevBuf* b : bufs) release(c, *b);
+    if (c->h_stage) cudaFreeHost(c->h_stage);
+    if (c->stage_ev) cudaEventDestroy(c->stage_ev);
+    if (c->own) cudaStreamDestroy(c->own);
+    delete c;
+}
+
+const char* bs_last_error(const bs_ctx*) { return g_err.c_str(); }
+
+int bs_ctx_set_stream(bs_ctx* c, void* stream) {
+    if (!ok_ctx(c)) return BS_EINVAL;
+    std::lock_guard<std::mutex> lk(c->mu);
+    c->stream = static_cast<cudaStream_t>(stream);
+    return BS_OK;
+}
+
+int bs_ctx_use_own_stream(bs_ctx* c) {
+    if (!ok_ctx(c)) return BS_EINVAL;
+    std::lock_guard<std::mutex> lk(c->mu);
+    c->stream = c->own;
+    return BS_OK;
+}
+
+int bs_ctx_sync(bs_ctx* c) {
+    if (!ok_ctx(c)) return BS_EINVAL;
+    std::lock_guard<std::mutex> lk(c->mu);
+    cudaSetDevice(c->device);
+    return sync_and_check(c);
+}
+
+int bs_ctx_set_deadline(bs_ctx* c, double seconds) {
+    if (!ok_ctx(c)) return BS_EINVAL;
+    if (!(seconds >= 0.0)) return fail(BS_EINVAL, "deadline must be >= 0");
+    c->deadline_s = seconds;
+    return BS_OK;
+}
+
+int bs_ctx_set_chunk_log2(bs_ctx* c, bs_mode mode, int log2_chunk_max) {
+    if (!ok_ctx(c)) return BS_EINVAL;
+    if (mode != BS_FP64 && mode != BS_MIXED) return fail(BS_EINVAL, "unknown mode");
+    if (log2_chunk_max < 4 || log2_chunk_max > 20) return fail(BS_EINVAL, "log2 chunk %d outside [4, 20]", log2_chunk_max);
+    c->log2max[mode == BS_MIXED ? 1 : 0] = log2_chunk_max;
+    return BS_OK;
+}
+
+int bs_ctx_get_chunk_log2(const bs_ctx* c, bs_mode mode) {
+    if (!c) return BS_EINVAL;
+    return c->log2max[mode == BS_MIXED ? 1 : 0];
+}
+
+int bs_perm(bs_ctx* c, const bs_c128* A, int rows, int cols, int ld, const int* row_mult, const int* col_mult,
+            bs_mode mode, bs_c128* out, bs_c128* out_lo) {
+    if (!out) return fail(BS_EINVAL, "out is NULL");
+    IntPlan p;
+    std::vector<double2> hi, lo;
+    int rc = single_job(c, A, rows, cols, ld, row_mult, col_mult, BS_KIND_PERM, mode, p, hi, lo);
+    if (rc) return rc;
+    out->re = hi[0].x;
+    out->im = hi[0].y;
+    if (out_lo) {
+        out_lo->re = lo[0].x;
+        out_lo->im = lo[0].y;
+    }
+    return BS_OK;
+}
+
+int bs_laplace_minors(bs_ctx* c, const bs_c128* A, int rows, int cols, int ld, const int* row_mult,
+                      const int* col_mult, bs_mode mode, bs_c128* minors) {
+    if (!minors) return fail(BS_EINVAL, "minors is NULL");
+    IntPlan p;
+    std::vector<double2> hi, lo;
+    int rc = single_job(c, A, rows, cols, ld, row_mult, col_mult, BS_KIND_MINORS, mode, p, hi, lo);
+    if (rc) return rc;
+    for (int j = 0; j < cols; ++j) {
+        const int e = p.trivial ? (col_mult[j] > 0 ? 0 : -1) : first_product_col(col_mult, j);
+        if (e < 0) {
+            minors[j].re = 0.0;
+            minors[j].im = 0.0;
+        } else {
+            minors[j].re = hi[e].x;
+            minors[j].im = hi[e].y;
+        }
+    }
+    return BS_OK;
+}
+
+static int batch_common(bs_ctx* c, int count, const bs_c128* A_packed, const int64_t* a_offset, const int* rows,
+                        const int* cols, const int* mult_packed, const int64_t* row_mult_off,
+                        const int64_t* col_mult_off, bs_mode mode, std::vector<IntPlan>& plans) {
+    if (!ok_ctx(c)) return BS_EINVAL;
+    if (count < 0) return fail(BS_EINVAL, "negative count");
+    if (mode != BS_FP64 && mode != BS_MIXED) return fail(BS_EINVAL, "unknown mode %d", (int)mode);
+    if (count > 0 && (!a_offset || !rows || !cols || !mult_packed || !row_mult_off || !col_mult_off))
+        return fail(BS_EINVAL, "NULL batch array");
+    plans.resize(count);
+    for (int b = 0; b < count; ++b) {
+        int rc = plan_job(rows[b], cols[b], mult_packed + row_mult_off[b], mult_packed + col_mult_off[b],
+                          BS_KIND_PERM, plans[b]);
+        if (rc) return fail(rc, "item %d: %s", b, g_err.c_str());
+        if (!plans[b].trivial && (!A_packed || a_offset[b] < 0))
+            return fail(BS_EINVAL, "item %d: bad matrix pointer or offset", b);
+    }
+    return BS_OK;
+}
+
+int bs_perm_batch(bs_ctx* c, int count, const bs_c128* A_packed, const int64_t* a_offset, const int* rows,
+                  const int* cols, const int* mult_packed, const int64_t* row_mult_off, const int64_t* col_mult_off,
+                  bs_mode mode, bs_c128* out) {
+    std::vector<IntPlan> plans;
+    int rc = batch_common(c, count, A_packed, a_offset, rows, cols, mult_packed, row_mult_off, col_mult_off, mode,
+                          plans);
+    if (rc) return rc;
+    if (count == 0) return BS_OK;
+    if (!out) return fail(BS_EINVAL, "out is NULL");
+    std::lock_guard<std::mutex> lk(c->mu);
+    BS_CUDA(cudaSetDevice(c->device));
+    size_t total = 0;
+    std::vector<int64_t> off(count);
+    for (int b = 0; b < count; ++b) {
+        off[b] = (int64_t)total;
+        if (!plans[b].trivial) total += (size_t)rows[b] * cols[b];
+    }
+    if ((rc = ensure(c, c->src, total * sizeof(bs_c128)))) return rc;
+    if ((rc = ensure(c, c->out, count * sizeof(double2)))) return rc;
+    bs_c128* h = static_cast<bs_c128*>(stage(c, total * sizeof(bs_c128)));
+    if (!h) return fail(BS_ENOMEM, "pinned host staging allocation failed");
+    std::vector<JobIn> ins;
+    for (int b = 0; b < count; ++b) {
+        if (plans[b].trivial) continue;
+        copy_matrix(h + off[b], A_packed + a_offset[b], rows[b], cols[b], cols[b]);
+        ins.push_back({&plans[b], off[b], cols[b], b});
+    }
+    BS_CUDA(cudaMemcpyAsync(c->src.p, h, total * sizeof(bs_c128), cudaMemcpyHostToDevice, c->stream));
+    BS_CUDA(cudaEventRecord(c->stage_ev, c->stream));
+    rc = run_jobs(c, ins, static_cast<const double2*>(c->src.p), mode, static_cast<double2*>(c->out.p), nullptr);
+    if (rc) return rc;
+    std::vector<double2> res(count);
+    BS_CUDA(cudaMemcpyAsync(res.data(), c->out.p, count * sizeof(double2), cudaMemcpyDeviceToHost, c->stream));
+    if ((rc = sync_and_check(c))) return rc;
+    for (int b = 0; b < count; ++b) {
+        if (plans[b].trivial) {
+            out[b].re = 1.0;
+            out[b].im = 0.0;
+        } else {
+            out[b].re = res[b].x;
+            out[b].im = res[b].y;
+        }
+    }
+    return BS_OK;
+}
+
+int bs_perm_batch_dev(bs_ctx* c, int count, const bs_c128* A_packed_dev, const int64_t* a_offset, const int* rows,
+                      const int* cols, const int* mult_packed, const int64_t* row_mult_off,
+                      const int64_t* col_mult_off, bs_mode mode, bs_c128* out_dev) {
+    std::vector<IntPlan> plans;
+    int rc = batch_common(c, count, A_packed_dev, a_offset, rows, cols, mult_packed, row_mult_off, col_mult_off,
+                          mode, plans);
+    if (rc) return rc;
+    if (count == 0) return BS_OK;
+    if (!out_dev) return fail(BS_EINVAL, "out is NULL");
+    std::lock_guard<std::mutex> lk(c->mu);
+    BS_CUDA(cudaSetDevice(c->device));
+    std::vector<JobIn> ins;
+    std::vector<int> trivial;
+    for (int b = 0; b < count; ++b) {
+        if (plans[b].trivial)
+            trivial.push_back(b);
+        else
+            ins.push_back({&plans[b], a_offset[b], cols[b], b});
+    }
+    rc = run_jobs(c, ins, reinterpret_cast<const double2*>(A_packed_dev), mode, reinterpret_cast<double2*>(out_dev),
+                  nullptr);
+    if (rc) return rc;
+    if (!trivial.empty()) {
+        static const double2 one = {1.0, 0.0};
+        for (int b : trivial)
+            BS_CUDA(cudaMemcpyAsync(out_dev + b, &one, sizeof(double2), cudaMemcpyHostToDevice, c->stream));
+    }
+    return BS_OK;
+}
+
+int bs_sample_dev(bs_ctx* c, const bs_c128* U_dev, int m_rows, int m_cols, int ld, const int* input_occupation,
+                  int n_samples, uint64_t seed, int m_detected, bs_mode mode, int* out_dev) {
+    if (!ok_ctx(c)) return BS_EINVAL;
+    if (mode != BS_FP64 && mode != BS_MIXED) return fail(BS_EINVAL, "unknown mode %d", (int)mode);
+    if (!U_dev || (!out_dev && n_samples > 0)) return fail(BS_EINVAL, "NULL device pointer");
+    std::lock_guard<std::mutex> lk(c->mu);
+    BS_CUDA(cudaSetDevice(c->device));
+    return sample_dev(c, reinterpret_cast<const double2*>(U_dev), m_rows, m_cols, ld, input_occupation, n_samples,
+                      seed, m_detected, mode, out_dev);
+}
+
+int bs_sample_ex(bs_ctx* c, const bs_c128* U, int m_rows, int m_cols, int ld, const int* input_occupation,
+                 int n_samples, uint64_t seed, int m_detected, bs_mode mode, int* out) {
+    if (!ok_ctx(c)) return BS_EINVAL;
+    if (mode != BS_FP64 && mode != BS_MIXED) return fail(BS_EINVAL, "unknown mode %d", (int)mode);
+    if (!U || (!out && n_samples > 0)) return fail(BS_EINVAL, "NULL pointer");
+    if (m_rows <= 0 || m_cols <= 0 || ld < m_cols) return fail(BS_EINVAL, "bad interferometer size");
+    if (n_samples <= 0) return n_samples < 0 ? fail(BS_EINVAL, "negative sample count") : BS_OK;
+    const int mdet = (m_detected <= 0 || m_detected > m_rows) ? m_rows : m_detected;
+    std::lock_guard<std::mutex> lk(c->mu);
+    BS_CUDA(cudaSetDevice(c->device));
+    const size_t ub = (size_t)m_rows * m_cols * sizeof(bs_c128);
+    const size_t ob = (size_t)n_samples * mdet * sizeof(int);
+    int rc;
+    if ((rc = ensure(c, c->cc_U, ub))) return rc;
+    if ((rc = ensure(c, c->cc_out, ob))) return rc;
+    bs_c128* h = static_cast<bs_c128*>(stage(c, std::max(ub, ob)));
+    if (!h) return fail(BS_ENOMEM, "pinned host staging allocation failed");
+    copy_matrix(h, U, m_rows, m_cols, ld);
+    BS_CUDA(cudaMemcpyAsync(c->cc_U.p, h, ub, cudaMemcpyHostToDevice, c->stream));
+    BS_CUDA(cudaEventRecord(c->stage_ev, c->stream));
+    rc = sample_dev(c, static_cast<const double2*>(c->cc_U.p), m_rows, m_cols, m_cols, input_occupation, n_samples,
+                    seed, mdet, mode, static_cast<int*>(c->cc_out.p));
+    if (rc) return rc;
+    BS_CUDA(cudaEventSynchronize(c->stage_ev));
+    BS_CUDA(cudaMemcpyAsync(c->h_stage, c->cc_out.p, ob, cudaMemcpyDeviceToHost, c->stream));
+    if ((rc = sync_and_check(c))) return rc;
+    std::memcpy(out, c->h_stage, ob);
+    return BS_OK;
+}
+
+int bs_sample(bs_ctx* c, const bs_c128* U, int m, const int* input_occupation, int n_samples, uint64_t seed,
+              bs_mode mode, int* out) {
+    return bs_sample_ex(c, U, m, m, m, input_occupation, n_samples, seed, m, mode, out);
+}
+
+int bs_ctx_set_profiling(bs_ctx* c, int on) {
+    if (!ok_ctx(c)) return BS_EINVAL;
+    c->profiling = on != 0;
+    return BS_OK;
+}
+
+// Converts recorded walk event pairs into durations (stream must be idle).
+static void collect_timed(bs_ctx* c) {
+    for (auto& t : c->timed) {
+        float ms = 0.f;
+        if (cudaEventElapsedTime(&ms, t.e0, t.e1) == cudaSuccess) {
+            c->stats.walk_ms[t.fp32] += ms;
+            c->stats.timed_launches[t.fp32]++;
+            c->walk_log.push_back(ms);
+        }
+        cudaEventDestroy(t.e0);
+        cudaEventDestroy(t.e1);
+    }
+    c->timed.clear();
+}
+
+int bs_ctx_get_walk_times(bs_ctx* c, double* ms_out, int max_entries) {
+    if (!ok_ctx(c) || (max_entries > 0 && !ms_out)) return fail(BS_EINVAL, "NULL argument");
+    std::lock_guard<std::mutex> lk(c->mu);
+    cudaSetDevice(c->device);
+    cudaError_t e = cudaStreamSynchronize(c->stream);
+    if (e != cudaSuccess) return fail(BS_ECUDA, "stream synchronize: %s", cudaGetErrorString(e));
+    collect_timed(c);
+    int n = (int)c->walk_log.size();
+    for (int i = 0; i < n && i < max_entries; ++i) ms_out[i] = c->walk_log[i];
+    c->walk_log.clear();
+    return n;
+}
+
+int bs_ctx_get_stats(bs_ctx* c, bs_stats* out) {
+    if (!ok_ctx(c) || !out) return fail(BS_EINVAL, "NULL argument");
+    std::lock_guard<std::mutex> lk(c->mu);
+    cudaSetDevice(c->device);
+    cudaError_t e = cudaStreamSynchronize(c->stream);
+    if (e != cudaSuccess) return fail(BS_ECUDA, "stream synchronize: %s", cudaGetErrorString(e));
+    collect_timed(c);
+    *out = c->stats;
+    for (int p = 0; p < 2; ++p) {
+        out->addends[p] += read_device_stat(c, 2 * p);
+        out->addend_flops[p] += read_device_stat(c, 2 * p + 1);
+    }
+    return BS_OK;
+}
+
+int bs_ctx_reset_stats(bs_ctx* c) {
+    if (!ok_ctx(c)) return BS_EINVAL;
+    std::lock_guard<std::mutex> lk(c->mu);
+    cudaSetDevice(c->device);
+    cudaStreamSynchronize(c->stream);
+    for (auto& t : c->timed) {
+        cudaEventDestroy(t.e0);
+        cudaEventDestroy(t.e1);
+    }
+    c->timed.clear();
+    c->walk_log.clear();
+    c->stats = bs_stats();
+    if (c->ctl.p) cudaMemset(static_cast<unsigned long long*>(c->ctl.p) + kCtlStats, 0, 32);
+    return BS_OK;
+}
+
+int bs_measure_fma_rates(bs_ctx* c, double* fp64, double* fp32) {
+    if (!ok_ctx(c) || !fp64 || !fp32) return fail(BS_EINVAL, "NULL argument");
+    std::lock_guard<std::mutex> lk(c->mu);
+    cudaError_t e = bs::measure_fma_rates(c->device, fp64, fp32);
+    if (e != cudaSuccess) return fail(BS_ECUDA, "microbenchmark: %s", cudaGetErrorString(e));
+    return BS_OK;
+}
+
+int bs_debug_gray_walk(int ndigits, int nbin, const int* radix, uint64_t start, int steps, int* deltas, int* moved,
+                       uint64_t* weights) {
+    if (ndigits < 0 || ndigits > BS_MAX_DIGITS || nbin < 0 || nbin > ndigits || !radix || steps < 0)
+        return fail(BS_EINVAL, "bad digit description");
+    uint64_t C = 1;
+    for (int j = 0; j < ndigits; ++j) {
+        if (radix[j] < 2 || radix[j] > 61 || (j < nbin && radix[j] != 2))
+            return fail(BS_EINVAL, "bad radix %d at digit %d", radix[j], j);
+        C *= (uint64_t)radix[j];
+        if (C > (1ull << 50)) return fail(BS_EINVAL, "too many addends");
+    }
+    if (start >= C || start + (uint64_t)steps > C) return fail(BS_EINVAL, "walk leaves [0, C)");
+    bs_gray g;
+    bs_gray_decode(g, start, nbin, ndigits, radix);
+    for (int s = 0; s < steps; ++s) {
+        if (s > 0) {
+            int coef, wch;
+            int row = bs_gray_step(g, radix, &coef, &wch);
+            if (moved) moved[s] = row;
+        } else if (moved) {
+            moved[0] = -1;
+        }
+        if (deltas)
+            for (int j = 0; j < ndigits; ++j) deltas[(size_t)s * ndigits + j] = bs_gray_delta(g, j);
+        if (weights) weights[s] = g.w;
+    }
+    return BS_OK;
+}
+
+int bs_debug_plan(int rows, int cols, const int* row_mult, const int* col_mult, int kind, int64_t* info) {
+    if (!info) return fail(BS_EINVAL, "info is NULL");
+    IntPlan p;
+    int rc = plan_job(rows, cols, row_mult, col_mult, kind == 1 ? BS_KIND_MINORS : BS_KIND_PERM, p);
+    if (rc) return rc;
+    info[0] = p.trivial ? 0 : (int64_t)p.C;
+    info[1] = p.nrows;
+    info[2] = p.nbin;
+    info[3] = p.K;
+    info[4] = p.trans ? 1 : 0;
+    info[5] = p.pinned_src;
+    return BS_OK;
+}
+
+}  // extern "C"
+#pragma GCC visibility pop

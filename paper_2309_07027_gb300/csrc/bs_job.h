@@ -1,0 +1,77 @@
+// Job descriptor shared by the host planner and the walk kernels.
+//
+// A job is one generalized BB/FG sum (Eq. bbfgrepeated) in canonical form:
+//   * K product columns, each with multiplicity 1 (repeated columns are
+//     expanded by the planner, so the product length equals K);
+//   * one pinned row (delta = +1, Sec. 2.2) folded into the base column sums;
+//   * nrows digit rows; digit j has radix R_j = M_j + 1 and counts the -1
+//     entries Delta_j among the M_j copies of that row (Eq. Deltak).  The
+//     first nbin digits are binary (M_j = 1) and vary fastest.
+// The addend index i in [0, C), C = prod_j R_j, is read as a mixed-radix
+// number (digit 0 least significant) and mapped to the reflected n-ary Gray
+// code of Sec. 2.2; each addend is
+//     (-1)^{sum Delta} prod_j C(M_j, Delta_j) * prod_col c_col
+// with c_col = c0_col - sum_j Delta_j * (2 a_j,col).
+//
+// kind == BS_KIND_PERM   : one output, sum * 2^{scale_exp}
+// kind == BS_KIND_MINORS : K outputs, output l = sum over addends of
+//                          (-1)^.. C(..) prod_{col != l} c_col, scaled by
+//                          2^{colexp[l]} (Laplace minors, one column removed).
+#pragma once
+#include <stdint.h>
+
+#define BS_KIND_PERM 0
+#define BS_KIND_MINORS 1
+
+#define BS_MAX_COLS 48     // product columns per job
+#define BS_MAX_DIGITS 48   // digit rows per job
+#define BS_MAX_PHOTONS 48  // n = sum of multiplicities
+
+struct bs_job {
+    uint64_t C;            // number of addends = prod of radices
+    uint64_t task_begin;   // first global warp-task index of this job
+    uint32_t ntasks;       // warp tasks: each covers 32 chunks of 2^log2L addends
+    int32_t K;             // product columns
+    int32_t nrows;         // digit rows
+    int32_t nbin;          // leading binary digits
+    int32_t kind;          // BS_KIND_PERM or BS_KIND_MINORS
+    int32_t log2L;         // chunk length exponent (one chunk per lane per task)
+    int32_t out_index;     // perm: output slot; minors: first of K output slots
+    int32_t n;             // photons of the formula (prefactor 2^(1-n))
+    int32_t normalize;     // 1: scale each column by a power of two (FP32 range)
+    int32_t fp32;          // 1: walked by the FP32 kernels, 0: by the FP64 kernels
+    int64_t data_off;      // complex elements: c0[KP] then 2a[nrows][KP], KP = BS_ROW_STRIDE(K)
+    int64_t meta_off;      // ints, see BS_META_* below
+    int64_t partial_off;   // double-double complex slots: ntasks * (perm ? 1 : K)
+    int64_t src_off;       // source matrix: element offset of entry (0, 0)
+    int32_t src_ld;        // source leading dimension (complex elements)
+    int32_t src_trans;     // 1: formula row r / column c read source (c, r)
+};
+
+// Integer metadata of a job, at meta_off (all int32):
+//   radix[nrows]        digit radices R_j = M_j + 1 (binary digits first)
+//   digit_src[nrows]    source row of each digit
+//   col_src[K]          source column of each product column
+//   colexp[K]           power-of-two column scale chosen by the pack kernel
+//   pinned_src          source row of the pinned (delta = +1) row
+#define BS_META_RADIX(jb) ((jb).meta_off)
+#define BS_META_DIGIT_SRC(jb) ((jb).meta_off + (jb).nrows)
+#define BS_META_COL_SRC(jb) ((jb).meta_off + 2 * (jb).nrows)
+#define BS_META_COLEXP(jb) ((jb).meta_off + 2 * (jb).nrows + (jb).K)
+#define BS_META_PINNED(jb) ((jb).meta_off + 2 * (jb).nrows + 2 * (jb).K)
+#define BS_META_SIZE(nrows, K) (2 * (nrows) + 2 * (K) + 1)
+
+// Row stride of the packed matrix c0 / 2a: K rounded up to even, so FP32
+// rows start on 16-byte boundaries (column pairs load as one float4); the
+// pad column holds zeros.
+#define BS_ROW_STRIDE(K) ((((K) + 1) / 2) * 2)
+
+// Double-double complex partial: re = (re_hi, re_lo), im = (im_hi, im_lo).
+struct bs_zdd {
+    double re_hi, re_lo, im_hi, im_lo;
+};
+
+// Device status word values (written by kernels, read by the host).
+#define BS_STATUS_OK 0
+#define BS_STATUS_TIMEOUT 1
+#define BS_STATUS_BADJOB 2

@@ -1,0 +1,82 @@
+// Pack and reduce kernels.
+//
+// pack:   for every job, reads its source matrix (device) and writes
+//           c0[col]   = sum over all rows of M_row * a_row,col  (all delta = +1)
+//           2a[j][col] = 2 * a_digit_j,col
+//         in the job's working precision.  With normalize set, column col is
+//         first scaled by 2^-e, e the smallest integer with
+//         sum_rows M_row (|Re a| + |Im a|) <= 2^e, so every column sum of the
+//         walk has modulus <= sqrt(2) and FP32 products cannot overflow; the
+//         exponents go to colexp[] and are undone exactly by the reduce
+//         kernel (Appendix A.5 normalises columns for the same reason; here the
+//         factors are powers of two, so the rescaling is exact).
+// reduce: sums each job's task partials in double-double in a fixed order and
+//         applies 2^(1-n) (Eq. bbfgrepeated prefactor) and the column scales.
+#include <cuda_runtime.h>
+#include "kernels.h"
+#include "pack.cuh"
+#include "walk.cuh"
+
+namespace bs {
+
+__global__ void pack_kernel(const bs_job* __restrict__ jobs, const double2* __restrict__ src, int* __restrict__ meta,
+                            void* __restrict__ data, int fp32) {
+    const bs_job jb = jobs[blockIdx.x];
+    pack_job(jb, src, meta, data, fp32, threadIdx.x, blockDim.x);
+}
+
+cudaError_t launch_pack(const bs_job* jobs, int njobs, const double2* src, int* meta, void* data, int fp32,
+                        cudaStream_t s) {
+    if (njobs <= 0) return cudaSuccess;
+    pack_kernel<<<njobs, 64, 0, s>>>(jobs, src, meta, data, fp32);
+    return cudaGetLastError();
+}
+
+constexpr int kReduceBlock = 256;
+
+__global__ void __launch_bounds__(kReduceBlock) reduce_kernel(const bs_job* __restrict__ jobs,
+                                                              const bs_zdd* __restrict__ partials,
+                                                              const int* __restrict__ meta, double2* __restrict__ out,
+                                                              double2* __restrict__ out_lo) {
+    __shared__ ddv sre[kReduceBlock];
+    __shared__ ddv sim[kReduceBlock];
+    const bs_job jb = jobs[blockIdx.x];
+    const int ncols = jb.kind == BS_KIND_PERM ? 1 : jb.K;
+    const int col = blockIdx.y;
+    if (col >= ncols) return;
+    ddv re = {0.0, 0.0}, im = {0.0, 0.0};
+    for (uint32_t t = threadIdx.x; t < jb.ntasks; t += kReduceBlock) {
+        bs_zdd p = partials[jb.partial_off + (int64_t)t * ncols + col];
+        re = dd_add(re, ddv{p.re_hi, p.re_lo});
+        im = dd_add(im, ddv{p.im_hi, p.im_lo});
+    }
+    sre[threadIdx.x] = re;
+    sim[threadIdx.x] = im;
+    __syncthreads();
+    for (int w = kReduceBlock / 2; w > 0; w >>= 1) {
+        if ((int)threadIdx.x < w) {
+            sre[threadIdx.x] = dd_add(sre[threadIdx.x], sre[threadIdx.x + w]);
+            sim[threadIdx.x] = dd_add(sim[threadIdx.x], sim[threadIdx.x + w]);
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        const int* colexp = meta + BS_META_COLEXP(jb);
+        int e = 1 - jb.n;
+        for (int c = 0; c < jb.K; ++c) e += colexp[c];
+        if (jb.kind == BS_KIND_MINORS) e -= colexp[col];
+        ddv r = sre[0], i = sim[0];
+        out[jb.out_index + col] = make_double2(ldexp(r.hi, e), ldexp(i.hi, e));
+        if (out_lo) out_lo[jb.out_index + col] = make_double2(ldexp(r.lo, e), ldexp(i.lo, e));
+    }
+}
+
+cudaError_t launch_reduce(const bs_job* jobs, int njobs, const bs_zdd* partials, const int* meta, double2* out,
+                          double2* out_lo, int max_cols, cudaStream_t s) {
+    if (njobs <= 0) return cudaSuccess;
+    dim3 grid(njobs, max_cols < 1 ? 1 : max_cols);
+    reduce_kernel<<<grid, kReduceBlock, 0, s>>>(jobs, partials, meta, out, out_lo);
+    return cudaGetLastError();
+}
+
+}  // namespace bs

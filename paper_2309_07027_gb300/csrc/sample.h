@@ -1,0 +1,93 @@
+// Shared rules of the host planner, the device planner and the sampler.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+#include "bs_job.h"
+#include "gray.h"
+#include <math.h>
+
+// Chunk length exponent of a job with C addends whose warp tasks cover `cpt`
+// chunks: aim at about 4096 tasks per job (enough to fill the GPU with one
+// job), never below 2^6 addends per chunk (decode cost) nor above 2^log2max
+// (the re-seed interval).  Depends only on (C, cpt, log2max), so a job is cut
+// the same way alone or inside any batch.
+BS_HD int bs_choose_log2L(uint64_t C, int cpt, int log2max) {
+    uint64_t per = C / ((uint64_t)cpt * 4096ull);
+    int l = 0;
+    while ((2ull << l) <= per) ++l;  // floor(log2(per)) for per >= 1
+    if (per == 0) l = 0;
+    if (l < 6) l = 6;
+    if (l > log2max) l = log2max;
+    return l;
+}
+
+// Algorithmic flops of one addend (the roofline numerator):
+//   permanent: column update 2K + product 6(K-1) + weighted accumulate 4
+//   minors:    column update 2K + suffix and prefix products 12(K-2) + 2
+//              + per-column product-accumulate 8K
+BS_HD int64_t bs_flops_per_addend(int K, int kind) {
+    if (kind == BS_KIND_PERM) return 8 * (int64_t)K - 2;
+    int64_t kk = K < 2 ? 2 : K;
+    return 2 * (int64_t)K + 12 * (kk - 2) + 2 + 8 * (int64_t)K;
+}
+
+// MIXED-mode precision rule.  FP32 rounding gives each addend a relative
+// error of about K 2^-24, amplified by up to sqrt(M) where a column sum of a
+// repeated row cancels; the addends' root-sum-square is about
+// 2^(1-n) sqrt(prod_j C(2 M_j, M_j)) times prod_col ||a_col|| (Vandermonde:
+// sum_D C(M, D)^2 = C(2M, M)), so the predicted error relative to the MIXED
+// tolerance scale prod_col ||a_col|| is
+//   log2 K + log2(2n)/2 + log2(max M)/2 - 24 + (1 - n)
+//     + sum_j log2 C(2 M_j, M_j) / 2 + 2        (safety factor 4).
+// The job runs in FP32 when that is <= log2(1e-6), else in FP64 ("FP64 ...
+// at large k, where cancellation demands it").  Depends only on the
+// multiplicities, K and n, so every planner decides alike.
+BS_HD int bs_mixed_uses_fp32(const int* radix, int nrows, int K, int n) {
+    float lg = log2f((float)(K > 1 ? K : 1)) + 0.5f * log2f(2.0f * (float)(n > 1 ? n : 1)) - 24.0f +
+               (1.0f - (float)n) + 2.0f;
+    int mmax = 1;
+    for (int j = 0; j < nrows; ++j) {
+        const int M = radix[j] - 1;
+        if (M > mmax) mmax = M;
+        for (int t = 1; t <= M; ++t) lg += 0.5f * log2f((float)(M + t) / (float)t);
+    }
+    lg += 0.5f * log2f((float)mmax);
+    return lg <= -19.93f;
+}
+
+namespace bs {
+
+struct CcArgs {
+    int S;                        // chains (samples) in this batch
+    int n;                        // photons
+    int m_rows, m_det, ld;        // U rows, counted rows, leading dimension
+    uint64_t seed;
+    uint64_t sample_base;         // index of the first sample (RNG counter)
+    const double2* U;             // device, m_rows x ld
+    const int* inputs;            // device, n expanded input columns
+    int* cols;                    // device, S x n permuted columns
+    int* rows;                    // device, S x n drawn rows
+    bs_job* jobs;                 // device, S
+    int* meta;                    // device, S x meta_stride
+    void* data;                   // device arena (double or float complex)
+    bs_zdd* partials;             // device, S x tasks_stride x n
+    double2* minors;              // device, S x n
+    unsigned long long* total;    // device task totals [FP64, FP32]
+    unsigned long long* counter;  // device work counters [FP64, FP32]
+    unsigned long long* stats;    // device [addends64, flops64, addends32, flops32]
+    int* lists;                   // device job lists: [FP64: S][FP32: S]
+    int* list_len;                // device list lengths [FP64, FP32]
+    int* out;                     // device, S x m_det
+    int64_t meta_stride, data_stride, tasks_stride;
+    int mixed;                    // 1: MIXED mode (per-chain FP32 / FP64 rule)
+    int log2max64, log2max32;
+};
+
+cudaError_t launch_cc_init(const CcArgs& a, cudaStream_t st);
+cudaError_t launch_cc_plan(const CcArgs& a, int k, cudaStream_t st);
+cudaError_t launch_cc_scan(const CcArgs& a, int k, cudaStream_t st);
+cudaError_t launch_cc_draw(const CcArgs& a, int k, cudaStream_t st);
+cudaError_t launch_cc_counts(const CcArgs& a, cudaStream_t st);
+cudaError_t launch_philox(const uint32_t* in, uint32_t* out, int count, cudaStream_t s);
+
+}  // namespace bs

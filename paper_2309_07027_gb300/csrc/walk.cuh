@@ -1,0 +1,699 @@
+// Gray-walk kernels for the generalized BB/FG sum (Eq. bbfgrepeated) and its
+// fused Laplace-minor variant.
+//
+// Work decomposition (Sec. 2.1: contiguous index ranges walked
+// independently, each seeded by decoding its first index):
+//   * a job's index range [0, C) is cut into chunks of L = 2^log2L addends;
+//   * a warp task is 32 consecutive chunks, one per lane;
+//   * persistent warps pull tasks from a global counter (largest jobs are
+//     planned first), so uneven jobs share one launch;
+//   * every lane decodes its chunk start (re-seeding its column sums from the
+//     matrix, which bounds the drift of the incremental updates, Sec. 3.2)
+//     and then steps through the chunk one digit move at a time.
+// Because chunk starts are multiples of L, all lanes of a warp flip the same
+// binary digit at each step except at the rare carries past bit log2L, so the
+// row they read is a broadcast load.
+//
+// Per addend (thread-owns-chunk; all column sums in registers):
+//   update   c_col += coef * (2 a_row,col)       K complex FMAs
+//   product  P = prod_col c_col                   K-1 complex multiplies, two
+//                                                 independent chains
+//   weight   acc += (+-W) * P                      (Eq. bbfgrepeated weight)
+// Minors additionally form, for every column l, prod_{col != l} c_col from a
+// suffix pass and a running prefix (about 2.3x the FP64 work of one
+// permanent instead of K x).
+//
+// Accumulation: each lane sums its addends in plain precision for a short
+// run, folds the run into a compensated accumulator (double-double in FP64
+// mode, float-float in FP32 mode), and the 32 lanes of a task are combined in
+// double-double in a fixed shuffle order.  Tasks write one partial each; the
+// reduce kernel sums them in a fixed order, so results do not depend on which
+// warp ran which task or on what else was in the launch.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+#include "bs_job.h"
+#include "gray.h"
+#include "kernels.h"
+
+namespace bs {
+
+template <typename T>
+struct cx {
+    T re, im;
+};
+
+__device__ __forceinline__ float bfma(float a, float b, float c) { return __fmaf_rn(a, b, c); }
+__device__ __forceinline__ double bfma(double a, double b, double c) { return __fma_rn(a, b, c); }
+
+template <typename T>
+__device__ __forceinline__ cx<T> cmul(cx<T> a, cx<T> b) {
+    cx<T> r;
+    r.re = bfma(a.re, b.re, -(a.im * b.im));
+    r.im = bfma(a.re, b.im, a.im * b.re);
+    return r;
+}
+
+// ---------------------------------------------------------------- compensated sums
+struct ddv {
+    double hi, lo;
+};
+
+// TwoSum (Knuth) then renormalisation; adds a double into a double-double.
+__device__ __forceinline__ ddv dd_add_d(ddv a, double b) {
+    double s = __dadd_rn(a.hi, b);
+    double bb = __dsub_rn(s, a.hi);
+    double e = __dadd_rn(__dsub_rn(a.hi, __dsub_rn(s, bb)), __dsub_rn(b, bb));
+    e = __dadd_rn(e, a.lo);
+    double h = __dadd_rn(s, e);
+    ddv r;
+    r.hi = h;
+    r.lo = __dsub_rn(e, __dsub_rn(h, s));
+    return r;
+}
+
+// Double-double addition (two TwoSums, two renormalisations).
+__device__ __forceinline__ ddv dd_add(ddv a, ddv b) {
+    double s = __dadd_rn(a.hi, b.hi);
+    double bb = __dsub_rn(s, a.hi);
+    double e = __dadd_rn(__dsub_rn(a.hi, __dsub_rn(s, bb)), __dsub_rn(b.hi, bb));
+    double t = __dadd_rn(a.lo, b.lo);
+    double tb = __dsub_rn(t, a.lo);
+    double f = __dadd_rn(__dsub_rn(a.lo, __dsub_rn(t, tb)), __dsub_rn(b.lo, tb));
+    e = __dadd_rn(e, t);
+    double h = __dadd_rn(s, e);
+    e = __dsub_rn(e, __dsub_rn(h, s));
+    e = __dadd_rn(e, f);
+    ddv r;
+    r.hi = __dadd_rn(h, e);
+    r.lo = __dsub_rn(e, __dsub_rn(r.hi, h));
+    return r;
+}
+
+struct ffv {
+    float hi, lo;
+};
+
+// TwoSum in single precision: adds a float into a float-float.
+__device__ __forceinline__ ffv ff_add_f(ffv a, float b) {
+    float s = __fadd_rn(a.hi, b);
+    float bb = __fsub_rn(s, a.hi);
+    float e = __fadd_rn(__fsub_rn(a.hi, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+    e = __fadd_rn(e, a.lo);
+    ffv r;
+    r.hi = __fadd_rn(s, e);
+    r.lo = __fsub_rn(e, __fsub_rn(r.hi, s));
+    return r;
+}
+
+__device__ __forceinline__ ddv dd_from_ff(ffv a) {
+    ddv r;
+    r.hi = (double)a.hi;
+    r.lo = 0.0;
+    return dd_add_d(r, (double)a.lo);
+}
+
+// Float-float addition (TwoSum of the high parts, low parts added, one
+// renormalisation); used for cross-lane sums in the FP32 kernels so that no
+// FP64 instruction runs in their loops.
+__device__ __forceinline__ ffv ff_add(ffv a, ffv b) {
+    float s = __fadd_rn(a.hi, b.hi);
+    float bb = __fsub_rn(s, a.hi);
+    float e = __fadd_rn(__fsub_rn(a.hi, __fsub_rn(s, bb)), __fsub_rn(b.hi, bb));
+    e = __fadd_rn(e, __fadd_rn(a.lo, b.lo));
+    ffv r;
+    r.hi = __fadd_rn(s, e);
+    r.lo = __fsub_rn(e, __fsub_rn(r.hi, s));
+    return r;
+}
+
+__device__ __forceinline__ ffv shfl_down_ff(ffv v, int off) {
+    ffv r;
+    r.hi = __shfl_down_sync(0xffffffffu, v.hi, off);
+    r.lo = __shfl_down_sync(0xffffffffu, v.lo, off);
+    return r;
+}
+
+__device__ __forceinline__ ddv shfl_down_dd(ddv v, int off) {
+    ddv r;
+    r.hi = __shfl_down_sync(0xffffffffu, v.hi, off);
+    r.lo = __shfl_down_sync(0xffffffffu, v.lo, off);
+    return r;
+}
+
+// Fixed-order warp reduction of a double-double complex value; lane 0 ends
+// with the sum.
+__device__ __forceinline__ void warp_reduce_zdd(ddv& re, ddv& im) {
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) {
+        ddv ore = shfl_down_dd(re, off);
+        ddv oim = shfl_down_dd(im, off);
+        re = dd_add(re, ore);
+        im = dd_add(im, oim);
+    }
+}
+
+__device__ __forceinline__ double flip_sign(double x) {
+    return __longlong_as_double(__double_as_longlong(x) ^ (long long)0x8000000000000000ull);
+}
+__device__ __forceinline__ float flip_sign(float x) {
+    return __int_as_float(__float_as_int(x) ^ (int)0x80000000u);
+}
+
+// +1 or -1 (neg = 1) built from bits, so no int-to-float conversion runs in
+// the loop.
+__device__ __forceinline__ float unit_sign_f(uint32_t neg) { return __int_as_float(0x3f800000u | (neg << 31)); }
+__device__ __forceinline__ double unit_sign_d(uint32_t neg) {
+    return __longlong_as_double((long long)(0x3ff0000000000000ull | ((unsigned long long)neg << 63)));
+}
+template <typename T>
+__device__ __forceinline__ T unit_sign(uint32_t neg);
+template <>
+__device__ __forceinline__ float unit_sign<float>(uint32_t neg) { return unit_sign_f(neg); }
+template <>
+__device__ __forceinline__ double unit_sign<double>(uint32_t neg) { return unit_sign_d(neg); }
+
+// In-chunk stepper.  A chunk starts at a multiple i0 of L = 2^log2L and
+// takes fewer than L steps, so the index i0 + s has exactly the trailing
+// ones of s: the digit that moves at step s -> s + 1 is t = ctz(s + 1) < 12
+// when t < nbin (a binary flip, 32-bit arithmetic only), and otherwise every
+// binary digit is saturated and a repeated-row digit moves (general step).
+struct ChunkStepper {
+    bs_gray g;
+    uint64_t i0;
+    uint32_t dlo;   // Delta bits of binary digits 0..31
+    int parity0;    // parity at the chunk start
+    int nbin;
+
+    __device__ __forceinline__ void init(uint64_t start, int nb, int nrows, const int* radix) {
+        bs_gray_decode(g, start, nb, nrows, radix);
+        i0 = start;
+        dlo = (uint32_t)g.dbin;
+        parity0 = g.parity;
+        nbin = nb;
+    }
+    // Move from index i0 + s to i0 + s + 1.  Returns the digit row; *neg is 1
+    // when the column sums move by -2a_row (Delta rises), 0 for +2a_row;
+    // *wch is 1 when the binomial weight changed (then g.w, g.parity are
+    // current).
+    __device__ __forceinline__ int step(uint32_t s, const int* radix, uint32_t* neg, int* wch) {
+        const int t = __ffs((int)(s + 1u)) - 1;
+        if (t < nbin) {
+            const uint32_t was = (dlo >> t) & 1u;
+            dlo ^= 1u << t;
+            *neg = was ^ 1u;
+            *wch = 0;
+            return t;
+        }
+        g.i = i0 + s;
+        g.parity = parity0 ^ (int)(s & 1u);
+        g.dbin = (g.dbin & ~0xffffffffull) | (uint64_t)dlo;
+        int coef;
+        const int row = bs_gray_step(g, radix, &coef, wch);
+        *neg = coef < 0 ? 1u : 0u;
+        return row;
+    }
+};
+
+// Padded row stride of the packed matrix: an even number of columns, so
+// FP32 rows load as 16-byte column pairs.
+__device__ __forceinline__ int row_stride(int K) { return BS_ROW_STRIDE(K); }
+
+// Column `col` of a bucket KB is live when col < K; K >= KB - 3 always, so
+// only the last three columns of a bucket need a runtime test.
+#define BS_LIVE(col) ((col) < KB - 3 || (col) < K)
+
+// Seed the column sums of the decoded state: c = c0 - sum_j Delta_j * 2a_j
+// (rows of the packed matrix have stride KP).
+template <typename T, int KB>
+__device__ __forceinline__ void seed_columns(cx<T> (&c)[KB], const bs_gray& g, const cx<T>* __restrict__ c0,
+                                             const cx<T>* __restrict__ a2, int K, int KP, int nbin, int nrows) {
+#pragma unroll
+    for (int col = 0; col < KB; ++col)
+        if (BS_LIVE(col)) c[col] = c0[col];
+    uint64_t bits = g.dbin;
+    while (bits) {
+        int j = bs_ctz64(bits);
+        bits &= bits - 1;
+        const cx<T>* row = a2 + (size_t)j * KP;
+#pragma unroll
+        for (int col = 0; col < KB; ++col)
+            if (BS_LIVE(col)) {
+                cx<T> a = row[col];
+                c[col].re -= a.re;
+                c[col].im -= a.im;
+            }
+    }
+    for (int j = nbin; j < nrows; ++j) {
+        int d = g.del[j];
+        if (d == 0) continue;
+        T fd = (T)(-d);
+        const cx<T>* row = a2 + (size_t)j * KP;
+#pragma unroll
+        for (int col = 0; col < KB; ++col)
+            if (BS_LIVE(col)) {
+                cx<T> a = row[col];
+                c[col].re = bfma(fd, a.re, c[col].re);
+                c[col].im = bfma(fd, a.im, c[col].im);
+            }
+    }
+}
+
+__device__ __forceinline__ cx<double> ldg_cx(const cx<double>* p) {
+    double2 v = __ldg(reinterpret_cast<const double2*>(p));
+    return cx<double>{v.x, v.y};
+}
+
+// c_col += cf * row_col for the live columns (FP64: one 16-byte load per
+// column; FP32: one 16-byte load per column pair, rows padded to even K).
+template <int KB>
+__device__ __forceinline__ void update_columns(cx<double> (&c)[KB], const cx<double>* __restrict__ row, double cf,
+                                               int K) {
+#pragma unroll
+    for (int col = 0; col < KB; ++col)
+        if (BS_LIVE(col)) {
+            cx<double> a = ldg_cx(row + col);
+            c[col].re = bfma(cf, a.re, c[col].re);
+            c[col].im = bfma(cf, a.im, c[col].im);
+        }
+}
+template <int KB>
+__device__ __forceinline__ void update_columns(cx<float> (&c)[KB], const cx<float>* __restrict__ row, float cf,
+                                               int K) {
+#pragma unroll
+    for (int p = 0; p < KB / 2; ++p) {
+        const int col = 2 * p;
+        if (BS_LIVE(col)) {
+            const float4 v = __ldg(reinterpret_cast<const float4*>(row) + p);
+            c[col].re = bfma(cf, v.x, c[col].re);
+            c[col].im = bfma(cf, v.y, c[col].im);
+            if (BS_LIVE(col + 1)) {
+                c[col + 1].re = bfma(cf, v.z, c[col + 1].re);
+                c[col + 1].im = bfma(cf, v.w, c[col + 1].im);
+            }
+        }
+    }
+}
+
+// prod_col c_col with two interleaved chains (even / odd columns).
+template <typename T, int KB>
+__device__ __forceinline__ cx<T> product_columns(const cx<T> (&c)[KB], int K) {
+    if (KB == 4 && K == 1) return c[0];
+    cx<T> pe = c[0];
+    cx<T> po = c[1];
+#pragma unroll
+    for (int col = 2; col < KB; ++col)
+        if (BS_LIVE(col)) {
+            if (col & 1)
+                po = cmul(po, c[col]);
+            else
+                pe = cmul(pe, c[col]);
+        }
+    return cmul(pe, po);
+}
+
+template <typename T>
+__device__ __forceinline__ T signed_weight(uint64_t w, int parity) {
+    T x = (T)w;
+    return parity ? -x : x;
+}
+
+__device__ __forceinline__ void store_partial(bs_zdd* p, ddv re, ddv im) {
+    bs_zdd o;
+    o.re_hi = re.hi;
+    o.re_lo = re.lo;
+    o.im_hi = im.hi;
+    o.im_lo = im.lo;
+    *p = o;
+}
+
+// ---------------------------------------------------------------- one task: permanent
+// Each lane: plain-precision runs of FOLD addends folded into a compensated
+// sum (double-double in FP64, float-float in FP32); the 32 lanes are then
+// combined in the same compensated format (no FP64 instruction in the FP32
+// kernel) and lane 0 writes the task's double-double partial.
+template <typename T, int KB>
+__device__ void walk_task_perm(const bs_job& jb, const cx<T>* __restrict__ data, const int* __restrict__ radix,
+                               bs_zdd* __restrict__ partials, uint32_t local, int lane) {
+    constexpr bool F64 = sizeof(T) == 8;
+    constexpr uint32_t FOLD = F64 ? 64 : 32;
+    const int K = jb.K;
+    const int KP = row_stride(K);
+    const cx<T>* c0 = data + jb.data_off;
+    const cx<T>* a2 = c0 + KP;
+    ddv sre = {0.0, 0.0}, sim = {0.0, 0.0};
+    ffv fre = {0.f, 0.f}, fim = {0.f, 0.f};
+    const uint64_t i0 = ((uint64_t)local * 32u + (uint64_t)lane) << jb.log2L;
+    if (i0 < jb.C) {
+        const uint64_t rem = jb.C - i0;
+        const uint32_t len = (uint32_t)(rem < (1ull << jb.log2L) ? rem : (1ull << jb.log2L));
+        ChunkStepper st;
+        st.init(i0, jb.nbin, jb.nrows, radix);
+        cx<T> c[KB];
+        seed_columns<T, KB>(c, st.g, c0, a2, K, KP, jb.nbin, jb.nrows);
+        T ws = signed_weight<T>(st.g.w, st.g.parity);
+        cx<T> acc = {(T)0, (T)0};
+        uint32_t run = 0;
+        for (uint32_t s = 0;; ++s) {
+            const cx<T> p = product_columns<T, KB>(c, K);
+            acc.re = bfma(ws, p.re, acc.re);
+            acc.im = bfma(ws, p.im, acc.im);
+            if (++run == FOLD) {
+                run = 0;
+                if constexpr (F64) {
+                    sre = dd_add_d(sre, (double)acc.re);
+                    sim = dd_add_d(sim, (double)acc.im);
+                } else {
+                    fre = ff_add_f(fre, (float)acc.re);
+                    fim = ff_add_f(fim, (float)acc.im);
+                }
+                acc.re = (T)0;
+                acc.im = (T)0;
+            }
+            if (s + 1 == len) break;
+            uint32_t neg;
+            int wch;
+            const int row = st.step(s, radix, &neg, &wch);
+            ws = wch ? signed_weight<T>(st.g.w, st.g.parity) : flip_sign(ws);
+            update_columns<KB>(c, a2 + (size_t)row * KP, unit_sign<T>(neg), K);
+        }
+        if constexpr (F64) {
+            sre = dd_add_d(sre, (double)acc.re);
+            sim = dd_add_d(sim, (double)acc.im);
+        } else {
+            fre = ff_add_f(fre, (float)acc.re);
+            fim = ff_add_f(fim, (float)acc.im);
+        }
+    }
+    if constexpr (F64) {
+        warp_reduce_zdd(sre, sim);
+    } else {
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) {
+            fre = ff_add(fre, shfl_down_ff(fre, off));
+            fim = ff_add(fim, shfl_down_ff(fim, off));
+        }
+        if (lane == 0) {
+            sre = dd_from_ff(fre);
+            sim = dd_from_ff(fim);
+        }
+    }
+    if (lane == 0) store_partial(partials + jb.partial_off + local, sre, sim);
+}
+
+// ---------------------------------------------------------------- one task: minors, FP64
+// Suffix products and per-column accumulators live in shared memory, laid
+// out [col][thread] (conflict-free); the column sums stay in registers.  The
+// FP64 pipe is the bottleneck, so the extra shared-memory traffic is free.
+template <int KB>
+__device__ void walk_task_minors_fp64(const bs_job& jb, const cx<double>* __restrict__ data,
+                                      const int* __restrict__ radix, bs_zdd* __restrict__ partials, uint32_t local,
+                                      int lane, cx<double>* __restrict__ sm_suf, cx<double>* __restrict__ sm_acc,
+                                      int stride) {
+    const int K = jb.K;
+    const int KP = row_stride(K);
+    const cx<double>* c0 = data + jb.data_off;
+    const cx<double>* a2 = c0 + KP;
+#pragma unroll
+    for (int col = 0; col < KB; ++col)
+        if (BS_LIVE(col)) sm_acc[col * stride] = cx<double>{0.0, 0.0};
+    const uint64_t i0 = ((uint64_t)local * 32u + (uint64_t)lane) << jb.log2L;
+    if (i0 < jb.C) {
+        const uint64_t rem = jb.C - i0;
+        const uint32_t len = (uint32_t)(rem < (1ull << jb.log2L) ? rem : (1ull << jb.log2L));
+        ChunkStepper st;
+        st.init(i0, jb.nbin, jb.nrows, radix);
+        cx<double> c[KB];
+        seed_columns<double, KB>(c, st.g, c0, a2, K, KP, jb.nbin, jb.nrows);
+        double ws = signed_weight<double>(st.g.w, st.g.parity);
+        for (uint32_t s = 0;; ++s) {
+            // suffix pass: suf[l] = ws * prod_{col > l} c_col
+            cx<double> sfx = {ws, 0.0};
+            bool top = true;
+#pragma unroll
+            for (int col = KB - 1; col >= 0; --col)
+                if (BS_LIVE(col)) {
+                    sm_suf[col * stride] = sfx;
+                    if (col > 0) {
+                        if (top) {
+                            sfx.re = ws * c[col].re;
+                            sfx.im = ws * c[col].im;
+                        } else {
+                            sfx = cmul(sfx, c[col]);
+                        }
+                    }
+                    top = false;
+                }
+            // forward pass: acc[l] += (prod_{col < l} c_col) * suf[l]
+            cx<double> pre = c[0];
+            {
+                cx<double> a = sm_acc[0];
+                cx<double> f = sm_suf[0];
+                a.re += f.re;
+                a.im += f.im;
+                sm_acc[0] = a;
+            }
+#pragma unroll
+            for (int col = 1; col < KB; ++col)
+                if (BS_LIVE(col)) {
+                    cx<double> a = sm_acc[col * stride];
+                    cx<double> f = sm_suf[col * stride];
+                    a.re = bfma(pre.re, f.re, a.re);
+                    a.re = bfma(-pre.im, f.im, a.re);
+                    a.im = bfma(pre.re, f.im, a.im);
+                    a.im = bfma(pre.im, f.re, a.im);
+                    sm_acc[col * stride] = a;
+                    if (col + 1 < KB - 3 || col + 1 < K) pre = cmul(pre, c[col]);
+                }
+            if (s + 1 == len) break;
+            uint32_t neg;
+            int wch;
+            const int row = st.step(s, radix, &neg, &wch);
+            ws = wch ? signed_weight<double>(st.g.w, st.g.parity) : flip_sign(ws);
+            update_columns<KB>(c, a2 + (size_t)row * KP, unit_sign_d(neg), K);
+        }
+    }
+    for (int col = 0; col < K; ++col) {
+        cx<double> a = sm_acc[col * stride];
+        ddv re = {a.re, 0.0}, im = {a.im, 0.0};
+        warp_reduce_zdd(re, im);
+        if (lane == 0) store_partial(partials + jb.partial_off + (int64_t)local * K + col, re, im);
+    }
+}
+
+// ---------------------------------------------------------------- one task: minors, FP32
+// Two lanes share one chunk: lane (2p + h) owns columns [h*H, h*H + H),
+// H = KB/2.  Per addend each lane
+//   1. forms suffix products over its own columns, starting from 1; the
+//      last one is Q_own = prod of its own columns,
+//   2. swaps Q with its partner (one shuffle of a complex value),
+//   3. runs the prefix pass over its own columns starting from
+//      X = (+-W) * Q_partner:  acc[l] += X * prefix_l * suffix_l.
+// Both lanes run the same instructions, the arithmetic equals the one-lane
+// form, and each lane holds only H column sums, suffixes and accumulators.
+// A warp task therefore covers 16 chunks.  Float-float fold targets live in
+// shared memory, [col][thread]; the cross-lane sums stay in float-float.
+template <int KB>
+__device__ void walk_task_minors_fp32(const bs_job& jb, const cx<float>* __restrict__ data,
+                                      const int* __restrict__ radix, bs_zdd* __restrict__ partials, uint32_t local,
+                                      int lane, float4* __restrict__ sm_ff, int stride) {
+    constexpr uint32_t FOLD = 32;
+    constexpr int H = KB / 2;
+    const int K = jb.K;
+    const int KP = row_stride(K);
+    const int half = lane & 1;
+    const int cbase = half * H;
+    // live columns of this lane: t < KH (only the last 3 of a half can die)
+    const int KH = min(H, max(K - cbase, 0));
+    const unsigned pair_mask = 3u << (lane & ~1);
+#define BS_LIVEH(t) ((t) < H - 3 || (t) < KH)
+    const cx<float>* c0 = data + jb.data_off;
+    const cx<float>* a2 = c0 + KP;
+#pragma unroll
+    for (int t = 0; t < H; ++t)
+        if (BS_LIVEH(t)) sm_ff[t * stride] = make_float4(0.f, 0.f, 0.f, 0.f);
+    const uint64_t i0 = ((uint64_t)local * 16u + (uint64_t)(lane >> 1)) << jb.log2L;
+    // both lanes of a pair take the same branch
+    if (i0 < jb.C) {
+        const uint64_t rem = jb.C - i0;
+        const uint32_t len = (uint32_t)(rem < (1ull << jb.log2L) ? rem : (1ull << jb.log2L));
+        ChunkStepper st;
+        st.init(i0, jb.nbin, jb.nrows, radix);
+        cx<float> c[H];
+        {
+            // seed own columns: c = c0 - sum_j Delta_j 2a_j
+#pragma unroll
+            for (int t = 0; t < H; ++t)
+                if (BS_LIVEH(t)) c[t] = c0[cbase + t];
+            uint64_t bits = st.g.dbin;
+            while (bits) {
+                int j = bs_ctz64(bits);
+                bits &= bits - 1;
+                const cx<float>* row = a2 + (size_t)j * KP + cbase;
+#pragma unroll
+                for (int t = 0; t < H; ++t)
+                    if (BS_LIVEH(t)) {
+                        c[t].re -= row[t].re;
+                        c[t].im -= row[t].im;
+                    }
+            }
+            for (int j = jb.nbin; j < jb.nrows; ++j) {
+                int d = st.g.del[j];
+                if (d == 0) continue;
+                float fd = (float)(-d);
+                const cx<float>* row = a2 + (size_t)j * KP + cbase;
+#pragma unroll
+                for (int t = 0; t < H; ++t)
+                    if (BS_LIVEH(t)) {
+                        c[t].re = bfma(fd, row[t].re, c[t].re);
+                        c[t].im = bfma(fd, row[t].im, c[t].im);
+                    }
+            }
+        }
+        float ws = signed_weight<float>(st.g.w, st.g.parity);
+        cx<float> acc[H];
+#pragma unroll
+        for (int t = 0; t < H; ++t) acc[t] = cx<float>{0.f, 0.f};
+        uint32_t run = 0;
+        for (uint32_t s = 0;; ++s) {
+            // 1. suffix products over own columns, from 1
+            cx<float> suf[H];
+            cx<float> sfx = {1.f, 0.f};
+            bool first = true;
+#pragma unroll
+            for (int t = H - 1; t >= 0; --t)
+                if (BS_LIVEH(t)) {
+                    suf[t] = sfx;
+                    sfx = first ? c[t] : cmul(sfx, c[t]);
+                    first = false;
+                }
+            // a lane with no live columns contributes Q = 1
+            // 2. swap Q with the partner lane (pairs leave the loop at
+            //    different steps: only the pair syncs)
+            cx<float> q;
+            q.re = __shfl_xor_sync(pair_mask, sfx.re, 1);
+            q.im = __shfl_xor_sync(pair_mask, sfx.im, 1);
+            // 3. prefix pass from X = ws * Q_partner
+            cx<float> pre = {ws * q.re, ws * q.im};
+#pragma unroll
+            for (int t = 0; t < H; ++t)
+                if (BS_LIVEH(t)) {
+                    acc[t].re = bfma(pre.re, suf[t].re, acc[t].re);
+                    acc[t].re = bfma(-pre.im, suf[t].im, acc[t].re);
+                    acc[t].im = bfma(pre.re, suf[t].im, acc[t].im);
+                    acc[t].im = bfma(pre.im, suf[t].re, acc[t].im);
+                    if (t + 1 < H - 3 || t + 1 < KH) pre = cmul(pre, c[t]);
+                }
+            if (++run == FOLD) {
+                run = 0;
+#pragma unroll
+                for (int t = 0; t < H; ++t)
+                    if (BS_LIVEH(t)) {
+                        float4 f = sm_ff[t * stride];
+                        ffv re = {f.x, f.y}, im = {f.z, f.w};
+                        re = ff_add_f(re, acc[t].re);
+                        im = ff_add_f(im, acc[t].im);
+                        sm_ff[t * stride] = make_float4(re.hi, re.lo, im.hi, im.lo);
+                        acc[t] = cx<float>{0.f, 0.f};
+                    }
+            }
+            if (s + 1 == len) break;
+            uint32_t neg;
+            int wch;
+            const int row = st.step(s, radix, &neg, &wch);
+            ws = wch ? signed_weight<float>(st.g.w, st.g.parity) : flip_sign(ws);
+            const float4* rp = reinterpret_cast<const float4*>(a2 + (size_t)row * KP + cbase);
+            const float cf = unit_sign_f(neg);
+#pragma unroll
+            for (int p = 0; p < H / 2; ++p)
+                if (BS_LIVEH(2 * p)) {
+                    const float4 v = __ldg(rp + p);
+                    c[2 * p].re = bfma(cf, v.x, c[2 * p].re);
+                    c[2 * p].im = bfma(cf, v.y, c[2 * p].im);
+                    if (BS_LIVEH(2 * p + 1)) {
+                        c[2 * p + 1].re = bfma(cf, v.z, c[2 * p + 1].re);
+                        c[2 * p + 1].im = bfma(cf, v.w, c[2 * p + 1].im);
+                    }
+                }
+        }
+#pragma unroll
+        for (int t = 0; t < H; ++t)
+            if (BS_LIVEH(t)) {
+                float4 f = sm_ff[t * stride];
+                ffv re = {f.x, f.y}, im = {f.z, f.w};
+                re = ff_add_f(re, acc[t].re);
+                im = ff_add_f(im, acc[t].im);
+                sm_ff[t * stride] = make_float4(re.hi, re.lo, im.hi, im.lo);
+            }
+    }
+    // reduce over the 16 pairs in float-float: lanes of equal parity; lane 0
+    // / lane 1 end with the sums of columns [0, H) / [H, 2H)
+    for (int t = 0; t < H; ++t) {
+        const float4 f = (t < KH) ? sm_ff[t * stride] : make_float4(0.f, 0.f, 0.f, 0.f);
+        ffv re = {f.x, f.y}, im = {f.z, f.w};
+#pragma unroll
+        for (int off = 16; off > 1; off >>= 1) {
+            re = ff_add(re, shfl_down_ff(re, off));
+            im = ff_add(im, shfl_down_ff(im, off));
+        }
+        if (lane < 2 && t < KH)
+            store_partial(partials + jb.partial_off + (int64_t)local * K + cbase + t, dd_from_ff(re), dd_from_ff(im));
+    }
+#undef BS_LIVEH
+}
+
+#undef BS_LIVE
+
+__device__ __forceinline__ unsigned long long global_ns() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+// Job owning global task t: the last job (in list order) whose task_begin
+// <= t.  Jobs are jobs[i], or jobs[list[i]] when a device-built list is
+// given.
+__device__ __forceinline__ int find_job(const bs_job* __restrict__ jobs, const int* __restrict__ list, int njobs,
+                                        unsigned long long t) {
+    int lo = 0, hi = njobs - 1;
+    while (lo < hi) {
+        int mid = (lo + hi + 1) >> 1;
+        const int jm = list ? list[mid] : mid;
+        if (jobs[jm].task_begin <= t)
+            lo = mid;
+        else
+            hi = mid - 1;
+    }
+    return list ? list[lo] : lo;
+}
+
+// Pull the next warp task (lane 0 takes it, all lanes learn it).  A task
+// index >= total means stop: either the work is done or the deadline passed
+// (then the status word says so and the host reports a timeout).
+// deadline_ns is absolute (%globaltimer), 0 = none.
+__device__ __forceinline__ unsigned long long next_task(unsigned long long* counter, unsigned long long total,
+                                                        int* status, unsigned long long deadline_ns, int lane) {
+    unsigned long long t = 0;
+    if (lane == 0) {
+        if (deadline_ns != 0ull && global_ns() > deadline_ns) {
+            atomicExch(status, BS_STATUS_TIMEOUT);
+            t = total;
+        } else {
+            t = atomicAdd(counter, 1ull);
+        }
+    }
+    return __shfl_sync(0xffffffffu, t, 0);
+}
+
+// Per-warp absolute deadline from a relative one (0 = none).
+__device__ __forceinline__ unsigned long long warp_deadline(unsigned long long rel_ns) {
+    return rel_ns == 0ull ? 0ull : global_ns() + rel_ns;
+}
+
+// Task total and job count: from device memory when planned on the device.
+__device__ __forceinline__ unsigned long long task_total(const WalkArgsBase& a) {
+    return a.total_dev ? *a.total_dev : a.total_tasks;
+}
+__device__ __forceinline__ int job_count(const WalkArgsBase& a) { return a.njobs_dev ? *a.njobs_dev : a.njobs; }
+
+}  // namespace bs

@@ -25,3 +25,23 @@ def read_golden(name):
                 continue
             rows.append(line.split())
     return rows
+
+
+@pytest.fixture(scope="session")
+def bslib():
+    """Build (if stale) and load libbs.so."""
+    from paper_2309_07027_gb300 import _build
+    _build.build()
+    import paper_2309_07027_gb300 as bs
+    bs.load()
+    return bs
+
+
+@pytest.fixture(scope="session")
+def ctx(bslib):
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    c = bslib.Context(0)
+    yield c
+    c.close()

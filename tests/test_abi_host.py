@@ -1,0 +1,132 @@
+"""Host-side checks of libbs.so that need no GPU: every symbol declared in
+include/bs.h is exported, the n-ary reflected Gray counter used by the
+kernels (compiled for the host from the same header) has the Gray
+properties of Sec. 2.2, the planner's canonicalisation decisions, and that
+compute calls fail loudly without a device."""
+import ctypes
+import itertools
+import math
+import os
+import re
+
+import numpy as np
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def declared_functions():
+    src = open(os.path.join(ROOT, "include", "bs.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"^\s*(?:int|void|const char\*)\s+(bs_[a-z0-9_]+)\s*\(", src, flags=re.M)))
+
+
+def test_all_declared_symbols_exported(bslib):
+    names = declared_functions()
+    assert len(names) >= 20
+    lib = ctypes.CDLL(bslib.library_path())
+    for n in names:
+        assert hasattr(lib, n), n
+
+
+def _reference_gray(radix):
+    """Reflected mixed-radix Gray code by its recursive definition: the code
+    for digits 0..j is the code for digits 0..j-1 traversed forward for even
+    values of digit j and backward for odd values (digit 0 fastest)."""
+    seq = [()]
+    for r in radix:
+        nxt = []
+        for v in range(r):
+            part = seq if v % 2 == 0 else seq[::-1]
+            nxt.extend(code + (v,) for code in part)
+        seq = nxt
+    return [list(c) for c in seq]
+
+
+@pytest.mark.parametrize("radix,nbin", [([2, 2, 2], 3), ([2, 2, 3], 2), ([3, 4, 2], 0), ([2, 3, 3, 5], 1),
+                                        ([2] * 10, 10), ([2, 2, 2, 2, 4, 3], 4), ([5], 0), ([], 0)])
+def test_gray_walk_is_reflected_gray_code(bslib, radix, nbin):
+    C = int(np.prod(radix)) if radix else 1
+    deltas, moved, w = bslib.debug_gray_walk(radix, nbin, 0, C)
+    ref = _reference_gray(radix)
+    assert [list(r) for r in deltas] == ref
+    # one digit moves by +-1 per step, every code appears once
+    for s in range(1, C):
+        diff = deltas[s] - deltas[s - 1]
+        assert np.count_nonzero(diff) == 1 and abs(diff[moved[s]]) == 1
+    assert len({tuple(r) for r in deltas}) == C
+    # weights = prod C(M_j, Delta_j) over digits (binary digits weigh 1)
+    for s in range(C):
+        want = 1
+        for j, r in enumerate(radix):
+            want *= math.comb(r - 1, int(deltas[s][j]))
+        assert int(w[s]) == want
+
+
+@pytest.mark.parametrize("radix,nbin", [([2, 2, 3, 4], 2), ([2] * 6 + [3, 3], 6), ([4, 5, 3], 0)])
+def test_gray_decode_matches_stepping(bslib, radix, nbin):
+    """Decoding any start index gives the state reached by stepping from 0
+    (Sec. 2.2: constant-time decode enables independent chunks)."""
+    C = int(np.prod(radix))
+    full, _, wf = bslib.debug_gray_walk(radix, nbin, 0, C)
+    for start in range(0, C, max(1, C // 17)):
+        part, _, wp = bslib.debug_gray_walk(radix, nbin, start, C - start)
+        assert np.array_equal(part, full[start:])
+        assert np.array_equal(wp, wf[start:])
+
+
+def test_gray_binary_matches_paper_table(bslib):
+    from conftest import read_golden
+    deltas, moved, _ = bslib.debug_gray_walk([2, 2, 2], 3, 0, 8)
+    gold = read_golden("gray_code_3bit.txt")
+    for (idx, code), row in zip(gold, deltas):
+        # code string is written most significant bit first
+        assert "".join(str(int(b)) for b in row[::-1]) == code
+
+
+def test_gray_walk_rejects_bad_radix(bslib):
+    with pytest.raises(bslib.BsError):
+        bslib.debug_gray_walk([3, 2], 1, 0, 2)      # first digit must be binary
+    with pytest.raises(bslib.BsError):
+        bslib.debug_gray_walk([2, 2], 2, 3, 5)      # walk leaves [0, C)
+
+
+def test_planner_addend_counts_and_orientation(bslib):
+    # config 1: rows (3,2,2,1,1,1,1,1), 12 distinct columns -> 4*3*3*2^4 = 576
+    p = bslib.debug_plan([3, 2, 2, 1, 1, 1, 1, 1], [1] * 12)
+    assert p["C"] == 576 and p["K"] == 12 and not p["transposed"]
+    assert p["nbin"] == 4 and p["nrows"] == 7
+    # the orientation with repeated entries on the row side is chosen:
+    # rows cost 1 * 2^5 = 32 addends, columns 3 * 4 = 12
+    q = bslib.debug_plan([1] * 6, [3, 3])
+    assert q["transposed"] and q["C"] == 12 and q["K"] == 6
+    # rows (2,3) x one column of multiplicity 5: transposed, the single row
+    # of multiplicity 5 splits into the pinned copy + a radix-5 digit
+    r = bslib.debug_plan([2, 3], [5])
+    assert r["transposed"] and r["C"] == 5 and r["nrows"] == 1 and r["K"] == 5
+    # no row of multiplicity one and no cheaper transpose: the smallest
+    # multiplicity is split (1 + (M-1)): digits radix 2 and 4
+    t = bslib.debug_plan([2, 3], [1] * 5)
+    assert not t["transposed"] and t["C"] == 8 and t["nrows"] == 2 and t["nbin"] == 1
+    # zero multiplicities are dropped
+    z = bslib.debug_plan([0, 1, 0, 1], [1, 0, 1])
+    assert z["C"] == 2 and z["K"] == 2
+    # minors: sum M = sum N - 1, never transposed, K = sum N
+    m = bslib.debug_plan([1, 1], [1, 1, 1], kind=1)
+    assert m["C"] == 2 and m["K"] == 3 and not m["transposed"]
+
+
+def test_planner_rejects_invalid(bslib):
+    for M, N, kind in [([1, 1], [1], 0), ([-1, 2], [1], 0), ([25, 25], [50], 0), ([1], [1], 1)]:
+        with pytest.raises(bslib.BsError) as e:
+            bslib.debug_plan(M, N, kind)
+        assert e.value.code == bslib.BS_EINVAL
+
+
+def test_no_gpu_fails_loudly(bslib):
+    import torch
+    if torch.cuda.is_available():
+        pytest.skip("a GPU is present")
+    with pytest.raises(bslib.BsError) as e:
+        bslib.Context(0)
+    assert "BS_ENODEV" in str(e.value)

@@ -1,0 +1,322 @@
+"""GPU parity: the CUDA path (through the C ABI) against the CPU oracle.
+
+Tolerances (from the accuracy targets of the method, Sec. 3.2):
+  FP64 mode   |perm_gpu - perm_oracle| <= 1e-10 * prod_j ||a_j||_2^{N_j}
+  MIXED mode  |perm_gpu - perm_oracle| <= 1e-6  * prod_j ||a_j||_2^{N_j}
+with ||a_j|| the 2-norm of column j over the rows repeated by their
+multiplicities (a Hadamard-type scale of the permanent).  Heavily repeated
+rows make the addends cancel far below that scale; there the rounding
+error is bounded by the modulus-sum of the addends S_abs (oracle
+perm_mult_abs): each addend carries a relative error of about K u, so
+|error| <= TOL_L1 * S_abs with TOL_L1 = 1e-12 (FP64; K <= 48, u = 2^-53,
+plus the re-seeded column-sum drift).  MIXED mode sends such jobs to the
+FP64 kernels, so the same bound applies to them.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+import synthetic as S
+
+pytestmark = pytest.mark.gpu
+
+TOL = {0: 1e-10, 1: 1e-6}
+TOL_L1 = 1e-12
+
+
+def scale(a, M, N):
+    a = np.asarray(a)
+    M = np.asarray(M)
+    N = np.asarray(N)
+    norms = np.sqrt((np.abs(a) ** 2 * M[:, None]).sum(axis=0))
+    return float(np.prod(norms ** N))
+
+
+def minor_scale(a, M, N, l):
+    N2 = np.array(N).copy()
+    N2[l] -= 1
+    return scale(a, M, N2)
+
+
+def ref_perm(a, M, N):
+    v, t = oracle.perm_mult(a, M, N)
+    return v + t
+
+
+@pytest.mark.parametrize("mode", [0, 1])
+def test_config_single_perm(ctx, mode):
+    a, M, N, _, _ = S.config_single(seed=1)
+    got = ctx.perm(a, M, N, mode=mode)
+    ref = ref_perm(a, M, N)
+    assert abs(got - ref) <= TOL[mode] * scale(a, M, N), (got, ref)
+    if mode == 0:
+        got2, tail = ctx.perm(a, M, N, mode=0, with_tail=True)
+        assert abs((got2 + tail) - ref) <= 1e-13 * scale(a, M, N)
+
+
+@pytest.mark.parametrize("mode", [0, 1])
+def test_config_single_minors(ctx, mode):
+    a, M, N, _, _ = S.config_single(seed=1)
+    # remove one photon from the last multiplicity-1 row: 11 rows x 12 columns
+    M2 = M.copy()
+    M2[-1] -= 1
+    got = ctx.laplace_minors(a, M2, N, mode=mode)
+    ref, tail = oracle.minors(a, M2, N)
+    for l in range(len(N)):
+        assert abs(got[l] - (ref[l] + tail[l])) <= TOL[mode] * minor_scale(a, M2, N, l), l
+    # Laplace identity: sum_l N_l a_{r,l} minor_l = perm with row r restored
+    full = ref_perm(a, M, N)
+    lap = np.sum(N * a[-1] * got)
+    assert abs(lap - full) <= 10 * TOL[mode] * scale(a, M, N)
+
+
+@pytest.mark.parametrize("mode", [0, 1])
+@pytest.mark.parametrize("n", [1, 2, 3, 4, 5, 7, 8, 9, 12, 13, 16, 17, 20, 21])
+def test_distinct_sizes(ctx, mode, n):
+    """Distinct rows and columns: C = 2^(n-1) addends, spanning many chunks
+    and tasks with a ragged last task."""
+    u = S.haar_unitary(48, 100 + n)
+    a = u[:n, 10:10 + n]
+    ones = np.ones(n, dtype=np.int32)
+    got = ctx.perm(a, ones, ones, mode=mode)
+    v, t = oracle.bbfg_gray(a)
+    assert abs(got - (v + t)) <= TOL[mode] * scale(a, ones, ones), (n, got, v)
+
+
+@pytest.mark.parametrize("mode", [0, 1])
+@pytest.mark.parametrize("K", [4, 6, 11, 15, 19, 24, 27, 30, 32, 33, 36, 38, 41, 44, 45, 48])
+def test_every_column_bucket(ctx, mode, K):
+    """Few distinct rows with large multiplicities: every K bucket (up to 48
+    product columns) with an addend count the oracle finishes quickly."""
+    g = S.rng(2000 + K)
+    R = 3 if K > 30 else 4
+    M = np.full(R, K // R, dtype=np.int32)
+    M[: K - M.sum()] += 1
+    u = S.haar_unitary(64, 300 + K)
+    a = u[g.permutation(64)[:R]][:, g.permutation(64)[:K]]
+    N = np.ones(K, dtype=np.int32)
+    got = ctx.perm(a, M, N, mode=mode)
+    ref = ref_perm(a, M, N)
+    bound = TOL[mode] * scale(a, M, N) + TOL_L1 * oracle.perm_mult_abs(a, M, N)
+    assert abs(got - ref) <= bound, (K, got, ref, bound)
+
+
+def test_mixed_routes_heavy_collisions_to_fp64(ctx):
+    """MIXED keeps FP32 only while prod C(M, M/2) <= 128; heavier jobs run in
+    the FP64 kernels and give exactly the FP64-mode result."""
+    u = S.haar_unitary(40, 9)
+    a = u[:3, :20]
+    M = np.array([7, 7, 6], dtype=np.int32)       # weights 35 * 35 * 10 > 128
+    N = np.ones(20, dtype=np.int32)
+    assert ctx.perm(a, M, N, mode=1) == ctx.perm(a, M, N, mode=0)
+    b = u[:12, :14]
+    Mb = np.array([2, 2, 2] + [1] * 9, dtype=np.int32)  # 2 * 2 * 2 <= 128: FP32
+    Nb = np.ones(14, dtype=np.int32)
+    Nb[0] += 1                                    # sum M = 15 = sum N
+    r64, r32 = ctx.perm(b, Mb, Nb, mode=0), ctx.perm(b, Mb, Nb, mode=1)
+    assert r64 != r32
+    assert abs(r32 - ref_perm(b, Mb, Nb)) <= TOL[1] * scale(b, Mb, Nb)
+
+
+@pytest.mark.parametrize("mode", [0, 1])
+def test_edge_cases(ctx, mode):
+    # n = 0: the empty permanent
+    assert ctx.perm(np.zeros((2, 2)), [0, 0], [0, 0], mode=mode) == 1
+    # n = 1
+    a = np.array([[0.3 - 0.7j]])
+    assert abs(ctx.perm(a, [1], [1], mode=mode) - a[0, 0]) <= TOL[mode] * abs(a[0, 0])
+    # a single row and column repeated n times: perm = n! a^n
+    for n in (2, 5, 9):
+        got = ctx.perm(a, [n], [n], mode=mode)
+        ref = math.factorial(n) * a[0, 0] ** n
+        assert abs(got - ref) <= TOL[mode] * abs(ref) * 10
+    # zero multiplicities, repeated first row, column multiplicities
+    b = S.random_complex(4, 5, 77)
+    M = np.array([3, 0, 2, 1])
+    N = np.array([2, 1, 0, 2, 1])
+    got = ctx.perm(b, M, N, mode=mode)
+    assert abs(got - ref_perm(b, M, N)) <= TOL[mode] * scale(b, M, N)
+    # transposed orientation chosen (columns repeated more than rows)
+    c = S.random_complex(6, 2, 78)
+    got = ctx.perm(c, np.ones(6, np.int32), [3, 3], mode=mode)
+    assert abs(got - ref_perm(c, np.ones(6), [3, 3])) <= TOL[mode] * scale(c, np.ones(6), [3, 3])
+    # all rows repeated (no binary digit besides the split pinned row)
+    d = S.random_complex(3, 6, 79)
+    got = ctx.perm(d, [2, 2, 2], np.ones(6, np.int32), mode=mode)
+    assert abs(got - ref_perm(d, [2, 2, 2], np.ones(6))) <= TOL[mode] * scale(d, [2, 2, 2], np.ones(6))
+
+
+def test_invalid_arguments(ctx, bslib):
+    with pytest.raises(bslib.BsError) as e:
+        ctx.perm(np.ones((2, 2)), [1, 1], [1, 2])
+    assert e.value.code == bslib.BS_EINVAL
+    with pytest.raises(bslib.BsError):
+        ctx.perm(np.ones((2, 2)), [-1, 3], [1, 1])
+    with pytest.raises(bslib.BsError):
+        ctx.perm(np.ones((1, 1)), [49], [49])
+    # the context still works afterwards
+    assert abs(ctx.perm(np.array([[2.0]]), [1], [1]) - 2.0) < 1e-15
+
+
+@pytest.mark.parametrize("mode", [0, 1])
+def test_minors_with_repeats_and_empty(ctx, mode):
+    g = S.rng(55)
+    for trial in range(6):
+        R, K = int(g.integers(1, 5)), int(g.integers(2, 7))
+        a = S.random_complex(R, K, 900 + trial)
+        N = np.ones(K, dtype=np.int32)
+        N[g.integers(0, K)] += 1
+        n = int(N.sum()) - 1
+        M = np.zeros(R, dtype=np.int32)
+        for _ in range(n):
+            M[g.integers(0, R)] += 1
+        got = ctx.laplace_minors(a, M, N, mode=mode)
+        ref, tail = oracle.minors(a, M, N)
+        for l in range(K):
+            assert abs(got[l] - (ref[l] + tail[l])) <= TOL[mode] * max(minor_scale(a, M, N, l), 1e-300) * 10
+    # zero rows: the single minor is per(0x0) = 1
+    got = ctx.laplace_minors(np.zeros((1, 1)), [0], [1], mode=mode)
+    assert got[0] == 1
+
+
+@pytest.mark.parametrize("mode", [0, 1])
+def test_batch_matches_oracle_and_single_calls(ctx, mode):
+    items = S.config_batch(count=48, seed=7, kmin=6, kmax=18, m=60, group=16)
+    items.append((np.zeros((1, 1)), np.array([0]), np.array([0])))       # trivial item
+    got = ctx.perm_batch(items, mode=mode)
+    for b, (a, M, N) in enumerate(items):
+        ref = ref_perm(a, M, N)
+        assert abs(got[b] - ref) <= TOL[mode] * scale(a, M, N) + (0 if np.sum(M) else 1e-300), b
+        # each result is bit-identical whether computed alone or in the batch
+        alone = ctx.perm(a, M, N, mode=mode)
+        assert alone == got[b], (b, alone, got[b])
+
+
+@pytest.mark.parametrize("mode", [0, 1])
+def test_full_batch_config_sampled(ctx, mode):
+    """4096 uneven permanents (k in [10, 28]) in one call; the oracle checks
+    the cheapest items one by one, and FP64 / MIXED agree on every item."""
+    items = S.config_batch(count=4096, seed=2)
+    got = ctx.perm_batch(items, mode=mode)
+    costs = [int(np.prod(np.asarray(M) + 1)) for _, M, _ in items]
+    order = np.argsort(costs)
+    for b in list(order[:12]) + list(order[2048:2051]):
+        a, M, N = items[b]
+        assert abs(got[b] - ref_perm(a, M, N)) <= TOL[mode] * scale(a, M, N), b
+    if mode == 1:
+        ref64 = ctx.perm_batch(items, mode=0)
+        sc = np.array([scale(a, M, N) for a, M, N in items])
+        assert np.all(np.abs(got - ref64) <= 1e-6 * sc)
+
+
+def test_batch_device_pointers(ctx):
+    import torch
+    items = S.config_batch(count=32, seed=9, kmin=8, kmax=14)
+    packed, offs, rows, cols, mults, roff, coff = ctx.pack_batch(items)
+    dev = torch.from_numpy(packed).cuda()
+    out = torch.zeros(len(items), dtype=torch.complex128, device="cuda")
+    ctx.set_stream(torch.cuda.current_stream())
+    try:
+        ctx.perm_batch_dev(dev, offs, rows, cols, mults, roff, coff, 0, out)
+        ctx.sync()
+    finally:
+        ctx.set_stream(None)
+    host = ctx.perm_batch(items, mode=0)
+    assert np.array_equal(out.cpu().numpy(), host)
+
+
+def test_deadline_returns_timeout_and_context_survives(ctx, bslib):
+    u = S.haar_unitary(40, 5)
+    a = u[:30, :30]
+    ones = np.ones(30, dtype=np.int32)
+    ctx.set_deadline(1e-6)
+    try:
+        with pytest.raises(bslib.BsError) as e:
+            ctx.perm(a, ones, ones, mode=0)
+        assert e.value.code == bslib.BS_ETIMEOUT
+    finally:
+        ctx.set_deadline(0.0)
+    b = u[:6, :6]
+    v, t = oracle.bbfg_gray(b)
+    assert abs(ctx.perm(b, np.ones(6), np.ones(6)) - (v + t)) <= 1e-10 * scale(b, np.ones(6), np.ones(6))
+
+
+# ---------------------------------------------------------------- sampling
+def test_sampler_matches_oracle_sampler_fp64(ctx):
+    """Same seed, same Philox counters: the GPU chain and the oracle chain draw
+    the same rows, except a draw that lands within 1e-9 of a CDF boundary."""
+    u, occ = S.config_cc(n=6, m=12, seed=3)
+    ns = 200
+    got = ctx.sample(u, occ, ns, seed=2024, mode=0)
+    ref, margin, _ = oracle.cc_sample(u, occ, ns, seed=2024)
+    mismatch = [s for s in range(ns) if not np.array_equal(got[s], ref[s])]
+    assert all(margin[s] < 1e-9 for s in mismatch), (mismatch, margin[mismatch])
+    assert len(mismatch) <= 1
+    assert np.all(got.sum(axis=1) == 6)
+
+
+def test_sampler_seed_and_batch_independence(ctx):
+    u, occ = S.config_cc(n=8, m=16, seed=4)
+    a = ctx.sample(u, occ, 40, seed=11, mode=0)
+    b = ctx.sample(u, occ, 40, seed=11, mode=0)
+    c = ctx.sample(u, occ, 10, seed=11, mode=0)
+    assert np.array_equal(a, b)
+    assert np.array_equal(a[:10], c)
+
+
+def test_sampler_mixed_chi_square(ctx):
+    st = pytest.importorskip("scipy.stats")
+    import itertools
+    n, m = 3, 5
+    u = S.haar_unitary(m, 31)
+    s = np.zeros(m, dtype=np.int32)
+    s[:n] = 1
+    pats = []
+    for c in itertools.combinations_with_replacement(range(m), n):
+        t = np.zeros(m, dtype=np.int32)
+        for i in c:
+            t[i] += 1
+        pats.append(t)
+    probs = np.array([oracle.bs_probability(u, s, t) for t in pats])
+    counts = ctx.sample(u, s, 20000, seed=99, mode=1)
+    index = {tuple(t): i for i, t in enumerate(pats)}
+    obs = np.zeros(len(pats))
+    for row in counts:
+        obs[index[tuple(row)]] += 1
+    exp = probs * len(counts)
+    keep = exp >= 5
+    o = np.append(obs[keep], obs[~keep].sum())
+    e = np.append(exp[keep], exp[~keep].sum())
+    chi2 = float(np.sum((o - e) ** 2 / np.maximum(e, 1e-300)))
+    assert st.chi2.sf(chi2, len(o) - 1) > 1e-3, chi2
+
+
+def test_sampler_marginals_and_lossy(ctx):
+    u, occ = S.config_cc(n=6, m=12, seed=26)
+    counts = ctx.sample(u, occ, 4000, seed=5, mode=1)
+    ref = (np.abs(u) ** 2) @ occ
+    mean = counts.mean(axis=0)
+    sd = counts.std(axis=0) / np.sqrt(len(counts))
+    assert np.all(np.abs(mean - ref) < 5 * sd + 1e-3)
+    # lossy isometry: detected photon number ~ Binomial(n, eta)
+    v, mdet = S.config_lossy(n=6, m=12, eta=0.5, seed=5)
+    lc = ctx.sample_ex(v, np.ones(6, dtype=np.int32), 4000, seed=6, m_detected=mdet, mode=1)
+    det = lc.sum(axis=1)
+    assert det.max() <= 6
+    assert abs(det.mean() - 3.0) < 5 * math.sqrt(6 * 0.25 / 4000)
+
+
+def test_sampler_first_steps_match_oracle_at_config_size(ctx):
+    """n = 30, m = 60 (the sampling workload): the first 14 steps of a few
+    chains equal the oracle's (the oracle stops after max_steps)."""
+    u, occ = S.config_cc(n=30, m=60, seed=3)
+    full = ctx.sample(u, occ, 4, seed=7, mode=0)
+    assert np.all(full.sum(axis=1) == 30)
+    ref, margin, _ = oracle.cc_sample(u, occ, 4, seed=7, max_steps=14)
+    # the oracle's partial chain is a prefix of the GPU chain: every mode it
+    # occupies after 14 draws is occupied at least as often in the full sample
+    for s in range(4):
+        if margin[s] > 1e-9:
+            assert np.all(full[s] >= ref[s])

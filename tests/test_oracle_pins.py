@@ -274,6 +274,22 @@ def test_all_ones_partial_sum_matches_paper():
     assert abs((pos + neg) - float(total)) < 1e-12 * worst
 
 
+def test_abs_sum_bounds_and_closed_form():
+    """S_abs >= |perm| (triangle inequality); for the n x n all-ones matrix
+    (one row of multiplicity n, one column of multiplicity n) the addends are
+    C(n-1, j) |n - 2j|^n, so S_abs = 2^(1-n) sum_j C(n-1, j) |n-2j|^n; a single
+    column (K = 1) with one row gives |a|."""
+    g = S.rng(21)
+    for trial in range(15):
+        a, M, N = _random_mult_case(g, 3, 4, int(g.integers(1, 9)), 1400 + trial)
+        v, t = oracle.perm_mult(a, M, N)
+        assert oracle.perm_mult_abs(a, M, N) >= abs(v + t) * (1 - 1e-14)
+    for n in (3, 10, 25):
+        ref = sum(math.comb(n - 1, j) * abs(n - 2 * j) ** n for j in range(n)) / 2 ** (n - 1)
+        assert abs(oracle.perm_mult_abs(np.ones((1, 1)), [n], [n]) - ref) <= 1e-13 * ref
+    assert abs(oracle.perm_mult_abs(np.array([[0.6 - 0.8j]]), [1], [1]) - 1.0) < 1e-15
+
+
 # ---------------------------------------------------------------- minors
 def test_laplace_identity():
     g = S.rng(13)
