@@ -16,7 +16,7 @@ BUILD = os.path.join(PKG, "_build")
 LIB = os.path.join(PKG, "libbs.so")
 
 SOURCES = ["kern_walk_fp64.cu", "kern_walk_fp32.cu", "kern_pack.cu", "kern_sample.cu", "kern_peaks.cu",
-           "api.cpp"]
+           "api.cpp", "plan.cpp"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-fvisibility=hidden",
          "-I" + CSRC, "-I" + INCLUDE]
@@ -55,7 +55,7 @@ def build(force: bool = False, verbose: bool = False) -> str:
     def compile_one(src: str) -> str:
         obj = os.path.join(BUILD, src + ".o")
         cmd = [cc] + ARCH + FLAGS + ["-c", os.path.join(CSRC, src), "-o", obj]
-        if src == "api.cpp":
+        if src.endswith(".cpp"):
             cmd = [cc] + FLAGS + ["-x", "cu", "-c", os.path.join(CSRC, src), "-o", obj] + ARCH
         r = subprocess.run(cmd, capture_output=True, text=True)
         if r.returncode != 0:
