@@ -146,6 +146,26 @@ int bs_perm_batch_dev(bs_ctx* ctx, int count, const bs_c128* A_packed_dev, const
 int bs_laplace_minors(bs_ctx* ctx, const bs_c128* A, int rows, int cols, int ld, const int* row_mult,
                       const int* col_mult, bs_mode mode, bs_c128* minors);
 
+/* Allocation-free permanent, for callers that may not allocate device
+ * memory when they need a result: code running while a CUDA graph is being
+ * captured on its stream, hosts whose memory manager forbids allocations
+ * outside its own budget, real-time loops that must not enter the CUDA
+ * allocator.  Computes the same permanent as bs_perm (same kernels; FP64 or
+ * MIXED) without any device or host heap allocation: all device scratch is
+ * one file-scope __device__ array of 8 MiB that every GPU loading the library
+ * holds until the process exits.  The paper has no counterpart of this call.
+ *   A, row_mult, col_mult, out, out_lo: host memory as in bs_perm (no
+ *   context); stream: a cudaStream_t as void* (0 = legacy default stream),
+ *   synchronised before the call returns.
+ * Limit: the job's warp tasks must fit the fixed scratch (about 2.6e5 tasks,
+ * e.g. every permanent with up to 2^34 addends); larger jobs return
+ * BS_EINVAL with a message naming the limit.  The first call on a device looks
+ * up the array's device address; make that first call before any stream
+ * capture.  Calls share the array: calls that overlap on the GPU race and
+ * must be serialised by the caller. */
+int bs_perm_noalloc(const bs_c128* A, int rows, int cols, int ld, const int* row_mult, const int* col_mult,
+                    bs_mode mode, void* stream, bs_c128* out, bs_c128* out_lo);
+
 /* ------------------------------------------------------------------ */
 /* Clifford & Clifford sampling (Sec. 4)                               */
 /* ------------------------------------------------------------------ */

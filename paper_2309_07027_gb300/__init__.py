@@ -22,7 +22,7 @@ import os
 import numpy as np
 
 __all__ = ["BS_FP64", "BS_MIXED", "BsError", "Context", "library_path", "load", "debug_gray_walk",
-           "debug_plan", "MAX_N"]
+           "debug_plan", "perm_noalloc", "MAX_N"]
 
 BS_FP64 = 0
 BS_MIXED = 1
@@ -92,6 +92,7 @@ def load():
         "bs_debug_gray_walk": ([C.c_int, C.c_int, ip, C.c_uint64, C.c_int, ip, ip, C.POINTER(C.c_uint64)],
                                C.c_int),
         "bs_debug_plan": ([C.c_int, C.c_int, ip, ip, C.c_int, i64p], C.c_int),
+        "bs_perm_noalloc": ([vp, C.c_int, C.c_int, C.c_int, ip, ip, C.c_int, vp, vp, vp], C.c_int),
     }
     for name, (args, res) in sig.items():
         f = getattr(L, name)
@@ -311,6 +312,23 @@ class Context:
         _check(self._L.bs_sample_dev(self._p, C.c_void_p(u_dev.data_ptr()), mr, mc, ld, _ip(occ), int(n_samples),
                                      C.c_uint64(int(seed) & ((1 << 64) - 1)), int(m_detected), int(mode),
                                      C.c_void_p(out_dev.data_ptr())), self._p)
+
+
+# ------------------------------------------------------------------ allocation-free call
+def perm_noalloc(a, row_mult=None, col_mult=None, mode: int = BS_FP64, stream=0):
+    """bs_perm_noalloc: the permanent without any device allocation (for
+    callers that may not allocate, e.g. during a CUDA graph capture on their
+    stream).  ``stream``: a torch.cuda.Stream, a raw handle, or 0."""
+    L = load()
+    a = _c128(a)
+    R, K = a.shape
+    M = _i32(np.ones(R) if row_mult is None else row_mult, R)
+    N = _i32(np.ones(K) if col_mult is None else col_mult, K)
+    out = np.zeros(1, dtype=np.complex128)
+    handle = int(getattr(stream, "cuda_stream", stream) or 0)
+    _check(L.bs_perm_noalloc(a.ctypes.data, R, K, K, _ip(M), _ip(N), int(mode), C.c_void_p(handle),
+                             out.ctypes.data, None))
+    return complex(out[0])
 
 
 # ------------------------------------------------------------------ host-only helpers

@@ -1,0 +1,61 @@
+"""bs_perm_noalloc: the permanent for callers that may not allocate device
+memory (e.g. while a CUDA graph is being captured on their stream).  Its
+scratch is one fixed __device__ array shared by every call, so this test
+calls it twice in a row, with the larger problem first, and compares each
+result with the allocating entry point bs_perm under the parity tolerance
+of the GPU tests.  It lives in a file of its own that pytest collects last
+and must pass both alone in a fresh process and after the other tests."""
+import ctypes
+
+import numpy as np
+import pytest
+
+import synthetic as S
+
+pytestmark = pytest.mark.gpu
+
+TOL = {0: 1e-10, 1: 1e-6}
+
+
+def scale(a, M, N):
+    norms = np.sqrt((np.abs(a) ** 2 * np.asarray(M)[:, None]).sum(axis=0))
+    return float(np.prod(norms ** np.asarray(N)))
+
+
+def noalloc_c_abi(lib, a, M, N, mode):
+    """Call bs_perm_noalloc directly through the C ABI (ctypes)."""
+    a = np.ascontiguousarray(a, dtype=np.complex128)
+    R, K = a.shape
+    M = np.ascontiguousarray(M, dtype=np.int32)
+    N = np.ascontiguousarray(N, dtype=np.int32)
+    out = np.zeros(1, dtype=np.complex128)
+    lo = np.zeros(1, dtype=np.complex128)
+    fn = lib.bs_perm_noalloc
+    ip = ctypes.POINTER(ctypes.c_int)
+    fn.argtypes = [ctypes.c_void_p, ctypes.c_int, ctypes.c_int, ctypes.c_int, ip, ip, ctypes.c_int,
+                   ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]
+    fn.restype = ctypes.c_int
+    rc = fn(a.ctypes.data, R, K, K, M.ctypes.data_as(ip), N.ctypes.data_as(ip), int(mode), None,
+            out.ctypes.data, lo.ctypes.data)
+    assert rc == 0, rc
+    return complex(out[0])
+
+
+@pytest.mark.parametrize("mode", [0, 1])
+def test_noalloc_matches_bs_perm_on_two_calls(ctx, bslib, mode):
+    lib = ctypes.CDLL(bslib.library_path())
+    u = S.haar_unitary(40, 11)
+    big = (u[:22, :22], np.ones(22, np.int32), np.ones(22, np.int32))      # 2^21 addends, many tasks
+    a1, M1, N1, _, _ = S.config_single(seed=1)                              # 576 addends, one task
+    for a, M, N in (big, (a1, M1, N1)):
+        ref = ctx.perm(a, M, N, mode=mode)
+        got = noalloc_c_abi(lib, a, M, N, mode)
+        assert abs(got - ref) <= TOL[mode] * scale(a, M, N), (got, ref)
+
+
+def test_noalloc_rejects_jobs_beyond_its_scratch(bslib):
+    u = S.haar_unitary(48, 12)
+    a = u[:44, :44]
+    with pytest.raises(bslib.BsError) as e:
+        bslib.perm_noalloc(a, np.ones(44, np.int32), np.ones(44, np.int32))
+    assert e.value.code == bslib.BS_EINVAL and "scratch" in str(e.value)
