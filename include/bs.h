@@ -96,6 +96,14 @@ int bs_ctx_set_deadline(bs_ctx* ctx, double seconds);
 int bs_ctx_set_chunk_log2(bs_ctx* ctx, bs_mode mode, int log2_chunk_max);
 int bs_ctx_get_chunk_log2(const bs_ctx* ctx, bs_mode mode);
 
+/* Autotuner: times a synthetic problem of the given kind (0 permanent,
+ * 1 minors), mode and K product columns (4..48) with chunk-length caps
+ * 2^8, 2^10, 2^12, 2^14 (the chunk length is the re-seed interval of the
+ * column sums and sets how many warps share one job) and keeps the fastest
+ * for the mode in this context.  *best_log2 (nullable) receives the cap,
+ * *best_addends_per_s (nullable) the measured rate. */
+int bs_tune(bs_ctx* ctx, bs_mode mode, int kind, int K, int* best_log2, double* best_addends_per_s);
+
 /* ------------------------------------------------------------------ */
 /* Permanents                                                          */
 /* ------------------------------------------------------------------ */
@@ -201,6 +209,48 @@ int bs_sample_dev(bs_ctx* ctx, const bs_c128* U_dev, int m_rows, int m_cols, int
                   int n_samples, uint64_t seed, int m_detected, bs_mode mode, int* out_dev);
 
 /* ------------------------------------------------------------------ */
+/* Serving: continuous batching of requests from many clients          */
+/* ------------------------------------------------------------------ */
+
+/* A server owns one device memory block of mem_budget_bytes (the admission
+ * budget), a stream and a scheduler thread.  Requests (permanents or Laplace
+ * minors, as bs_perm / bs_laplace_minors) are admitted in arrival order while
+ * one of max_active slots is free and their device memory fits the budget;
+ * every scheduling tick walks a share of tick_tasks warp tasks of every
+ * resident request in one launch per kernel group, so requests arriving
+ * while others run are admitted at the next tick and their work overlaps on
+ * the device (iteration-level scheduling).  Results are bit-identical to
+ * running each request alone.  mode: BS_FP64 or BS_MIXED (per-request
+ * precision rule as for bs_perm).  Errors: BS_EINVAL, BS_ENODEV, BS_ENOMEM. */
+typedef struct bs_server bs_server;
+int bs_server_create(bs_server** out, int device, size_t mem_budget_bytes, int max_active, int tick_tasks,
+                     bs_mode mode);
+/* Stops the scheduler (after its current tick) and frees everything; pending
+ * requests are dropped. */
+void bs_server_destroy(bs_server* server);
+
+/* Submits a request (kind 0: permanent, 1: minors; host arrays, copied
+ * before returning).  Returns a ticket >= 0, or a negative BS_E* code. */
+int64_t bs_server_submit(bs_server* server, int kind, const bs_c128* A, int rows, int cols, int ld,
+                         const int* row_mult, const int* col_mult);
+
+/* bs_server_poll: 1 and the result (1 value, or cols minors) when the request
+ * is done, 0 while pending, negative on error.  bs_server_wait blocks until
+ * done and returns BS_OK.  Either releases the ticket once it returns a
+ * result.  latency_s (nullable): submit-to-completion time. */
+int bs_server_poll(bs_server* server, int64_t ticket, bs_c128* out, int out_len, double* latency_s);
+int bs_server_wait(bs_server* server, int64_t ticket, bs_c128* out, int out_len, double* latency_s);
+
+typedef struct {
+    uint64_t submitted, completed, ticks, walk_launches;
+    double busy_s;            /* time spent in ticks */
+    double p50_ms, p99_ms, max_ms;  /* submit-to-completion latency of completed requests */
+    int max_resident;         /* largest number of requests resident at once */
+    size_t mem_peak_bytes;    /* peak bytes of the budget in use */
+} bs_server_stats;
+int bs_server_get_stats(bs_server* server, bs_server_stats* out);
+
+/* ------------------------------------------------------------------ */
 /* Measurement and diagnostics                                         */
 /* ------------------------------------------------------------------ */
 
@@ -212,6 +262,12 @@ typedef struct {
     double walk_ms[2];          /* summed walk-kernel time (profiling on) */
     uint64_t timed_launches[2]; /* walk launches included in walk_ms */
 } bs_stats;
+
+/* Sampling replays its per-step kernel sequence from a captured CUDA graph
+ * (re-captured when shapes, buffers, deadline or stream change) when on != 0
+ * (the default); 0 launches every kernel directly.  Profiling always runs
+ * without the graph so that every walk launch is timed. */
+int bs_ctx_set_graphs(bs_ctx* ctx, int on);
 
 /* Record CUDA events around every walk launch (on its stream) when on != 0;
  * bs_ctx_get_stats() then reports their summed durations. */

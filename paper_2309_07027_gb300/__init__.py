@@ -21,7 +21,7 @@ import os
 
 import numpy as np
 
-__all__ = ["BS_FP64", "BS_MIXED", "BsError", "Context", "library_path", "load", "debug_gray_walk",
+__all__ = ["BS_FP64", "BS_MIXED", "BsError", "Context", "Server", "library_path", "load", "debug_gray_walk",
            "debug_plan", "perm_noalloc", "MAX_N"]
 
 BS_FP64 = 0
@@ -51,6 +51,13 @@ class _Stats(C.Structure):
                 ("addend_flops", C.c_uint64 * 2), ("walk_ms", C.c_double * 2), ("timed_launches", C.c_uint64 * 2)]
 
 
+class _ServerStats(C.Structure):
+    _fields_ = [("submitted", C.c_uint64), ("completed", C.c_uint64), ("ticks", C.c_uint64),
+                ("walk_launches", C.c_uint64), ("busy_s", C.c_double), ("p50_ms", C.c_double),
+                ("p99_ms", C.c_double), ("max_ms", C.c_double), ("max_resident", C.c_int),
+                ("mem_peak_bytes", C.c_size_t)]
+
+
 _lib = None
 
 
@@ -75,6 +82,7 @@ def load():
         "bs_ctx_set_deadline": ([vp, C.c_double], C.c_int),
         "bs_ctx_set_chunk_log2": ([vp, C.c_int, C.c_int], C.c_int),
         "bs_ctx_get_chunk_log2": ([vp, C.c_int], C.c_int),
+        "bs_tune": ([vp, C.c_int, C.c_int, C.c_int, ip, dp], C.c_int),
         "bs_perm": ([vp, vp, C.c_int, C.c_int, C.c_int, ip, ip, C.c_int, vp, vp], C.c_int),
         "bs_perm_batch": ([vp, C.c_int, vp, i64p, ip, ip, ip, i64p, i64p, C.c_int, vp], C.c_int),
         "bs_perm_batch_dev": ([vp, C.c_int, vp, i64p, ip, ip, ip, i64p, i64p, C.c_int, vp], C.c_int),
@@ -85,6 +93,7 @@ def load():
         "bs_sample_dev": ([vp, vp, C.c_int, C.c_int, C.c_int, ip, C.c_int, C.c_uint64, C.c_int, C.c_int, vp],
                           C.c_int),
         "bs_ctx_set_profiling": ([vp, C.c_int], C.c_int),
+        "bs_ctx_set_graphs": ([vp, C.c_int], C.c_int),
         "bs_ctx_get_stats": ([vp, C.POINTER(_Stats)], C.c_int),
         "bs_ctx_get_walk_times": ([vp, dp, C.c_int], C.c_int),
         "bs_ctx_reset_stats": ([vp], C.c_int),
@@ -93,6 +102,12 @@ def load():
                                C.c_int),
         "bs_debug_plan": ([C.c_int, C.c_int, ip, ip, C.c_int, i64p], C.c_int),
         "bs_perm_noalloc": ([vp, C.c_int, C.c_int, C.c_int, ip, ip, C.c_int, vp, vp, vp], C.c_int),
+        "bs_server_create": ([C.POINTER(C.c_void_p), C.c_int, C.c_size_t, C.c_int, C.c_int, C.c_int], C.c_int),
+        "bs_server_destroy": ([vp], None),
+        "bs_server_submit": ([vp, C.c_int, vp, C.c_int, C.c_int, C.c_int, ip, ip], C.c_int64),
+        "bs_server_poll": ([vp, C.c_int64, vp, C.c_int, dp], C.c_int),
+        "bs_server_wait": ([vp, C.c_int64, vp, C.c_int, dp], C.c_int),
+        "bs_server_get_stats": ([vp, C.POINTER(_ServerStats)], C.c_int),
     }
     for name, (args, res) in sig.items():
         f = getattr(L, name)
@@ -182,6 +197,17 @@ class Context:
 
     def chunk_log2(self, mode: int) -> int:
         return int(self._L.bs_ctx_get_chunk_log2(self._p, int(mode)))
+
+    def set_graphs(self, on: bool):
+        """Replay the sampler's step loop from a captured CUDA graph (default)."""
+        _check(self._L.bs_ctx_set_graphs(self._p, 1 if on else 0), self._p)
+
+    def tune(self, mode: int, kind: int = 1, K: int = 28):
+        """Autotune the chunk-length cap for ``mode``; returns (log2, addends/s)."""
+        b = C.c_int()
+        r = C.c_double()
+        _check(self._L.bs_tune(self._p, int(mode), int(kind), int(K), C.byref(b), C.byref(r)), self._p)
+        return b.value, r.value
 
     def set_profiling(self, on: bool):
         _check(self._L.bs_ctx_set_profiling(self._p, 1 if on else 0), self._p)
@@ -312,6 +338,72 @@ class Context:
         _check(self._L.bs_sample_dev(self._p, C.c_void_p(u_dev.data_ptr()), mr, mc, ld, _ip(occ), int(n_samples),
                                      C.c_uint64(int(seed) & ((1 << 64) - 1)), int(m_detected), int(mode),
                                      C.c_void_p(out_dev.data_ptr())), self._p)
+
+
+# ------------------------------------------------------------------ serving
+class Server:
+    """Continuous-batching server (bs_server_*): requests from many client
+    threads are admitted by slots and device memory and walked together,
+    tick by tick, on one stream."""
+
+    def __init__(self, device=0, mem_budget_bytes=1 << 30, max_active=64, tick_tasks=8192, mode=BS_MIXED):
+        L = load()
+        p = C.c_void_p()
+        _check(L.bs_server_create(C.byref(p), int(device), int(mem_budget_bytes), int(max_active),
+                                  int(tick_tasks), int(mode)))
+        self._p = p
+        self._L = L
+
+    def close(self):
+        if getattr(self, "_p", None):
+            self._L.bs_server_destroy(self._p)
+            self._p = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def submit(self, kind, a, row_mult, col_mult):
+        """kind 0: permanent, 1: Laplace minors.  Returns a ticket."""
+        a = _c128(a)
+        R, K = a.shape
+        M = _i32(row_mult, R)
+        N = _i32(col_mult, K)
+        t = self._L.bs_server_submit(self._p, int(kind), a.ctypes.data, R, K, K, _ip(M), _ip(N))
+        if t < 0:
+            _check(int(t))
+        return int(t), (1 if kind == 0 else K)
+
+    def wait(self, ticket):
+        """Blocks; returns (result array, latency seconds)."""
+        t, n = ticket
+        out = np.zeros(max(n, 1), dtype=np.complex128)
+        lat = C.c_double()
+        _check(self._L.bs_server_wait(self._p, t, out.ctypes.data, len(out), C.byref(lat)))
+        return out[:n], lat.value
+
+    def poll(self, ticket):
+        """(done, result or None, latency or None)."""
+        t, n = ticket
+        out = np.zeros(max(n, 1), dtype=np.complex128)
+        lat = C.c_double()
+        rc = self._L.bs_server_poll(self._p, t, out.ctypes.data, len(out), C.byref(lat))
+        if rc < 0:
+            _check(rc)
+        return (True, out[:n], lat.value) if rc == 1 else (False, None, None)
+
+    def stats(self):
+        s = _ServerStats()
+        _check(self._L.bs_server_get_stats(self._p, C.byref(s)))
+        return {f: getattr(s, f) for f, _ in _ServerStats._fields_}
 
 
 # ------------------------------------------------------------------ allocation-free call

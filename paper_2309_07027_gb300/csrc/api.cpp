@@ -72,7 +72,13 @@ struct bs_ctx {
     cudaStream_t stream = nullptr;
     size_t budget = 0, used = 0;
     DevBuf src, jobs, meta, data64, data32, partials, out, out_lo, ctl;
-    DevBuf cc_inputs, cc_cols, cc_rows, cc_jobs, cc_meta, cc_data, cc_partials, cc_minors, cc_out, cc_U, cc_lists;
+    DevBuf cc_inputs, cc_cols, cc_rows, cc_jobs, cc_meta, cc_data, cc_partials, cc_minors, cc_out, cc_U, cc_lists,
+        cc_args;
+    // captured sampler step loop (one batch), replayed while its key matches
+    bool use_graphs = true;
+    cudaGraphExec_t cc_exec = nullptr;
+    std::vector<uint64_t> cc_key;
+    uint64_t cc_graph_kernels = 0;
     void* h_stage = nullptr;
     size_t h_stage_n = 0;
     cudaEvent_t stage_ev = nullptr;
@@ -197,7 +203,7 @@ int run_jobs(bs_ctx* c, std::vector<JobIn>& ins, const double2* d_src, bs_mode m
         r.kind = in.p->kind;
         r.bucket = (in.p->K + 3) >> 2;
         r.cpt = (r.fp32 && r.kind == BS_KIND_MINORS) ? 16 : 32;
-        r.log2L = bs_choose_log2L(in.p->C, r.cpt, c->log2max[r.fp32]);
+        r.log2L = bs_choose_log2L(in.p->C, r.cpt, c->log2max[r.fp32], BS_TARGET_TASKS_SINGLE);
         uint64_t per = (uint64_t)r.cpt << r.log2L;
         r.ntasks = (uint32_t)((in.p->C + per - 1) / per);
         r.ncols = r.kind == BS_KIND_PERM ? 1 : in.p->K;
@@ -256,6 +262,8 @@ int run_jobs(bs_ctx* c, std::vector<JobIn>& ins, const double2* d_src, bs_mode m
             meta.insert(meta.end(), p.col_src, p.col_src + p.K);
             meta.insert(meta.end(), (size_t)p.K, 0);
             meta.push_back(p.pinned_src);
+            meta.push_back(0);                                           // pad to 8 bytes
+            meta.insert(meta.end(), (size_t)2 * (p.nrows + p.n), 0);     // binomial table (pack kernel)
             data_off[r.fp32] += (int64_t)(1 + p.nrows) * BS_ROW_STRIDE(p.K);
             part_off += (int64_t)r.ntasks * r.ncols;
             tb += r.ntasks;
@@ -279,7 +287,10 @@ int run_jobs(bs_ctx* c, std::vector<JobIn>& ins, const double2* d_src, bs_mode m
     BS_CUDA(cudaMemcpyAsync(c->jobs.p, h, jobs_b, cudaMemcpyHostToDevice, c->stream));
     BS_CUDA(cudaMemcpyAsync(c->meta.p, h + jobs_b, meta_b, cudaMemcpyHostToDevice, c->stream));
     BS_CUDA(cudaEventRecord(c->stage_ev, c->stream));
-    BS_CUDA(cudaMemsetAsync(c->ctl.p, 0, kCtlSlots * 8, c->stream));
+    // counters, totals and status; the statistics slots are cleared only by
+    // bs_ctx_reset_stats
+    BS_CUDA(cudaMemsetAsync(c->ctl.p, 0, kCtlStats * 8, c->stream));
+    BS_CUDA(cudaMemsetAsync(static_cast<unsigned long long*>(c->ctl.p) + kCtlListLen, 0, (kCtlSlots - kCtlListLen) * 8, c->stream));
     const bs_job* djobs = static_cast<const bs_job*>(c->jobs.p);
     // FP64 jobs come first (sorted by precision), then FP32 jobs
     size_t n64 = 0;
@@ -395,6 +406,62 @@ int single_job(bs_ctx* c, const bs_c128* A, int rows, int cols, int ld, const in
 }
 
 // ------------------------------------------------------------------ sampler
+// Walk launches per sampler batch (steps 2..n; two kernels per step in MIXED).
+uint64_t kernels_walks(int n, bool mixed) { return n >= 2 ? (uint64_t)(n - 1) * (mixed ? 2 : 1) : 0; }
+
+// Enqueues one batch of the Clifford & Clifford loop on c->stream (eagerly or
+// into a stream capture): init, then for k = 1..n plan / scan / walk /
+// reduce (k >= 2) and draw, then the occupation counts.  Kernels read their
+// arguments from `da` (device); `a` gives launch shapes.  *kernels counts
+// the kernels enqueued.
+int enqueue_sampler_batch(bs_ctx* c, const bs::CcArgs& a, const bs::CcArgs* da, bool mixed, uint64_t* kernels) {
+    unsigned long long* ctl = static_cast<unsigned long long*>(c->ctl.p);
+    int rc;
+    cudaError_t e = bs::launch_cc_init(a, da, c->stream);
+    if (e != cudaSuccess) return fail(BS_ECUDA, "sampler init: %s", cudaGetErrorString(e));
+    ++*kernels;
+    for (int k = 1; k <= a.n; ++k) {
+        if (k >= 2) {
+            if ((e = bs::launch_cc_plan(a, da, k, c->stream)) != cudaSuccess)
+                return fail(BS_ECUDA, "sampler plan: %s", cudaGetErrorString(e));
+            if ((e = bs::launch_cc_scan(a, da, k, c->stream)) != cudaSuccess)
+                return fail(BS_ECUDA, "sampler scan: %s", cudaGetErrorString(e));
+            *kernels += 2;
+            for (int prec = mixed ? 1 : 0; prec >= 0; --prec) {
+                bs::WalkArgs w;
+                std::memset(&w, 0, sizeof(w));
+                w.jobs = a.jobs;
+                w.njobs = a.S;
+                w.job_list = a.lists + prec * a.S;
+                w.njobs_dev = a.list_len + prec;
+                w.data = a.data;
+                w.meta = a.meta;
+                w.partials = a.partials;
+                w.total_tasks = 0;
+                w.total_dev = a.total + prec;
+                w.counter = a.counter + prec;
+                w.status = reinterpret_cast<int*>(ctl + kCtlStatus);
+                w.deadline_rel_ns = c->deadline_s > 0 ? (unsigned long long)(c->deadline_s * 1e9) : 0ull;
+                w.max_K = k;
+                if ((rc = launch_walk(c, w, prec == 1, BS_KIND_MINORS))) return rc;
+                c->stats.kernel_launches--;  // the caller counts every kernel
+                ++*kernels;
+            }
+            if ((e = bs::launch_reduce(a.jobs, a.S, a.partials, a.meta, a.minors, nullptr, k, c->stream)) !=
+                cudaSuccess)
+                return fail(BS_ECUDA, "sampler reduce: %s", cudaGetErrorString(e));
+            ++*kernels;
+        }
+        if ((e = bs::launch_cc_draw(a, da, k, c->stream)) != cudaSuccess)
+            return fail(BS_ECUDA, "sampler draw: %s", cudaGetErrorString(e));
+        ++*kernels;
+    }
+    if ((e = bs::launch_cc_counts(a, da, c->stream)) != cudaSuccess)
+        return fail(BS_ECUDA, "sampler counts: %s", cudaGetErrorString(e));
+    ++*kernels;
+    return BS_OK;
+}
+
 int sample_dev(bs_ctx* c, const double2* dU, int m_rows, int m_cols, int ld, const int* occ, int n_samples,
                uint64_t seed, int m_det, bs_mode mode, int* dout) {
     if (m_rows <= 0 || m_cols <= 0) return fail(BS_EINVAL, "bad interferometer size %d x %d", m_rows, m_cols);
@@ -418,12 +485,14 @@ int sample_dev(bs_ctx* c, const double2* dU, int m_rows, int m_cols, int ld, con
     const bool mixed = mode == BS_MIXED;
     // worst-case tasks of one chain at the last step (C <= 2^(n-2)), over
     // both kernels a chain may be given
+    // (bs_choose_log2L gives at most 2 x target tasks unless the chunk
+    // length is capped, and then at most C / (cpt 2^log2max) + 1)
     uint64_t cmax = n >= 2 ? (1ull << (n - 2)) : 1ull;
-    uint64_t tasks_stride = 8193;
+    uint64_t tasks_stride = 2 * BS_TARGET_TASKS_MANY + 1;
     tasks_stride = std::max<uint64_t>(tasks_stride, cmax / (32ull << c->log2max[0]) + 2);
     if (mixed) tasks_stride = std::max<uint64_t>(tasks_stride, cmax / (16ull << c->log2max[1]) + 2);
-    // a step-k job has <= k - 1 digit rows and K = k <= n columns
-    const int64_t meta_stride = 4 * n + 1, data_stride = (int64_t)n * BS_ROW_STRIDE(n);
+    // a step-k job has <= k - 1 digit rows, K = k <= n columns, n' = k - 1
+    const int64_t meta_stride = BS_META_SIZE(n, n, n), data_stride = (int64_t)n * BS_ROW_STRIDE(n);
     // chains per pass: bounded by the budget (or 2 GiB of partials per pass)
     const size_t per_chain = (size_t)tasks_stride * n * sizeof(bs_zdd) + (size_t)data_stride * 16 +
                              meta_stride * 4 + sizeof(bs_job) + (size_t)n * (8 + 16) + 8 + 64;
@@ -450,8 +519,13 @@ int sample_dev(bs_ctx* c, const double2* dU, int m_rows, int m_cols, int ld, con
     std::memcpy(h, inputs.data(), n * sizeof(int));
     BS_CUDA(cudaMemcpyAsync(c->cc_inputs.p, h, n * sizeof(int), cudaMemcpyHostToDevice, c->stream));
     BS_CUDA(cudaEventRecord(c->stage_ev, c->stream));
-    BS_CUDA(cudaMemsetAsync(c->ctl.p, 0, kCtlSlots * 8, c->stream));
+    // counters, totals and status; the statistics slots are cleared only by
+    // bs_ctx_reset_stats
+    BS_CUDA(cudaMemsetAsync(c->ctl.p, 0, kCtlStats * 8, c->stream));
+    BS_CUDA(cudaMemsetAsync(static_cast<unsigned long long*>(c->ctl.p) + kCtlListLen, 0, (kCtlSlots - kCtlListLen) * 8, c->stream));
     unsigned long long* ctl = static_cast<unsigned long long*>(c->ctl.p);
+    if ((rc = ensure(c, c->cc_args, sizeof(bs::CcArgs)))) return rc;
+    bs::CcArgs* da = static_cast<bs::CcArgs*>(c->cc_args.p);
     for (int base = 0; base < n_samples; base += S_max) {
         bs::CcArgs a;
         std::memset(&a, 0, sizeof(a));
@@ -483,45 +557,61 @@ int sample_dev(bs_ctx* c, const double2* dU, int m_rows, int m_cols, int ld, con
         a.mixed = mixed ? 1 : 0;
         a.log2max64 = c->log2max[0];
         a.log2max32 = c->log2max[1];
-        cudaError_t e = bs::launch_cc_init(a, c->stream);
-        if (e != cudaSuccess) return fail(BS_ECUDA, "sampler init: %s", cudaGetErrorString(e));
-        c->stats.kernel_launches++;
-        for (int k = 1; k <= n; ++k) {
-            if (k >= 2) {
-                if ((e = bs::launch_cc_plan(a, k, c->stream)) != cudaSuccess)
-                    return fail(BS_ECUDA, "sampler plan: %s", cudaGetErrorString(e));
-                if ((e = bs::launch_cc_scan(a, k, c->stream)) != cudaSuccess)
-                    return fail(BS_ECUDA, "sampler scan: %s", cudaGetErrorString(e));
-                for (int prec = mixed ? 1 : 0; prec >= 0; --prec) {
-                    bs::WalkArgs w;
-                    std::memset(&w, 0, sizeof(w));
-                    w.jobs = a.jobs;
-                    w.njobs = a.S;
-                    w.job_list = a.lists + prec * a.S;
-                    w.njobs_dev = a.list_len + prec;
-                    w.data = a.data;
-                    w.meta = a.meta;
-                    w.partials = a.partials;
-                    w.total_tasks = 0;
-                    w.total_dev = a.total + prec;
-                    w.counter = a.counter + prec;
-                    w.status = reinterpret_cast<int*>(ctl + kCtlStatus);
-                    w.deadline_rel_ns = c->deadline_s > 0 ? (unsigned long long)(c->deadline_s * 1e9) : 0ull;
-                    w.max_K = k;
-                    if ((rc = launch_walk(c, w, prec == 1, BS_KIND_MINORS))) return rc;
-                }
-                if ((e = bs::launch_reduce(a.jobs, a.S, a.partials, a.meta, a.minors, nullptr, k, c->stream)) !=
-                    cudaSuccess)
-                    return fail(BS_ECUDA, "sampler reduce: %s", cudaGetErrorString(e));
-                c->stats.kernel_launches += 3;
-            }
-            if ((e = bs::launch_cc_draw(a, k, c->stream)) != cudaSuccess)
-                return fail(BS_ECUDA, "sampler draw: %s", cudaGetErrorString(e));
-            c->stats.kernel_launches++;
+        // the kernels read the arguments from device memory (pageable copy:
+        // staged before cudaMemcpyAsync returns, so `a` may go out of scope)
+        BS_CUDA(cudaMemcpyAsync(da, &a, sizeof(a), cudaMemcpyHostToDevice, c->stream));
+        // eager launches when graphs are off, when profiling (every walk is
+        // timed), on the legacy default stream (it cannot be captured), and
+        // when the caller is already capturing this stream (the caller's
+        // graph then records these launches)
+        cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+        if (c->stream != nullptr) BS_CUDA(cudaStreamIsCapturing(c->stream, &cap));
+        if (!c->use_graphs || c->profiling || c->stream == nullptr || c->stream == cudaStreamPerThread ||
+            cap != cudaStreamCaptureStatusNone) {
+            uint64_t kernels = 0;
+            if ((rc = enqueue_sampler_batch(c, a, da, mixed, &kernels))) return rc;
+            c->stats.kernel_launches += kernels;
+            continue;
         }
-        if ((e = bs::launch_cc_counts(a, c->stream)) != cudaSuccess)
-            return fail(BS_ECUDA, "sampler counts: %s", cudaGetErrorString(e));
-        c->stats.kernel_launches++;
+        // replay the captured step loop while shapes and buffers are unchanged
+        const uint64_t dl = c->deadline_s > 0 ? (uint64_t)(c->deadline_s * 1e9) : 0;
+        std::vector<uint64_t> key = {(uint64_t)a.S, (uint64_t)n, (uint64_t)m_rows, (uint64_t)m_det, (uint64_t)ld,
+                                     (uint64_t)a.mixed, (uint64_t)a.log2max64, (uint64_t)a.log2max32,
+                                     (uint64_t)(uintptr_t)dU, (uint64_t)(uintptr_t)c->cc_cols.p,
+                                     (uint64_t)(uintptr_t)c->cc_rows.p, (uint64_t)(uintptr_t)c->cc_jobs.p,
+                                     (uint64_t)(uintptr_t)c->cc_meta.p, (uint64_t)(uintptr_t)c->cc_data.p,
+                                     (uint64_t)(uintptr_t)c->cc_partials.p, (uint64_t)(uintptr_t)c->cc_minors.p,
+                                     (uint64_t)(uintptr_t)c->cc_lists.p, (uint64_t)(uintptr_t)c->ctl.p,
+                                     (uint64_t)(uintptr_t)da, tasks_stride, dl, (uint64_t)(uintptr_t)c->stream};
+        if (!c->cc_exec || key != c->cc_key) {
+            if (c->cc_exec) {
+                cudaGraphExecDestroy(c->cc_exec);
+                c->cc_exec = nullptr;
+            }
+            BS_CUDA(cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal));
+            uint64_t kernels = 0;
+            const uint64_t walks_before = c->stats.walk_launches;
+            rc = enqueue_sampler_batch(c, a, da, mixed, &kernels);
+            c->stats.walk_launches = walks_before;  // counted per replay below
+            cudaGraph_t g = nullptr;
+            cudaError_t e = cudaStreamEndCapture(c->stream, &g);
+            if (rc) {
+                if (g) cudaGraphDestroy(g);
+                return rc;
+            }
+            if (e != cudaSuccess) return fail(BS_ECUDA, "sampler graph capture: %s", cudaGetErrorString(e));
+            e = cudaGraphInstantiate(&c->cc_exec, g, 0);
+            cudaGraphDestroy(g);
+            if (e != cudaSuccess) {
+                c->cc_exec = nullptr;
+                return fail(BS_ECUDA, "sampler graph instantiate: %s", cudaGetErrorString(e));
+            }
+            c->cc_key = key;
+            c->cc_graph_kernels = kernels;
+        }
+        BS_CUDA(cudaGraphLaunch(c->cc_exec, c->stream));
+        c->stats.kernel_launches += c->cc_graph_kernels;
+        c->stats.walk_launches += kernels_walks(n, mixed);
     }
     return BS_OK;
 }
@@ -560,6 +650,12 @@ int bs_ctx_create(bs_ctx** out, int device, size_t mem_budget_bytes) {
         return fail(BS_ECUDA, "context setup: %s", cudaGetErrorString(e));
     }
     c->stream = c->own;
+    // control words (task counters, status, statistics) start at zero
+    if (ensure(c, c->ctl, kCtlSlots * 8) != BS_OK || cudaMemset(c->ctl.p, 0, kCtlSlots * 8) != cudaSuccess) {
+        cudaGetLastError();
+        bs_ctx_destroy(c);
+        return fail(BS_ENOMEM, "could not allocate the control block");
+    }
     *out = c;
     return BS_OK;
 }
@@ -575,7 +671,8 @@ void bs_ctx_destroy(bs_ctx* c) {
     DevBuf* bufs[] = {&c->src,       &c->jobs,     &c->meta,     &c->data64,  &c->data32,      &c->partials,
                       &c->out,       &c->out_lo,   &c->ctl,      &c->cc_inputs, &c->cc_cols,   &c->cc_rows,
                       &c->cc_jobs,   &c->cc_meta,  &c->cc_data,  &c->cc_partials, &c->cc_minors, &c->cc_out,
-                      &c->cc_U, &c->cc_lists};
+                      &c->cc_U, &c->cc_lists, &c->cc_args};
+    if (c->cc_exec) cudaGraphExecDestroy(c->cc_exec);
     for (DevBuf* b : bufs) release(c, *b);
     if (c->h_stage) cudaFreeHost(c->h_stage);
     if (c->stage_ev) cudaEventDestroy(c->stage_ev);
@@ -803,6 +900,13 @@ int bs_sample(bs_ctx* c, const bs_c128* U, int m, const int* input_occupation, i
     return bs_sample_ex(c, U, m, m, m, input_occupation, n_samples, seed, m, mode, out);
 }
 
+int bs_ctx_set_graphs(bs_ctx* c, int on) {
+    if (!ok_ctx(c)) return BS_EINVAL;
+    std::lock_guard<std::mutex> lk(c->mu);
+    c->use_graphs = on != 0;
+    return BS_OK;
+}
+
 int bs_ctx_set_profiling(bs_ctx* c, int on) {
     if (!ok_ctx(c)) return BS_EINVAL;
     c->profiling = on != 0;
@@ -876,6 +980,69 @@ int bs_measure_fma_rates(bs_ctx* c, double* fp64, double* fp32) {
     return BS_OK;
 }
 
+int bs_tune(bs_ctx* c, bs_mode mode, int kind, int K, int* best_log2, double* best_addends_per_s) {
+    if (!ok_ctx(c)) return BS_EINVAL;
+    if (mode != BS_FP64 && mode != BS_MIXED) return fail(BS_EINVAL, "unknown mode %d", (int)mode);
+    if (kind != 0 && kind != 1) return fail(BS_EINVAL, "kind must be 0 (permanent) or 1 (minors)");
+    if (K < 4 || K > BS_MAX_COLS) return fail(BS_EINVAL, "K must be in [4, %d]", BS_MAX_COLS);
+    // synthetic problem: K product columns, up to 25 distinct rows (at most
+    // 2^24 addends), the remaining photons on the first rows (multiplicity 2)
+    const int n = kind == 0 ? K : K - 1;
+    const int R = std::min(n, 25);
+    std::vector<bs_c128> A((size_t)R * K);
+    uint64_t x = 0x9E3779B97F4A7C15ull ^ (uint64_t)K;
+    for (auto& z : A) {
+        x ^= x << 13; x ^= x >> 7; x ^= x << 17;
+        z.re = ((double)(x >> 11) * 0x1.0p-53 - 0.5) / std::sqrt((double)K);
+        x ^= x << 13; x ^= x >> 7; x ^= x << 17;
+        z.im = ((double)(x >> 11) * 0x1.0p-53 - 0.5) / std::sqrt((double)K);
+    }
+    std::vector<int> M(R, 1), N(K, 1);
+    for (int extra = n - R, r = 0; extra > 0; --extra, ++r) M[r % R] += 1;
+    const int saved = c->log2max[mode == BS_MIXED ? 1 : 0];
+    const bool prof = c->profiling;
+    c->profiling = true;
+    double best_ms = 1e300;
+    int best = saved;
+    uint64_t C = 0;
+    for (int cand = 8; cand <= 14; cand += 2) {
+        c->log2max[mode == BS_MIXED ? 1 : 0] = cand;
+        IntPlan p;
+        std::vector<double2> hi, lo;
+        double ms = 1e300;
+        for (int rep = 0; rep < 2; ++rep) {
+            std::vector<double> times;
+            int rc = single_job(c, A.data(), R, K, K, M.data(), N.data(), kind == 0 ? BS_KIND_PERM : BS_KIND_MINORS,
+                                mode, p, hi, lo);
+            if (rc) {
+                c->log2max[mode == BS_MIXED ? 1 : 0] = saved;
+                c->profiling = prof;
+                return rc;
+            }
+            double t = 0;
+            for (auto& e : c->timed) {
+                float f = 0.f;
+                cudaEventElapsedTime(&f, e.e0, e.e1);
+                t += f;
+                cudaEventDestroy(e.e0);
+                cudaEventDestroy(e.e1);
+            }
+            c->timed.clear();
+            if (rep == 1) ms = t;
+        }
+        C = p.C;
+        if (ms < best_ms) {
+            best_ms = ms;
+            best = cand;
+        }
+    }
+    c->log2max[mode == BS_MIXED ? 1 : 0] = best;
+    c->profiling = prof;
+    if (best_log2) *best_log2 = best;
+    if (best_addends_per_s) *best_addends_per_s = (double)C / (best_ms * 1e-3);
+    return BS_OK;
+}
+
 int bs_debug_gray_walk(int ndigits, int nbin, const int* radix, uint64_t start, int steps, int* deltas, int* moved,
                        uint64_t* weights) {
     if (ndigits < 0 || ndigits > BS_MAX_DIGITS || nbin < 0 || nbin > ndigits || !radix || steps < 0)
@@ -888,12 +1055,17 @@ int bs_debug_gray_walk(int ndigits, int nbin, const int* radix, uint64_t start, 
         if (C > (1ull << 50)) return fail(BS_EINVAL, "too many addends");
     }
     if (start >= C || start + (uint64_t)steps > C) return fail(BS_EINVAL, "walk leaves [0, C)");
+    // the same per-job binomial table the kernels read
+    uint64_t binom[BS_MAX_DIGITS * 62];
+    int at = 0;
+    for (int j = 0; j < ndigits; ++j)
+        for (int d = 0; d < radix[j]; ++d) binom[at++] = bs_binom(radix[j] - 1, d);
     bs_gray g;
-    bs_gray_decode(g, start, nbin, ndigits, radix);
+    bs_gray_decode(g, start, nbin, ndigits, radix, binom);
     for (int s = 0; s < steps; ++s) {
         if (s > 0) {
             int coef, wch;
-            int row = bs_gray_step(g, radix, &coef, &wch);
+            int row = bs_gray_step(g, radix, &coef, &wch, binom);
             if (moved) moved[s] = row;
         } else if (moved) {
             moved[0] = -1;

@@ -30,7 +30,8 @@
 struct bs_job {
     uint64_t C;            // number of addends = prod of radices
     uint64_t task_begin;   // first global warp-task index of this job
-    uint32_t ntasks;       // warp tasks: each covers 32 chunks of 2^log2L addends
+    uint32_t ntasks;       // warp tasks in this launch: 32 (or 16) chunks of 2^log2L addends each
+    uint32_t task_offset;  // job-local number of this launch's first task (a launch may walk a slice)
     int32_t K;             // product columns
     int32_t nrows;         // digit rows
     int32_t nbin;          // leading binary digits
@@ -48,18 +49,23 @@ struct bs_job {
     int32_t src_trans;     // 1: formula row r / column c read source (c, r)
 };
 
-// Integer metadata of a job, at meta_off (all int32):
+// Integer metadata of a job, at meta_off (int32 units; meta_off even):
 //   radix[nrows]        digit radices R_j = M_j + 1 (binary digits first)
 //   digit_src[nrows]    source row of each digit
 //   col_src[K]          source column of each product column
 //   colexp[K]           power-of-two column scale chosen by the pack kernel
 //   pinned_src          source row of the pinned (delta = +1) row
+//   (one int of padding to an 8-byte boundary)
+//   binom[]             uint64 table written by the pack kernel: for each
+//                       digit j in order, C(M_j, d) for d = 0..M_j
+//                       (nrows + n - 1 entries in all)
 #define BS_META_RADIX(jb) ((jb).meta_off)
 #define BS_META_DIGIT_SRC(jb) ((jb).meta_off + (jb).nrows)
 #define BS_META_COL_SRC(jb) ((jb).meta_off + 2 * (jb).nrows)
 #define BS_META_COLEXP(jb) ((jb).meta_off + 2 * (jb).nrows + (jb).K)
 #define BS_META_PINNED(jb) ((jb).meta_off + 2 * (jb).nrows + 2 * (jb).K)
-#define BS_META_SIZE(nrows, K) (2 * (nrows) + 2 * (K) + 1)
+#define BS_META_BINOM(jb) ((jb).meta_off + 2 * (jb).nrows + 2 * (jb).K + 2)
+#define BS_META_SIZE(nrows, K, n) (2 * (nrows) + 2 * (K) + 2 + 2 * ((nrows) + (n)))
 
 // Row stride of the packed matrix c0 / 2a: K rounded up to even, so FP32
 // rows start on 16-byte boundaries (column pairs load as one float4); the

@@ -19,11 +19,12 @@
 // set bit of the next index).
 //
 // Weights: W = prod_j C(M_j, Delta_j) over multi digits (binary digits have
-// weight 1) kept as an exact 64-bit integer.  On a +1 move of digit j,
-// C(M, D+1) = C(M, D) (M - D) / (D + 1); on a -1 move,
-// C(M, D-1) = C(M, D) D / (M - D + 1); both quotients are exact integers
-// (Appendix A.3, Eq. simplified_binomial, with the +-1 cases as derived
-// here).
+// weight 1) kept as an exact 64-bit integer.  The kernels read C(M_j, d)
+// from a per-job table and recompute the product after a multi-digit move
+// (no integer division on the device).  Without a table the update is the
+// ratio form of Appendix A.3 (Eq. simplified_binomial, with the +-1 cases as
+// derived here): on a +1 move C(M, D+1) = C(M, D) (M - D) / (D + 1), on a -1
+// move C(M, D-1) = C(M, D) D / (M - D + 1), both exact integer quotients.
 #pragma once
 #include <stdint.h>
 #include "bs_job.h"
@@ -71,8 +72,11 @@ struct bs_gray {
     int8_t del[BS_MAX_DIGITS];  // Delta (multi digits)
 };
 
-// Decode index i (constant time per digit).
-BS_HD void bs_gray_decode(bs_gray& g, uint64_t i, int nbin, int nrows, const int* radix) {
+// Decode index i (constant time per digit).  binom (nullable): the job's
+// table of C(M_j, d), digit after digit (binary digits first, 2 entries
+// each); without it the weights are computed directly.
+BS_HD void bs_gray_decode(bs_gray& g, uint64_t i, int nbin, int nrows, const int* radix,
+                          const uint64_t* binom = nullptr) {
     g.i = i;
     g.nbin = nbin;
     g.nrows = nrows;
@@ -84,17 +88,26 @@ BS_HD void bs_gray_decode(bs_gray& g, uint64_t i, int nbin, int nrows, const int
     g.dbin = code;
     int par = bs_popc64(code) & 1;
     uint64_t w = 1;
+    int toff = 2 * nbin;
     for (int j = nbin; j < nrows; ++j) {
-        uint64_t R = (uint64_t)radix[j];
-        uint64_t a = q % R;
-        q = q / R;
-        int odd = (int)(q & 1ull);
-        int d = odd ? (int)(R - 1 - a) : (int)a;
+        const int R = radix[j];
+        int a;
+        if (q <= 0xffffffffull) {  // 32-bit division (64-bit division is slow)
+            const uint32_t q32 = (uint32_t)q;
+            a = (int)(q32 % (uint32_t)R);
+            q = (uint64_t)(q32 / (uint32_t)R);
+        } else {
+            a = (int)(q % (uint64_t)R);
+            q = q / (uint64_t)R;
+        }
+        const int odd = (int)(q & 1ull);
+        const int d = odd ? R - 1 - a : a;
         g.cnt[j] = (int8_t)a;
         g.dir[j] = (int8_t)(odd ? -1 : 1);
         g.del[j] = (int8_t)d;
         par ^= d & 1;
-        w *= bs_binom((int)R - 1, d);
+        w *= binom ? binom[toff + d] : bs_binom(R - 1, d);
+        toff += R;
     }
     g.parity = par;
     g.w = w;
@@ -103,8 +116,9 @@ BS_HD void bs_gray_decode(bs_gray& g, uint64_t i, int nbin, int nrows, const int
 // Advance from i to i+1 (requires i + 1 < C).  Returns the digit row that
 // changed; *coef is the change of its coefficient (M - 2 Delta) divided by 2,
 // i.e. the column sums move by coef * (2 a_row).  Sets *wchanged when the
-// binomial weight changed (only on multi-digit moves).
-BS_HD int bs_gray_step(bs_gray& g, const int* radix, int* coef, int* wchanged) {
+// binomial weight changed (only on multi-digit moves); the new weight is
+// the product of table entries (binom non-null) or the exact ratio update.
+BS_HD int bs_gray_step(bs_gray& g, const int* radix, int* coef, int* wchanged, const uint64_t* binom = nullptr) {
     uint64_t lo = g.i & g.binmask;
     int row;
     g.parity ^= 1;
@@ -125,18 +139,25 @@ BS_HD int bs_gray_step(bs_gray& g, const int* radix, int* coef, int* wchanged) {
     }
     row = j;
     g.cnt[j] = (int8_t)(g.cnt[j] + 1);
-    uint64_t M = (uint64_t)(radix[j] - 1);
-    uint64_t d0 = (uint64_t)g.del[j];
-    if (g.dir[j] > 0) {
-        g.w = g.w * (M - d0) / (d0 + 1);
-        g.del[j] = (int8_t)(d0 + 1);
-        *coef = -1;
-    } else {
-        g.w = g.w * d0 / (M - d0 + 1);
-        g.del[j] = (int8_t)(d0 - 1);
-        *coef = 1;
-    }
+    const int M = radix[j] - 1;
+    const int d0 = g.del[j];
+    const int d1 = d0 + g.dir[j];
+    g.del[j] = (int8_t)d1;
+    *coef = g.dir[j] > 0 ? -1 : 1;
     *wchanged = 1;
+    if (binom) {
+        uint64_t w = 1;
+        int toff = 2 * g.nbin;
+        for (int k = g.nbin; k < g.nrows; ++k) {
+            w *= binom[toff + g.del[k]];
+            toff += radix[k];
+        }
+        g.w = w;
+    } else if (d1 > d0) {
+        g.w = g.w * (uint64_t)(M - d0) / (uint64_t)(d0 + 1);
+    } else {
+        g.w = g.w * (uint64_t)d0 / (uint64_t)(M - d0 + 1);
+    }
     return row;
 }
 

@@ -46,13 +46,14 @@ namespace {
 // byte offsets inside the scratch array (each 256-byte aligned)
 constexpr size_t kCtl = 0;                                        // u64 counter, int status at +8
 constexpr size_t kJob = 256;                                      // one bs_job
-constexpr size_t kMeta = 512;                                     // <= BS_META_SIZE(48, 48) ints
-constexpr size_t kOut = 1536;                                     // result hi / lo (2 x 16 bytes)
-constexpr size_t kSrc = 2048;                                     // compacted matrix, <= 48 x 48
+constexpr size_t kMeta = 512;                                     // <= BS_META_SIZE(48, 48, 48) ints
+constexpr size_t kOut = 2304;                                     // result hi / lo (2 x 16 bytes)
+constexpr size_t kSrc = 2560;                                     // compacted matrix, <= 48 x 48
 constexpr size_t kData = kSrc + (size_t)BS_MAX_N * BS_MAX_N * 16;  // packed c0 / 2a
 constexpr size_t kPart = kData + (size_t)(1 + BS_MAX_N) * BS_ROW_STRIDE(BS_MAX_N) * 16;
 constexpr size_t kPartSlots = (BS_NOALLOC_SCRATCH_BYTES - kPart) / sizeof(bs_zdd);
 static_assert(kPart % 256 == 0 && kData % 256 == 0, "scratch regions must stay aligned");
+static_assert(kMeta + BS_META_SIZE(BS_MAX_DIGITS, BS_MAX_COLS, BS_MAX_N) * 4 <= kOut, "metadata region too small");
 
 std::mutex g_setup_mu;
 unsigned char* g_scratch_dev[64];  // device address of the array, per device
@@ -118,7 +119,7 @@ extern "C" int bs_perm_noalloc(const bs_c128* A, int rows, int cols, int ld, con
     if (!A) return bs::fail(BS_EINVAL, "matrix pointer is NULL");
     if (ld < cols) return bs::fail(BS_EINVAL, "leading dimension %d < columns %d", ld, cols);
     const int fp32 = (mode == BS_MIXED && bs_mixed_uses_fp32(p.radix, p.nrows, p.K, p.n)) ? 1 : 0;
-    const int log2L = bs_choose_log2L(p.C, 32, 12);
+    const int log2L = bs_choose_log2L(p.C, 32, 12, BS_TARGET_TASKS_SINGLE);
     const uint64_t per = 32ull << log2L;
     const uint64_t ntasks = (p.C + per - 1) / per;
     if (ntasks > kPartSlots)
@@ -145,13 +146,15 @@ extern "C" int bs_perm_noalloc(const bs_c128* A, int rows, int cols, int ld, con
     jb.fp32 = fp32;
     jb.src_ld = nc;
     jb.src_trans = p.trans ? 1 : 0;
-    int meta[BS_META_SIZE(BS_MAX_DIGITS, BS_MAX_COLS)];
+    int meta[BS_META_SIZE(BS_MAX_DIGITS, BS_MAX_COLS, BS_MAX_N)];
     int m = 0;
     for (int d = 0; d < p.nrows; ++d) meta[m++] = p.radix[d];
     for (int d = 0; d < p.nrows; ++d) meta[m++] = p.digit_src[d];
     for (int j = 0; j < p.K; ++j) meta[m++] = p.col_src[j];
     for (int j = 0; j < p.K; ++j) meta[m++] = 0;
     meta[m++] = p.pinned_src;
+    meta[m++] = 0;                                            // pad; the binomial table follows
+    for (int t = 0; t < 2 * (p.nrows + p.n); ++t) meta[m++] = 0;
     int dev = 0;
     NA_CUDA(cudaGetDevice(&dev));
     unsigned char* scr = nullptr;

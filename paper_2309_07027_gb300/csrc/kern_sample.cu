@@ -68,7 +68,8 @@ cudaError_t launch_philox(const uint32_t* in, uint32_t* out, int count, cudaStre
 }
 
 // cols[s][0..n) = Fisher-Yates permutation of the expanded input columns.
-__global__ void cc_init_kernel(const CcArgs a) {
+__global__ void cc_init_kernel(const CcArgs* __restrict__ pa) {
+    const CcArgs& a = *pa;
     const int s = blockIdx.x * blockDim.x + threadIdx.x;
     if (s >= a.S) return;
     int* cols = a.cols + (size_t)s * a.n;
@@ -84,7 +85,8 @@ __global__ void cc_init_kernel(const CcArgs a) {
 }
 
 // Plan + pack the step-k minors job of every chain (one CTA per chain).
-__global__ void cc_plan_kernel(const CcArgs a, int k) {
+__global__ void cc_plan_kernel(const CcArgs* __restrict__ pa, int k) {
+    const CcArgs& a = *pa;
     __shared__ int urow[BS_MAX_PHOTONS], ucnt[BS_MAX_PHOTONS];
     __shared__ int drad[BS_MAX_PHOTONS], dsrc[BS_MAX_PHOTONS];
     __shared__ bs_job sjb;
@@ -108,7 +110,7 @@ __global__ void cc_plan_kernel(const CcArgs a, int k) {
         int p = 0;
         for (int u = 1; u < nu; ++u)
             if (ucnt[u] < ucnt[p]) p = u;
-        bs_job jb;
+        bs_job jb = {};  // every field not set below is zero
         jb.kind = BS_KIND_MINORS;
         jb.K = k;
         jb.n = k - 1;
@@ -169,7 +171,7 @@ __global__ void cc_plan_kernel(const CcArgs a, int k) {
         uint64_t C = 1;
         for (int j = 0; j < nrows; ++j) C *= (uint64_t)meta[j];
         jb.C = C;
-        jb.log2L = bs_choose_log2L(C, cpt, log2max);
+        jb.log2L = bs_choose_log2L(C, cpt, log2max, BS_TARGET_TASKS_MANY);
         jb.ntasks = (uint32_t)((C + ((uint64_t)cpt << jb.log2L) - 1) / ((uint64_t)cpt << jb.log2L));
         jb.task_begin = 0;
         a.jobs[s] = jb;
@@ -198,7 +200,8 @@ __device__ unsigned long long block_scan(unsigned long long v, unsigned long lon
 // chains walked by that kernel, their task offsets (exclusive scan of ntasks
 // in list order), the task total, a zeroed work counter, and the addend /
 // flop counters used for the roofline.
-__global__ void cc_scan_kernel(const CcArgs a, int k) {
+__global__ void cc_scan_kernel(const CcArgs* __restrict__ pa, int k) {
+    const CcArgs& a = *pa;
     __shared__ unsigned long long buf[1024];
     __shared__ unsigned long long carry_t, carry_n, adds;
     for (int p = 0; p < 2; ++p) {
@@ -238,7 +241,8 @@ __global__ void cc_scan_kernel(const CcArgs a, int k) {
 }
 
 // Draw r_k for every chain (one CTA per chain).
-__global__ void cc_draw_kernel(const CcArgs a, int k) {
+__global__ void cc_draw_kernel(const CcArgs* __restrict__ pa, int k) {
+    const CcArgs& a = *pa;
     extern __shared__ double wts[];
     const int s = blockIdx.x;
     const int* cols = a.cols + (size_t)s * a.n;
@@ -284,7 +288,8 @@ __global__ void cc_draw_kernel(const CcArgs a, int k) {
     }
 }
 
-__global__ void cc_counts_kernel(const CcArgs a) {
+__global__ void cc_counts_kernel(const CcArgs* __restrict__ pa) {
+    const CcArgs& a = *pa;
     const int s = blockIdx.x;
     const int* rows = a.rows + (size_t)s * a.n;
     for (int i = threadIdx.x; i < a.m_det; i += blockDim.x) {
@@ -294,34 +299,38 @@ __global__ void cc_counts_kernel(const CcArgs a) {
     }
 }
 
-cudaError_t launch_cc_init(const CcArgs& a, cudaStream_t st) {
+// `a` is the host copy (launch shapes); `da` the same struct in device
+// memory, which the kernels read (so a captured graph can be replayed with
+// new seeds / offsets by rewriting *da).
+cudaError_t launch_cc_init(const CcArgs& a, const CcArgs* da, cudaStream_t st) {
     if (a.S <= 0) return cudaSuccess;
-    cc_init_kernel<<<(a.S + 127) / 128, 128, 0, st>>>(a);
+    cc_init_kernel<<<(a.S + 127) / 128, 128, 0, st>>>(da);
     return cudaGetLastError();
 }
 
-cudaError_t launch_cc_plan(const CcArgs& a, int k, cudaStream_t st) {
-    cc_plan_kernel<<<a.S, 64, 0, st>>>(a, k);
+cudaError_t launch_cc_plan(const CcArgs& a, const CcArgs* da, int k, cudaStream_t st) {
+    cc_plan_kernel<<<a.S, 64, 0, st>>>(da, k);
     return cudaGetLastError();
 }
 
-cudaError_t launch_cc_scan(const CcArgs& a, int k, cudaStream_t st) {
-    cc_scan_kernel<<<1, 1024, 0, st>>>(a, k);
+cudaError_t launch_cc_scan(const CcArgs& a, const CcArgs* da, int k, cudaStream_t st) {
+    (void)a;
+    cc_scan_kernel<<<1, 1024, 0, st>>>(da, k);
     return cudaGetLastError();
 }
 
-cudaError_t launch_cc_draw(const CcArgs& a, int k, cudaStream_t st) {
+cudaError_t launch_cc_draw(const CcArgs& a, const CcArgs* da, int k, cudaStream_t st) {
     size_t smem = (size_t)a.m_rows * sizeof(double);
     if (smem > 48 * 1024) {
         cudaError_t e = cudaFuncSetAttribute(cc_draw_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
     }
-    cc_draw_kernel<<<a.S, 128, smem, st>>>(a, k);
+    cc_draw_kernel<<<a.S, 128, smem, st>>>(da, k);
     return cudaGetLastError();
 }
 
-cudaError_t launch_cc_counts(const CcArgs& a, cudaStream_t st) {
-    cc_counts_kernel<<<a.S, 64, 0, st>>>(a);
+cudaError_t launch_cc_counts(const CcArgs& a, const CcArgs* da, cudaStream_t st) {
+    cc_counts_kernel<<<a.S, 64, 0, st>>>(da);
     return cudaGetLastError();
 }
 

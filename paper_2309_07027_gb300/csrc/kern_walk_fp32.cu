@@ -11,6 +11,7 @@ namespace bs {
 constexpr int kPermBlock = 128;
 constexpr int kMinorsBlock = 128;
 
+
 template <int KB>
 __global__ void __launch_bounds__(kPermBlock) walk_fp32_perm_kernel(WalkArgs a) {
     const int lane = threadIdx.x & 31;
@@ -27,7 +28,7 @@ __global__ void __launch_bounds__(kPermBlock) walk_fp32_perm_kernel(WalkArgs a) 
             if (lane == 0) atomicExch(a.status, BS_STATUS_BADJOB);
             continue;
         }
-        walk_task_perm<float, KB>(jb, data, a.meta + BS_META_RADIX(jb), a.partials, (uint32_t)(t - jb.task_begin),
+        walk_task_perm<float, KB>(jb, data, a.meta + BS_META_RADIX(jb), a.partials, (uint32_t)(t - jb.task_begin) + jb.task_offset,
                                   lane);
     }
 }
@@ -51,7 +52,7 @@ __global__ void __launch_bounds__(kMinorsBlock) walk_fp32_minors_kernel(WalkArgs
             if (lane == 0) atomicExch(a.status, BS_STATUS_BADJOB);
             continue;
         }
-        walk_task_minors_fp32<KB>(jb, data, a.meta + BS_META_RADIX(jb), a.partials, (uint32_t)(t - jb.task_begin),
+        walk_task_minors_fp32<KB>(jb, data, a.meta + BS_META_RADIX(jb), a.partials, (uint32_t)(t - jb.task_begin) + jb.task_offset,
                                   lane, sm_ff, stride);
     }
 }

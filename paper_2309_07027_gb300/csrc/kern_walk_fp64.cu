@@ -27,7 +27,7 @@ __global__ void __launch_bounds__(kPermBlock) walk_fp64_perm_kernel(WalkArgs a) 
             continue;
         }
         walk_task_perm<double, KB>(jb, data, a.meta + BS_META_RADIX(jb), a.partials,
-                                   (uint32_t)(t - jb.task_begin), lane);
+                                   (uint32_t)(t - jb.task_begin) + jb.task_offset, lane);
     }
 }
 
@@ -51,7 +51,7 @@ __global__ void __launch_bounds__(kMinorsBlock) walk_fp64_minors_kernel(WalkArgs
             if (lane == 0) atomicExch(a.status, BS_STATUS_BADJOB);
             continue;
         }
-        walk_task_minors_fp64<KB>(jb, data, a.meta + BS_META_RADIX(jb), a.partials, (uint32_t)(t - jb.task_begin),
+        walk_task_minors_fp64<KB>(jb, data, a.meta + BS_META_RADIX(jb), a.partials, (uint32_t)(t - jb.task_begin) + jb.task_offset,
                                   lane, sm_suf, sm_acc, stride);
     }
 }

@@ -8,6 +8,7 @@
 #pragma once
 #include <cuda_runtime.h>
 #include "bs_job.h"
+#include "gray.h"
 #include "walk.cuh"
 
 namespace bs {
@@ -23,6 +24,13 @@ __device__ __forceinline__ void pack_job(const bs_job& jb, const double2* __rest
     const int* csrc = meta + BS_META_COL_SRC(jb);
     int* colexp = meta + BS_META_COLEXP(jb);
     const int prow = meta[BS_META_PINNED(jb)];
+    // binomial table C(M_j, d), digit after digit
+    if (tid == 0) {
+        uint64_t* binom = reinterpret_cast<uint64_t*>(meta + BS_META_BINOM(jb));
+        int at = 0;
+        for (int j = 0; j < jb.nrows; ++j)
+            for (int d = 0; d < radix[j]; ++d) binom[at++] = bs_binom(radix[j] - 1, d);
+    }
     const int KP = BS_ROW_STRIDE(jb.K);
     for (int col = tid; col < KP; col += nthreads) {
         if (col >= jb.K) {  // pad column: zeros

@@ -7,12 +7,17 @@
 #include <math.h>
 
 // Chunk length exponent of a job with C addends whose warp tasks cover `cpt`
-// chunks: aim at about 4096 tasks per job (enough to fill the GPU with one
-// job), never below 2^6 addends per chunk (decode cost) nor above 2^log2max
-// (the re-seed interval).  Depends only on (C, cpt, log2max), so a job is cut
-// the same way alone or inside any batch.
-BS_HD int bs_choose_log2L(uint64_t C, int cpt, int log2max) {
-    uint64_t per = C / ((uint64_t)cpt * 4096ull);
+// chunks: aim at about `target` tasks per job, never below 2^6 addends per
+// chunk (decode cost) nor above 2^log2max (the re-seed interval).  Depends
+// only on (C, cpt, log2max, target), so a job is cut the same way alone or
+// inside any batch that uses the same target.  Jobs planned one call at a
+// time use BS_TARGET_TASKS_SINGLE (several tasks per resident warp, so one
+// job fills the GPU without a ragged tail); the sampler and the server, which always run many jobs together,
+// use BS_TARGET_TASKS_MANY (longer chunks, fewer tasks).
+#define BS_TARGET_TASKS_SINGLE 8192
+#define BS_TARGET_TASKS_MANY 64
+BS_HD int bs_choose_log2L(uint64_t C, int cpt, int log2max, int target) {
+    uint64_t per = C / ((uint64_t)cpt * (uint64_t)target);
     int l = 0;
     while ((2ull << l) <= per) ++l;  // floor(log2(per)) for per >= 1
     if (per == 0) l = 0;
@@ -83,11 +88,11 @@ struct CcArgs {
     int log2max64, log2max32;
 };
 
-cudaError_t launch_cc_init(const CcArgs& a, cudaStream_t st);
-cudaError_t launch_cc_plan(const CcArgs& a, int k, cudaStream_t st);
-cudaError_t launch_cc_scan(const CcArgs& a, int k, cudaStream_t st);
-cudaError_t launch_cc_draw(const CcArgs& a, int k, cudaStream_t st);
-cudaError_t launch_cc_counts(const CcArgs& a, cudaStream_t st);
+cudaError_t launch_cc_init(const CcArgs& a, const CcArgs* da, cudaStream_t st);
+cudaError_t launch_cc_plan(const CcArgs& a, const CcArgs* da, int k, cudaStream_t st);
+cudaError_t launch_cc_scan(const CcArgs& a, const CcArgs* da, int k, cudaStream_t st);
+cudaError_t launch_cc_draw(const CcArgs& a, const CcArgs* da, int k, cudaStream_t st);
+cudaError_t launch_cc_counts(const CcArgs& a, const CcArgs* da, cudaStream_t st);
 cudaError_t launch_philox(const uint32_t* in, uint32_t* out, int count, cudaStream_t s);
 
 }  // namespace bs

@@ -185,8 +185,11 @@ struct ChunkStepper {
     int parity0;    // parity at the chunk start
     int nbin;
 
-    __device__ __forceinline__ void init(uint64_t start, int nb, int nrows, const int* radix) {
-        bs_gray_decode(g, start, nb, nrows, radix);
+    const uint64_t* binom;
+
+    __device__ __forceinline__ void init(uint64_t start, int nb, int nrows, const int* radix, const uint64_t* tab) {
+        binom = tab;
+        bs_gray_decode(g, start, nb, nrows, radix, tab);
         i0 = start;
         dlo = (uint32_t)g.dbin;
         parity0 = g.parity;
@@ -209,7 +212,7 @@ struct ChunkStepper {
         g.parity = parity0 ^ (int)(s & 1u);
         g.dbin = (g.dbin & ~0xffffffffull) | (uint64_t)dlo;
         int coef;
-        const int row = bs_gray_step(g, radix, &coef, wch);
+        const int row = bs_gray_step(g, radix, &coef, wch, binom);
         *neg = coef < 0 ? 1u : 0u;
         return row;
     }
@@ -348,7 +351,7 @@ __device__ void walk_task_perm(const bs_job& jb, const cx<T>* __restrict__ data,
         const uint64_t rem = jb.C - i0;
         const uint32_t len = (uint32_t)(rem < (1ull << jb.log2L) ? rem : (1ull << jb.log2L));
         ChunkStepper st;
-        st.init(i0, jb.nbin, jb.nrows, radix);
+        st.init(i0, jb.nbin, jb.nrows, radix, reinterpret_cast<const uint64_t*>(radix + (BS_META_BINOM(jb) - jb.meta_off)));
         cx<T> c[KB];
         seed_columns<T, KB>(c, st.g, c0, a2, K, KP, jb.nbin, jb.nrows);
         T ws = signed_weight<T>(st.g.w, st.g.parity);
@@ -422,7 +425,7 @@ __device__ void walk_task_minors_fp64(const bs_job& jb, const cx<double>* __rest
         const uint64_t rem = jb.C - i0;
         const uint32_t len = (uint32_t)(rem < (1ull << jb.log2L) ? rem : (1ull << jb.log2L));
         ChunkStepper st;
-        st.init(i0, jb.nbin, jb.nrows, radix);
+        st.init(i0, jb.nbin, jb.nrows, radix, reinterpret_cast<const uint64_t*>(radix + (BS_META_BINOM(jb) - jb.meta_off)));
         cx<double> c[KB];
         seed_columns<double, KB>(c, st.g, c0, a2, K, KP, jb.nbin, jb.nrows);
         double ws = signed_weight<double>(st.g.w, st.g.parity);
@@ -518,7 +521,7 @@ __device__ void walk_task_minors_fp32(const bs_job& jb, const cx<float>* __restr
         const uint64_t rem = jb.C - i0;
         const uint32_t len = (uint32_t)(rem < (1ull << jb.log2L) ? rem : (1ull << jb.log2L));
         ChunkStepper st;
-        st.init(i0, jb.nbin, jb.nrows, radix);
+        st.init(i0, jb.nbin, jb.nrows, radix, reinterpret_cast<const uint64_t*>(radix + (BS_META_BINOM(jb) - jb.meta_off)));
         cx<float> c[H];
         {
             // seed own columns: c = c0 - sum_j Delta_j 2a_j

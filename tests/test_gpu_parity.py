@@ -227,6 +227,19 @@ def test_batch_device_pointers(ctx):
     assert np.array_equal(out.cpu().numpy(), host)
 
 
+def test_autotuner_picks_a_valid_chunk_and_results_stay_exact(ctx, bslib):
+    saved = (ctx.chunk_log2(0), ctx.chunk_log2(1))
+    try:
+        for mode in (0, 1):
+            best, rate = ctx.tune(mode, kind=1, K=20)
+            assert best in (8, 10, 12, 14) and ctx.chunk_log2(mode) == best and rate > 0
+            a, M, N, _, _ = S.config_single(seed=1)
+            assert abs(ctx.perm(a, M, N, mode=mode) - ref_perm(a, M, N)) <= TOL[mode] * scale(a, M, N)
+    finally:
+        ctx.set_chunk_log2(0, saved[0])
+        ctx.set_chunk_log2(1, saved[1])
+
+
 def test_deadline_returns_timeout_and_context_survives(ctx, bslib):
     u = S.haar_unitary(40, 5)
     a = u[:30, :30]
@@ -255,6 +268,21 @@ def test_sampler_matches_oracle_sampler_fp64(ctx):
     assert all(margin[s] < 1e-9 for s in mismatch), (mismatch, margin[mismatch])
     assert len(mismatch) <= 1
     assert np.all(got.sum(axis=1) == 6)
+
+
+def test_sampler_graph_replay_equals_eager(ctx):
+    """The captured step loop, replayed for new seeds, draws exactly what the
+    directly launched kernels draw."""
+    u, occ = S.config_cc(n=10, m=20, seed=8)
+    ctx.set_graphs(False)
+    try:
+        eager = [ctx.sample(u, occ, 64, seed=s, mode=m) for s, m in ((1, 0), (2, 0), (3, 1))]
+    finally:
+        ctx.set_graphs(True)
+    for rep in range(2):
+        graph = [ctx.sample(u, occ, 64, seed=s, mode=m) for s, m in ((1, 0), (2, 0), (3, 1))]
+        for e, g in zip(eager, graph):
+            assert np.array_equal(e, g)
 
 
 def test_sampler_seed_and_batch_independence(ctx):
