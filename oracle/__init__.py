@@ -121,9 +121,7 @@ def ryser(a):
     return _dd_value(out)
 
 
-def ryser_exact_gauss(a_int):
-    """Exact Ryser for Gaussian-integer matrices; returns a Python complex of ints
-    as a (re, im) tuple of Python ints."""
+def _exact_gauss_call(name, a_int):
     a = np.asarray(a_int)
     n = a.shape[0]
     buf = np.zeros((n, n, 2), dtype=np.int64)
@@ -131,12 +129,44 @@ def ryser_exact_gauss(a_int):
     buf[..., 1] = np.imag(a).astype(np.int64)
     buf = np.ascontiguousarray(buf)
     out = np.zeros(4, dtype=np.int64)
-    _chk(lib().orc_ryser_exact_gauss(n, buf.ctypes.data_as(C.POINTER(C.c_int64)),
-                                      out.ctypes.data_as(C.POINTER(C.c_int64))), "ryser_exact_gauss")
+    _chk(getattr(lib(), name)(n, buf.ctypes.data_as(C.POINTER(C.c_int64)),
+                              out.ctypes.data_as(C.POINTER(C.c_int64))), name)
 
     def join(hi, lo):
         return (int(hi) << 64) + (int(lo) & ((1 << 64) - 1))
     return join(out[0], out[1]), join(out[2], out[3])
+
+
+def ryser_exact_gauss(a_int):
+    """Exact Ryser for Gaussian-integer matrices; returns a Python complex of ints
+    as a (re, im) tuple of Python ints."""
+    return _exact_gauss_call("orc_ryser_exact_gauss", a_int)
+
+
+def nw(a):
+    """Nijenhuis-Wilf form of Eq. (ryser) (Sec. 2), Gray-ordered subsets."""
+    a = _mat(a)
+    n = a.shape[0]
+    assert a.shape == (n, n)
+    out = np.zeros(4)
+    _chk(lib().orc_nw_gray(n, _dp(a.view(np.float64)), n, _dp(out)), "nw_gray")
+    return _dd_value(out)
+
+
+def nw_exact_gauss(a_int):
+    """Exact Nijenhuis-Wilf for Gaussian-integer matrices; (re, im) Python ints."""
+    return _exact_gauss_call("orc_nw_exact_gauss", a_int)
+
+
+def formula_abs(which, a):
+    """Modulus-sum of the addends of Eq. (ryser) (which='ryser') or of the
+    Nijenhuis-Wilf form (which='nw'), times the prefactor's modulus."""
+    a = _mat(a)
+    n = a.shape[0]
+    out = np.zeros(1)
+    code = {"ryser": 1, "nw": 2}[which]
+    _chk(lib().orc_formula_abs(code, n, _dp(a.view(np.float64)), n, _dp(out)), "formula_abs")
+    return float(out[0])
 
 
 def _mult_call(name, a, row_mult, col_mult, nout):

@@ -26,6 +26,12 @@
  *   orc_ryser_gray        Eq. (ryser), subsets walked in Gray order
  *   orc_ryser_exact_gauss Eq. (ryser) in exact 128-bit integers for
  *                         Gaussian-integer matrices
+ *   orc_nw_gray           the Nijenhuis-Wilf form of Eq. (ryser) (Sec. 2:
+ *                         x_i = a_in - sum_j a_ij / 2, subsets of the first
+ *                         n-1 columns), walked in Gray order
+ *   orc_nw_exact_gauss    the same in exact 128-bit integers
+ *   orc_formula_abs       modulus-sum of the addends of Eq. (ryser) or of
+ *                         the Nijenhuis-Wilf form (times their prefactor)
  *   orc_perm_mult         Eq. (bbfgrepeated) evaluated term by term: every
  *                         Delta vector enumerated in plain odometer order,
  *                         binomials and column sums computed directly
@@ -280,6 +286,121 @@ int orc_ryser_exact_gauss(int n, const int64_t* A, int64_t* out) {
     if (n & 1) { are = -are; aim = -aim; }
     out[0] = (int64_t)(are >> 64); out[1] = (int64_t)(uint64_t)are;
     out[2] = (int64_t)(aim >> 64); out[3] = (int64_t)(uint64_t)aim;
+    return 0;
+}
+
+/* ------------------------------------------------------------------ */
+/* Nijenhuis-Wilf form of Eq. (ryser) (Sec. 2):                         */
+/*   perm = (-1)^(n-1) 2 sum_{S in {1..n-1}} (-1)^|S|                   */
+/*          prod_i (x_i + sum_{j in S} a_ij),                           */
+/*   x_i = a_in - (a_i1 + ... + a_in) / 2.                              */
+/* Subsets of the first n-1 columns walked in Gray order.               */
+/* ------------------------------------------------------------------ */
+int orc_nw_gray(int n, const double* A, int ld, double* out) {
+    if (n < 0 || n > 30) return -1;
+    if (n == 0) { z_store(z_one(), out); return 0; }
+    zdd rs[64];
+    for (int i = 0; i < n; ++i) {
+        zdd row = z_zero();
+        for (int j = 0; j < n; ++j) row = z_add(row, z_elem(A, ld, i, j));
+        rs[i] = z_sub(z_elem(A, ld, i, n - 1), z_ldexp(row, -1));
+    }
+    zdd acc = z_zero();
+    uint64_t count = (uint64_t)1 << (n - 1);
+    uint64_t gray_prev = 0;
+    int card = 0;
+    for (uint64_t g = 0; g < count; ++g) {
+        if (g > 0) {
+            int t = __builtin_ctzll(g);
+            int in_set = (int)((gray_prev >> t) & 1u);
+            for (int i = 0; i < n; ++i) {
+                zdd a = z_elem(A, ld, i, t);
+                rs[i] = in_set ? z_sub(rs[i], a) : z_add(rs[i], a);
+            }
+            gray_prev ^= (uint64_t)1 << t;
+            card += in_set ? -1 : 1;
+        }
+        zdd p = z_one();
+        for (int i = 0; i < n; ++i) p = z_mul(p, rs[i]);
+        acc = (card & 1) ? z_sub(acc, p) : z_add(acc, p);
+    }
+    acc = z_ldexp(acc, 1);
+    if ((n - 1) & 1) acc = z_mul_d(acc, -1.0);
+    z_store(acc, out);
+    return 0;
+}
+
+/* The Nijenhuis-Wilf form in exact integers for Gaussian-integer matrices.
+ * With y_i = 2 x_i + 2 sum_{j in S} a_ij (an integer),
+ *   perm = (-1)^(n-1) 2^(1-n) sum_S (-1)^|S| prod_i y_i;
+ * the sum must be divisible by 2^(n-1) (else -2 is returned).  Output as in
+ * orc_ryser_exact_gauss. */
+int orc_nw_exact_gauss(int n, const int64_t* A, int64_t* out) {
+    if (n < 0 || n > 14) return -1;
+    i128 are = 0, aim = 0;
+    if (n == 0) are = 1;
+    if (n > 0) {
+        i128 x2re[64], x2im[64];
+        for (int i = 0; i < n; ++i) {
+            i128 sre = 0, sim = 0;
+            for (int j = 0; j < n; ++j) { sre += A[2 * (i * n + j)]; sim += A[2 * (i * n + j) + 1]; }
+            x2re[i] = 2 * (i128)A[2 * (i * n + n - 1)] - sre;
+            x2im[i] = 2 * (i128)A[2 * (i * n + n - 1) + 1] - sim;
+        }
+        uint64_t count = (uint64_t)1 << (n - 1);
+        for (uint64_t S = 0; S < count; ++S) {
+            i128 pre = 1, pim = 0;
+            for (int i = 0; i < n; ++i) {
+                i128 yre = x2re[i], yim = x2im[i];
+                for (int j = 0; j < n - 1; ++j)
+                    if ((S >> j) & 1u) { yre += 2 * (i128)A[2 * (i * n + j)]; yim += 2 * (i128)A[2 * (i * n + j) + 1]; }
+                i128 tre = pre * yre - pim * yim;
+                i128 tim = pre * yim + pim * yre;
+                pre = tre; pim = tim;
+            }
+            if (__builtin_popcountll(S) & 1) { are -= pre; aim -= pim; } else { are += pre; aim += pim; }
+        }
+        const i128 div = (i128)1 << (n - 1);
+        if (are % div != 0 || aim % div != 0) return -2;
+        are /= div; aim /= div;
+        if ((n - 1) & 1) { are = -are; aim = -aim; }
+    }
+    out[0] = (int64_t)(are >> 64); out[1] = (int64_t)(uint64_t)are;
+    out[2] = (int64_t)(aim >> 64); out[3] = (int64_t)(uint64_t)aim;
+    return 0;
+}
+
+/* Modulus-sum of the addends of Eq. (ryser) (which = 1) or of the
+ * Nijenhuis-Wilf form (which = 2), each addend |prod_i inner sum| times the
+ * modulus of the prefactor (1, or 2); every subset evaluated directly in
+ * plain double.  The scale of the rounding error of those formulas. */
+int orc_formula_abs(int which, int n, const double* A, int ld, double* out) {
+    if (n < 0 || n > 24 || (which != 1 && which != 2)) return -1;
+    if (n == 0) { out[0] = 1.0; return 0; }
+    double xre[64], xim[64];
+    for (int i = 0; i < n; ++i) {
+        xre[i] = 0.0; xim[i] = 0.0;
+        if (which == 2) {
+            double sre = 0.0, sim = 0.0;
+            for (int j = 0; j < n; ++j) { sre += A[2 * (i * ld + j)]; sim += A[2 * (i * ld + j) + 1]; }
+            xre[i] = A[2 * (i * ld + n - 1)] - 0.5 * sre;
+            xim[i] = A[2 * (i * ld + n - 1) + 1] - 0.5 * sim;
+        }
+    }
+    const int cols = which == 1 ? n : n - 1;
+    const uint64_t count = (uint64_t)1 << cols;
+    double acc = 0.0;
+    for (uint64_t S = 0; S < count; ++S) {
+        double mag = 1.0;
+        for (int i = 0; i < n; ++i) {
+            double re = xre[i], im = xim[i];
+            for (int j = 0; j < cols; ++j)
+                if ((S >> j) & 1u) { re += A[2 * (i * ld + j)]; im += A[2 * (i * ld + j) + 1]; }
+            mag *= hypot(re, im);
+        }
+        acc += mag;
+    }
+    out[0] = which == 2 ? 2.0 * acc : acc;
     return 0;
 }
 

@@ -59,10 +59,13 @@ def test_textbook_small_permanents():
     assert oracle.perm_bruteforce(np.arange(1, 10).reshape(3, 3))[0] == 450
     assert oracle.bbfg_gray(np.arange(1, 10).reshape(3, 3))[0] == 450
     assert oracle.ryser(np.arange(1, 10).reshape(3, 3))[0] == 450
+    assert oracle.nw(np.arange(1, 10).reshape(3, 3))[0] == 450
+    assert oracle.nw(np.array([[2.5 - 1j]]))[0] == 2.5 - 1j
     assert oracle.bbfg_gray(np.array([[2.5 - 1j]]))[0] == 2.5 - 1j
     # empty matrix: the permanent of the 0 x 0 matrix is 1
     assert oracle.bbfg_gray(np.zeros((0, 0)))[0] == 1
     assert oracle.ryser(np.zeros((0, 0)))[0] == 1
+    assert oracle.nw(np.zeros((0, 0)))[0] == 1
 
 
 def test_bruteforce_matches_python_bruteforce():
@@ -79,7 +82,7 @@ def test_bruteforce_matches_python_bruteforce():
 def test_four_formulas_agree(n):
     a = S.random_complex(n, n, 100 + n)
     ref = oracle.perm_bruteforce(a)
-    for f in (oracle.bbfg_gray, oracle.bbfg_direct, oracle.ryser):
+    for f in (oracle.bbfg_gray, oracle.bbfg_direct, oracle.ryser, oracle.nw):
         v = f(a)
         err = abs((v[0] - ref[0]) + (v[1] - ref[1]))
         assert err <= 1e-27 * max(1.0, abs(ref[0])) * math.factorial(n), (f.__name__, n, err)
@@ -105,7 +108,7 @@ def test_mpmath_50_digits():
 def test_ones_matrix_is_factorial():
     for n in range(1, 17):
         j = np.ones((n, n))
-        for f in (oracle.bbfg_gray, oracle.ryser):
+        for f in (oracle.bbfg_gray, oracle.ryser, oracle.nw):
             v, tail = f(j)
             assert v.imag == 0 and tail.imag == 0
             assert int(Fraction(v.real) + Fraction(tail.real)) == math.factorial(n), (f.__name__, n)
@@ -118,6 +121,8 @@ def test_diagonal_is_product():
         assert rel(v + tail, np.prod(d)) < 1e-15
         v2, _ = oracle.ryser(np.diag(d))
         assert rel(v2, np.prod(d)) < 1e-15
+        v3, _ = oracle.nw(np.diag(d))
+        assert rel(v3, np.prod(d)) < 1e-15
 
 
 def test_row_and_column_permutation_invariance():
@@ -143,6 +148,41 @@ def test_exact_gaussian_integer_permanents():
         got_re = Fraction(v.real) + Fraction(tail.real)
         got_im = Fraction(v.imag) + Fraction(tail.imag)
         assert got_re == re and got_im == im, n
+
+
+def test_nijenhuis_wilf_exact_gaussian_integers():
+    """The Nijenhuis-Wilf form (Sec. 2) in exact integers equals Ryser's
+    formula and the permanent's definition; its double-double Gray walk
+    gives the same integers."""
+    for n in range(1, 12):
+        a = S.gaussian_integer_matrix(n, 520 + n, bound=3)
+        nw_exact = oracle.nw_exact_gauss(a)
+        assert nw_exact == oracle.ryser_exact_gauss(a), n
+        if n <= 6:
+            ref = py_perm([[complex(int(x.real), int(x.imag)) for x in row] for row in a])
+            assert nw_exact == (int(ref.real), int(ref.imag))
+        v, tail = oracle.nw(a)
+        assert Fraction(v.real) + Fraction(tail.real) == nw_exact[0], n
+        assert Fraction(v.imag) + Fraction(tail.imag) == nw_exact[1], n
+
+
+def test_formula_abs_closed_forms():
+    """Modulus sums of the Ryser and Nijenhuis-Wilf addends: closed forms on
+    J_n and on the identity, and the bound S_abs >= |perm|."""
+    for n in range(1, 11):
+        j = np.ones((n, n))
+        ryser_abs = sum(math.comb(n, k) * k ** n for k in range(n + 1))
+        nw_abs = 2 * sum(math.comb(n - 1, k) * abs(Fraction(2 - n, 2) + k) ** n for k in range(n))
+        assert oracle.formula_abs("ryser", j) == pytest.approx(ryser_abs, rel=1e-13), n
+        assert oracle.formula_abs("nw", j) == pytest.approx(float(nw_abs), rel=1e-13), n
+        eye = np.eye(n)
+        assert oracle.formula_abs("ryser", eye) == pytest.approx(1.0, rel=1e-15)
+        assert oracle.formula_abs("nw", eye) == pytest.approx(1.0, rel=1e-15)
+    for n in (6, 10, 14):
+        a = S.haar_unitary(2 * n, 40 + n)[:n, :n]
+        p = abs(oracle.bbfg_gray(a)[0])
+        assert oracle.formula_abs("ryser", a) >= p
+        assert oracle.formula_abs("nw", a) >= p
 
 
 def test_ryser_and_bbfg_agree_on_unitary_submatrices():
