@@ -53,7 +53,7 @@ def parse():
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
-    ap.add_argument("--workload", default="cc", choices=["cc", "batch", "serving", "lossy"],
+    ap.add_argument("--workload", default="cc", choices=["cc", "batch", "serving", "lossy", "formulas"],
                     help="cc: the headline line; the others print their own line for the other configs")
     ap.add_argument("--chains", type=int, default=64)
     return ap.parse_args()
@@ -227,7 +227,10 @@ def run_mine(args):
     mode = bs.BS_MIXED if args.mode == "mixed" else bs.BS_FP64
     u, occ = S.config_cc(N_PHOTONS, M_MODES, SEED)
     ctx = bs.Context(local)
-    stream = torch.cuda.current_stream()
+    # a dedicated stream: on the legacy default stream the sampler cannot
+    # replay its captured graph and launches eagerly
+    stream = torch.cuda.Stream()
+    torch.cuda.set_stream(stream)
     ctx.set_stream(stream)
     fp64_rate, fp32_rate = ctx.measure_fma_rates()
     u_dev = torch.from_numpy(u).to("cuda")
@@ -460,6 +463,50 @@ def run_lossy(args):
     return 0
 
 
+def run_formulas(args):
+    """The comparison of Sec. 3.2 on this GPU: relative error (against the
+    double-double oracle) of the FP64 Gray walks of Eq. bbfg, Eq. ryser and
+    its Nijenhuis-Wilf form, plus MIXED BB/FG, on Haar-random n x n unitaries
+    (Fig. accuracy's inputs), and each formula's speed on one 30 x 30
+    permanent."""
+    import numpy as np
+    import oracle
+    import paper_2309_07027_gb300 as bs
+    import synthetic as S
+    ctx = bs.Context(0)
+    fp64_rate = ctx.measure_fma_rates()[0]
+    acc = {}
+    for n in (8, 12, 16, 20, 24):
+        worst = {"bbfg": 0.0, "ryser": 0.0, "nw": 0.0, "bbfg_mixed": 0.0}
+        for r in range(2):
+            a = S.haar_unitary(n, 1000 + 10 * n + r)
+            v, t = oracle.bbfg_gray(a)
+            ref = v + t
+            for f in ("bbfg", "ryser", "nw"):
+                worst[f] = max(worst[f], abs(ctx.perm_formula(a, f) - ref) / abs(ref))
+            worst["bbfg_mixed"] = max(worst["bbfg_mixed"], abs(ctx.perm(a, mode=bs.BS_MIXED) - ref) / abs(ref))
+        acc[str(n)] = worst
+    speed = {}
+    a = S.haar_unitary(30, 1030)
+    ctx.set_profiling(True)
+    for f in ("bbfg", "ryser", "nw"):
+        ctx.perm_formula(a, f)  # warm-up
+        ctx.reset_stats()
+        t0 = time.perf_counter()
+        ctx.perm_formula(a, f)
+        wall = time.perf_counter() - t0
+        st = ctx.stats()
+        secs = st["walk_ms"][0] / 1000.0
+        speed[f] = {"addends": int(st["addends"][0]), "walk_s": secs, "call_s": wall,
+                    "addends_per_s": st["addends"][0] / secs,
+                    "frac_of_fp64_peak": st["addend_flops"][0] / secs / (2.0 * fp64_rate)}
+    ctx.set_profiling(False)
+    print(json.dumps({"workload": "formulas_haar_n8_24_and_n30", "metric": "relative error; addends/s",
+                      "relative_error_max_of_2": acc, "speed_n30_fp64": speed,
+                      "reference": "oracle double-double BB/FG (Eq. bbfg)"}), flush=True)
+    return 0
+
+
 def main():
     args = parse()
     if args.impl == "reference":
@@ -472,6 +519,8 @@ def main():
         return run_serving(args)
     if args.workload == "lossy":
         return run_lossy(args)
+    if args.workload == "formulas":
+        return run_formulas(args)
     return run_mine(args)
 
 

@@ -154,6 +154,32 @@ int bs_perm_batch_dev(bs_ctx* ctx, int count, const bs_c128* A_packed_dev, const
 int bs_laplace_minors(bs_ctx* ctx, const bs_c128* A, int rows, int cols, int ld, const int* row_mult,
                       const int* col_mult, bs_mode mode, bs_c128* minors);
 
+/* Formula of a plain permanent for bs_perm_formula (Sec. 2): the
+ * generalized walk of this library in its binary case, or one of the two
+ * Gray-coded formulas the paper compares it with.
+ *   BS_FORMULA_BBFG   Eq. bbfg: delta_1 = +1, 2^(n-1) addends, prefactor
+ *                     2^(1-n); the same path as bs_perm with unit
+ *                     multiplicities.
+ *   BS_FORMULA_RYSER  Eq. ryser: column subsets S in Gray order, row sums
+ *                     sum_{j in S} a_ij updated by one column per step,
+ *                     2^n addends, prefactor (-1)^n.
+ *   BS_FORMULA_NW     Nijenhuis-Wilf form of Eq. ryser: row sums start at
+ *                     x_i = a_in - (a_i1 + ... + a_in) / 2 and walk subsets
+ *                     of the first n-1 columns, 2^(n-1) addends, prefactor
+ *                     (-1)^(n-1) 2. */
+typedef enum { BS_FORMULA_BBFG = 0, BS_FORMULA_RYSER = 1, BS_FORMULA_NW = 2 } bs_formula;
+
+/* Permanent of the n x n matrix A (row-major, leading dimension ld >= n) by
+ * `formula`, walked by the FP64 permanent kernel in double precision with
+ * double-double partial sums: the accuracy and speed comparison of Sec. 3.2
+ * (Fig. accuracy) on this GPU.  Only the packing of the start sums and the
+ * rows added per step, and the prefactor, differ between formulas.  n = 0
+ * gives 1.  out_lo (nullable) receives the double-double tail.
+ * Errors: BS_EINVAL (n < 0, n > BS_MAX_N, ld < n, NULL pointers, unknown
+ * formula), BS_ENOMEM, BS_ECUDA, BS_ETIMEOUT. */
+int bs_perm_formula(bs_ctx* ctx, const bs_c128* A, int n, int ld, bs_formula formula, bs_c128* out,
+                    bs_c128* out_lo);
+
 /* Allocation-free permanent, for callers that may not allocate device
  * memory when they need a result: code running while a CUDA graph is being
  * captured on its stream, hosts whose memory manager forbids allocations

@@ -26,6 +26,8 @@ __all__ = ["BS_FP64", "BS_MIXED", "BsError", "Context", "Server", "library_path"
 
 BS_FP64 = 0
 BS_MIXED = 1
+# formulas of bs_perm_formula (bs_formula)
+FORMULAS = {"bbfg": 0, "ryser": 1, "nw": 2}
 MAX_N = 48
 
 BS_OK, BS_EINVAL, BS_ENOMEM, BS_ECUDA, BS_ETIMEOUT, BS_ENODEV = 0, -1, -2, -3, -4, -5  # noqa: E501
@@ -84,6 +86,7 @@ def load():
         "bs_ctx_get_chunk_log2": ([vp, C.c_int], C.c_int),
         "bs_tune": ([vp, C.c_int, C.c_int, C.c_int, ip, dp], C.c_int),
         "bs_perm": ([vp, vp, C.c_int, C.c_int, C.c_int, ip, ip, C.c_int, vp, vp], C.c_int),
+        "bs_perm_formula": ([vp, vp, C.c_int, C.c_int, C.c_int, vp, vp], C.c_int),
         "bs_perm_batch": ([vp, C.c_int, vp, i64p, ip, ip, ip, i64p, i64p, C.c_int, vp], C.c_int),
         "bs_perm_batch_dev": ([vp, C.c_int, vp, i64p, ip, ip, ip, i64p, i64p, C.c_int, vp], C.c_int),
         "bs_laplace_minors": ([vp, vp, C.c_int, C.c_int, C.c_int, ip, ip, C.c_int, vp], C.c_int),
@@ -248,6 +251,20 @@ class Context:
         lo = np.zeros(1, dtype=np.complex128)
         _check(self._L.bs_perm(self._p, a.ctypes.data, R, K, K, _ip(M), _ip(N), int(mode), out.ctypes.data,
                                lo.ctypes.data), self._p)
+        return (complex(out[0]), complex(lo[0])) if with_tail else complex(out[0])
+
+    def perm_formula(self, a, formula: str = "bbfg", with_tail: bool = False):
+        """Permanent of a square matrix by Eq. bbfg ("bbfg"), Eq. ryser
+        ("ryser") or its Nijenhuis-Wilf form ("nw"), in FP64 (Sec. 3.2's
+        accuracy comparison)."""
+        a = _c128(a)
+        n = a.shape[0]
+        if a.shape != (n, n):
+            raise ValueError("perm_formula needs a square matrix")
+        out = np.zeros(1, dtype=np.complex128)
+        lo = np.zeros(1, dtype=np.complex128)
+        _check(self._L.bs_perm_formula(self._p, a.ctypes.data, n, n, FORMULAS[formula], out.ctypes.data,
+                                       lo.ctypes.data), self._p)
         return (complex(out[0]), complex(lo[0])) if with_tail else complex(out[0])
 
     def laplace_minors(self, a, row_mult=None, col_mult=None, mode: int = BS_FP64):

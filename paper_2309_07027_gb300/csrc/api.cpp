@@ -202,8 +202,8 @@ int run_jobs(bs_ctx* c, std::vector<JobIn>& ins, const double2* d_src, bs_mode m
         r.fp32 = (mode == BS_MIXED && bs_mixed_uses_fp32(in.p->radix, in.p->nrows, in.p->K, in.p->n)) ? 1 : 0;
         r.kind = in.p->kind;
         r.bucket = (in.p->K + 3) >> 2;
-        r.cpt = (r.fp32 && r.kind == BS_KIND_MINORS) ? 16 : 32;
-        r.log2L = bs_choose_log2L(in.p->C, r.cpt, c->log2max[r.fp32], BS_TARGET_TASKS_SINGLE);
+        r.cpt = bs_chunks_per_task(r.kind, r.fp32, in.p->K);
+        r.log2L = bs_choose_log2L(in.p->C, r.cpt, BS_LOG2L_MIN_SINGLE, c->log2max[r.fp32], BS_TARGET_TASKS_SINGLE);
         uint64_t per = (uint64_t)r.cpt << r.log2L;
         r.ntasks = (uint32_t)((in.p->C + per - 1) / per);
         r.ncols = r.kind == BS_KIND_PERM ? 1 : in.p->K;
@@ -257,6 +257,7 @@ int run_jobs(bs_ctx* c, std::vector<JobIn>& ins, const double2* d_src, bs_mode m
             jb.src_off = r.in.src_off;
             jb.src_ld = r.in.src_ld;
             jb.src_trans = p.trans ? 1 : 0;
+            jb.formula = p.formula;
             meta.insert(meta.end(), p.radix, p.radix + p.nrows);
             meta.insert(meta.end(), p.digit_src, p.digit_src + p.nrows);
             meta.insert(meta.end(), p.col_src, p.col_src + p.K);
@@ -370,12 +371,11 @@ void copy_matrix(bs_c128* dst, const bs_c128* A, int rows, int cols, int ld) {
     for (int r = 0; r < rows; ++r) std::memcpy(dst + (size_t)r * cols, A + (size_t)r * ld, sizeof(bs_c128) * cols);
 }
 
-int single_job(bs_ctx* c, const bs_c128* A, int rows, int cols, int ld, const int* M, const int* N, int kind,
-               bs_mode mode, IntPlan& p, std::vector<double2>& hi, std::vector<double2>& lo) {
-    if (!ok_ctx(c)) return BS_EINVAL;
-    if (mode != BS_FP64 && mode != BS_MIXED) return fail(BS_EINVAL, "unknown mode %d", (int)mode);
-    int rc = plan_job(rows, cols, M, N, kind, p);
-    if (rc) return rc;
+// One planned job on a rows x cols host matrix: upload, walk, reduce, read
+// back (hi, lo: one value per output column).
+int run_single(bs_ctx* c, const bs_c128* A, int rows, int cols, int ld, int kind, bs_mode mode, const IntPlan& p,
+               std::vector<double2>& hi, std::vector<double2>& lo) {
+    int rc;
     const int nout = kind == BS_KIND_PERM ? 1 : std::max(p.K, 1);
     hi.assign(nout, make_double2(0, 0));
     lo.assign(nout, make_double2(0, 0));
@@ -403,6 +403,15 @@ int single_job(bs_ctx* c, const bs_c128* A, int rows, int cols, int ld, const in
     BS_CUDA(cudaMemcpyAsync(hi.data(), c->out.p, nout * sizeof(double2), cudaMemcpyDeviceToHost, c->stream));
     BS_CUDA(cudaMemcpyAsync(lo.data(), c->out_lo.p, nout * sizeof(double2), cudaMemcpyDeviceToHost, c->stream));
     return sync_and_check(c);
+}
+
+int single_job(bs_ctx* c, const bs_c128* A, int rows, int cols, int ld, const int* M, const int* N, int kind,
+               bs_mode mode, IntPlan& p, std::vector<double2>& hi, std::vector<double2>& lo) {
+    if (!ok_ctx(c)) return BS_EINVAL;
+    if (mode != BS_FP64 && mode != BS_MIXED) return fail(BS_EINVAL, "unknown mode %d", (int)mode);
+    int rc = plan_job(rows, cols, M, N, kind, p);
+    if (rc) return rc;
+    return run_single(c, A, rows, cols, ld, kind, mode, p, hi, lo);
 }
 
 // ------------------------------------------------------------------ sampler
@@ -490,7 +499,7 @@ int sample_dev(bs_ctx* c, const double2* dU, int m_rows, int m_cols, int ld, con
     uint64_t cmax = n >= 2 ? (1ull << (n - 2)) : 1ull;
     uint64_t tasks_stride = 2 * BS_TARGET_TASKS_MANY + 1;
     tasks_stride = std::max<uint64_t>(tasks_stride, cmax / (32ull << c->log2max[0]) + 2);
-    if (mixed) tasks_stride = std::max<uint64_t>(tasks_stride, cmax / (16ull << c->log2max[1]) + 2);
+    if (mixed) tasks_stride = std::max<uint64_t>(tasks_stride, cmax / (8ull << c->log2max[1]) + 2);
     // a step-k job has <= k - 1 digit rows, K = k <= n columns, n' = k - 1
     const int64_t meta_stride = BS_META_SIZE(n, n, n), data_stride = (int64_t)n * BS_ROW_STRIDE(n);
     // chains per pass: bounded by the budget (or 2 GiB of partials per pass)
@@ -729,6 +738,34 @@ int bs_perm(bs_ctx* c, const bs_c128* A, int rows, int cols, int ld, const int* 
     IntPlan p;
     std::vector<double2> hi, lo;
     int rc = single_job(c, A, rows, cols, ld, row_mult, col_mult, BS_KIND_PERM, mode, p, hi, lo);
+    if (rc) return rc;
+    out->re = hi[0].x;
+    out->im = hi[0].y;
+    if (out_lo) {
+        out_lo->re = lo[0].x;
+        out_lo->im = lo[0].y;
+    }
+    return BS_OK;
+}
+
+int bs_perm_formula(bs_ctx* c, const bs_c128* A, int n, int ld, bs_formula formula, bs_c128* out, bs_c128* out_lo) {
+    if (!ok_ctx(c)) return BS_EINVAL;
+    if (!out) return fail(BS_EINVAL, "out is NULL");
+    if (n < 0 || n > BS_MAX_N) return fail(BS_EINVAL, "matrix size %d outside [0, %d]", n, BS_MAX_N);
+    IntPlan p;
+    int rc;
+    if (formula == BS_FORMULA_BBFG) {
+        int ones[BS_MAX_N];
+        for (int i = 0; i < n; ++i) ones[i] = 1;
+        rc = plan_job(n, n, ones, ones, BS_KIND_PERM, p);
+    } else if (formula == BS_FORMULA_RYSER || formula == BS_FORMULA_NW) {
+        rc = plan_formula(n, formula == BS_FORMULA_RYSER ? BS_JOB_RYSER : BS_JOB_NW, p);
+    } else {
+        return fail(BS_EINVAL, "unknown formula %d", (int)formula);
+    }
+    if (rc) return rc;
+    std::vector<double2> hi, lo;
+    rc = run_single(c, A, n, n, ld, BS_KIND_PERM, BS_FP64, p, hi, lo);
     if (rc) return rc;
     out->re = hi[0].x;
     out->im = hi[0].y;

@@ -47,7 +47,16 @@ struct bs_job {
     int64_t src_off;       // source matrix: element offset of entry (0, 0)
     int32_t src_ld;        // source leading dimension (complex elements)
     int32_t src_trans;     // 1: formula row r / column c read source (c, r)
+    int32_t formula;       // BS_JOB_BBFG (0), BS_JOB_RYSER or BS_JOB_NW (plain permanents, FP64)
+    int32_t reserved;
 };
+
+// Formula of a job (see bs_perm_formula).  Ryser and Nijenhuis-Wilf jobs
+// walk the columns of the matrix as binary digits with the rows as product
+// columns; the walk kernels are the same, only packing and prefactor differ.
+#define BS_JOB_BBFG 0
+#define BS_JOB_RYSER 1
+#define BS_JOB_NW 2
 
 // Integer metadata of a job, at meta_off (int32 units; meta_off even):
 //   radix[nrows]        digit radices R_j = M_j + 1 (binary digits first)
@@ -67,10 +76,13 @@ struct bs_job {
 #define BS_META_BINOM(jb) ((jb).meta_off + 2 * (jb).nrows + 2 * (jb).K + 2)
 #define BS_META_SIZE(nrows, K, n) (2 * (nrows) + 2 * (K) + 2 + 2 * ((nrows) + (n)))
 
-// Row stride of the packed matrix c0 / 2a: K rounded up to even, so FP32
-// rows start on 16-byte boundaries (column pairs load as one float4); the
-// pad column holds zeros.
-#define BS_ROW_STRIDE(K) ((((K) + 1) / 2) * 2)
+// Row stride of the packed matrix c0 / 2a: K rounded up to a multiple of 4
+// (the column bucket KB of the walk kernels), so FP32 rows are whole 16-byte
+// column pairs and every bucket column has a slot.  Pad columns are neutral:
+// rows hold zeros, and in FP32 jobs c0 holds 1, so a pad column sum stays
+// exactly 1 and leaves every product unchanged (FP64 jobs keep c0 = 0 there
+// and test columns against K instead).
+#define BS_ROW_STRIDE(K) ((((K) + 3) / 4) * 4)
 
 // Double-double complex partial: re = (re_hi, re_lo), im = (im_hi, im_lo).
 struct bs_zdd {

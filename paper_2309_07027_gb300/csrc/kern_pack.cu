@@ -61,13 +61,24 @@ __global__ void __launch_bounds__(kReduceBlock) reduce_kernel(const bs_job* __re
         __syncthreads();
     }
     if (threadIdx.x == 0) {
-        const int* colexp = meta + BS_META_COLEXP(jb);
-        int e = 1 - jb.n;
-        for (int c = 0; c < jb.K; ++c) e += colexp[c];
-        if (jb.kind == BS_KIND_MINORS) e -= colexp[col];
+        // prefactor: 2^(1-n) times the column scales (Eq. bbfgrepeated), or
+        // (-1)^n (Eq. ryser), or (-1)^(n-1) 2 (Nijenhuis-Wilf)
+        int e = 0;
+        double sgn = 1.0;
+        if (jb.formula == BS_JOB_BBFG) {
+            const int* colexp = meta + BS_META_COLEXP(jb);
+            e = 1 - jb.n;
+            for (int c = 0; c < jb.K; ++c) e += colexp[c];
+            if (jb.kind == BS_KIND_MINORS) e -= colexp[col];
+        } else if (jb.formula == BS_JOB_RYSER) {
+            sgn = (jb.n & 1) ? -1.0 : 1.0;
+        } else {
+            e = 1;
+            sgn = ((jb.n - 1) & 1) ? -1.0 : 1.0;
+        }
         ddv r = sre[0], i = sim[0];
-        out[jb.out_index + col] = make_double2(ldexp(r.hi, e), ldexp(i.hi, e));
-        if (out_lo) out_lo[jb.out_index + col] = make_double2(ldexp(r.lo, e), ldexp(i.lo, e));
+        out[jb.out_index + col] = make_double2(sgn * ldexp(r.hi, e), sgn * ldexp(i.hi, e));
+        if (out_lo) out_lo[jb.out_index + col] = make_double2(sgn * ldexp(r.lo, e), sgn * ldexp(i.lo, e));
     }
 }
 

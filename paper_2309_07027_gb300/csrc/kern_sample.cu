@@ -160,7 +160,7 @@ __global__ void cc_plan_kernel(const CcArgs* __restrict__ pa, int k) {
         // the chain's data slot holds data_stride complex doubles; an FP32
         // job indexes it in complex floats (twice as many, same bytes)
         jb.data_off = (int64_t)s * a.data_stride * (fp32 ? 2 : 1);
-        const int cpt = fp32 ? 16 : 32;
+        const int cpt = bs_chunks_per_task(BS_KIND_MINORS, fp32, k);
         const int log2max = fp32 ? a.log2max32 : a.log2max64;
         for (int j = 0; j < nrows; ++j) {
             meta[j] = drad[j];
@@ -171,7 +171,7 @@ __global__ void cc_plan_kernel(const CcArgs* __restrict__ pa, int k) {
         uint64_t C = 1;
         for (int j = 0; j < nrows; ++j) C *= (uint64_t)meta[j];
         jb.C = C;
-        jb.log2L = bs_choose_log2L(C, cpt, log2max, BS_TARGET_TASKS_MANY);
+        jb.log2L = bs_choose_log2L(C, cpt, BS_LOG2L_MIN_MANY, log2max, BS_TARGET_TASKS_MANY);
         jb.ntasks = (uint32_t)((C + ((uint64_t)cpt << jb.log2L) - 1) / ((uint64_t)cpt << jb.log2L));
         jb.task_begin = 0;
         a.jobs[s] = jb;

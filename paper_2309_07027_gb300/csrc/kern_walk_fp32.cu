@@ -1,10 +1,11 @@
 // FP32 ("mixed") walk kernels: column sums and products in single precision,
 // re-seeded from the matrix at every chunk start; addends summed in short
 // single-precision runs folded into float-float, chunk totals combined in
-// double-double.  Minors use lane pairs (16 chunks per warp task).  One
-// instantiation per column bucket.
+// double-double.  Column sums are packed pairs (walk_fp32.cuh).  Minors split
+// each chunk's column pairs over 2 or 4 lanes (16 or 8 chunks per warp task).
+// One instantiation per column bucket.
 #include "kernels.h"
-#include "walk.cuh"
+#include "walk_fp32.cuh"
 
 namespace bs {
 
@@ -16,7 +17,6 @@ template <int KB>
 __global__ void __launch_bounds__(kPermBlock) walk_fp32_perm_kernel(WalkArgs a) {
     const int lane = threadIdx.x & 31;
     const bs_job* __restrict__ jobs = a.jobs;
-    const cx<float>* __restrict__ data = static_cast<const cx<float>*>(a.data);
     const unsigned long long total = task_total(a);
     const int njobs = job_count(a);
     const unsigned long long deadline = warp_deadline(a.deadline_rel_ns);
@@ -28,19 +28,29 @@ __global__ void __launch_bounds__(kPermBlock) walk_fp32_perm_kernel(WalkArgs a) 
             if (lane == 0) atomicExch(a.status, BS_STATUS_BADJOB);
             continue;
         }
-        walk_task_perm<float, KB>(jb, data, a.meta + BS_META_RADIX(jb), a.partials, (uint32_t)(t - jb.task_begin) + jb.task_offset,
+        walk_task_perm_fp32<KB>(jb, a.data, a.meta + BS_META_RADIX(jb), a.partials, (uint32_t)(t - jb.task_begin) + jb.task_offset,
                                   lane);
     }
 }
 
+// Resident CTAs per SM the fused-minor kernel is compiled for: the most
+// that still needs no register spills (4-lane groups of up to 3 column pairs:
+// 96 registers, 5 CTAs; of 4 pairs: 128 registers, 4 CTAs); 2-lane groups
+// are left to the compiler.
 template <int KB>
-__global__ void __launch_bounds__(kMinorsBlock) walk_fp32_minors_kernel(WalkArgs a) {
+struct MinorsMinBlocks {
+    static constexpr int G = BS_MINORS_FP32_GROUP_KB(KB);
+    static constexpr int NP = KB / (2 * G);
+    static constexpr int value = G == 4 ? (NP <= 3 ? 5 : (NP == 4 ? 4 : 1)) : 1;
+};
+
+template <int KB>
+__global__ void __launch_bounds__(kMinorsBlock, MinorsMinBlocks<KB>::value) walk_fp32_minors_kernel(WalkArgs a) {
     extern __shared__ float4 smem_fp32[];
     const int lane = threadIdx.x & 31;
     const int stride = blockDim.x;
     float4* sm_ff = smem_fp32 + threadIdx.x;
     const bs_job* __restrict__ jobs = a.jobs;
-    const cx<float>* __restrict__ data = static_cast<const cx<float>*>(a.data);
     const unsigned long long total = task_total(a);
     const int njobs = job_count(a);
     const unsigned long long deadline = warp_deadline(a.deadline_rel_ns);
@@ -52,7 +62,7 @@ __global__ void __launch_bounds__(kMinorsBlock) walk_fp32_minors_kernel(WalkArgs
             if (lane == 0) atomicExch(a.status, BS_STATUS_BADJOB);
             continue;
         }
-        walk_task_minors_fp32<KB>(jb, data, a.meta + BS_META_RADIX(jb), a.partials, (uint32_t)(t - jb.task_begin) + jb.task_offset,
+        walk_task_minors_fp32<KB>(jb, a.data, a.meta + BS_META_RADIX(jb), a.partials, (uint32_t)(t - jb.task_begin) + jb.task_offset,
                                   lane, sm_ff, stride);
     }
 }
@@ -83,7 +93,7 @@ static cudaError_t run_perm(const WalkArgs& a, cudaStream_t s) {
 
 template <int KB>
 static cudaError_t run_minors(const WalkArgs& a, cudaStream_t s) {
-    size_t smem = (size_t)kMinorsBlock * (KB / 2) * sizeof(float4);
+    size_t smem = (size_t)kMinorsBlock * (KB / BS_MINORS_FP32_GROUP_KB(KB)) * sizeof(float4);
     cudaError_t e =
         cudaFuncSetAttribute(walk_fp32_minors_kernel<KB>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;

@@ -2,7 +2,10 @@
 // device planner): c0[col] = sum over rows of M_row * a_row,col (every
 // delta = +1), computed in double-double and rounded, and 2a[j][col] for every
 // digit row, in the job's working precision, rows of stride
-// KP = BS_ROW_STRIDE(K) with a zero pad column.  With normalize set, column col
+// KP = BS_ROW_STRIDE(K).  FP64 rows are plain complex doubles; FP32 rows are
+// column pairs {re(2p), re(2p+1), im(2p), im(2p+1)} (the packed layout of
+// walk_fp32.cuh).  Pad columns: zero rows, c0 = 1 in FP32 jobs (a neutral
+// factor) and 0 in FP64 jobs.  With normalize set, column col
 // is scaled by 2^-e (e: smallest integer with sum_rows M_row (|Re a| + |Im a|)
 // <= 2^e) and e is stored in colexp[col] for the reduce kernel.
 #pragma once
@@ -15,6 +18,13 @@ namespace bs {
 
 __device__ __forceinline__ double2 src_elem(const double2* __restrict__ src, const bs_job& jb, int r, int c) {
     return jb.src_trans ? src[jb.src_off + (int64_t)c * jb.src_ld + r] : src[jb.src_off + (int64_t)r * jb.src_ld + c];
+}
+
+// Element (row r, column col) of an FP32 job's packed rows.
+__device__ __forceinline__ void put_f32(void* data, const bs_job& jb, int KP, int r, int col, float re, float im) {
+    float* q = static_cast<float*>(data) + 2 * (jb.data_off + (int64_t)r * KP) + 4 * (col >> 1) + (col & 1);
+    q[0] = re;
+    q[2] = im;
 }
 
 __device__ __forceinline__ void pack_job(const bs_job& jb, const double2* __restrict__ src, int* __restrict__ meta,
@@ -32,11 +42,44 @@ __device__ __forceinline__ void pack_job(const bs_job& jb, const double2* __rest
             for (int d = 0; d < radix[j]; ++d) binom[at++] = bs_binom(radix[j] - 1, d);
     }
     const int KP = BS_ROW_STRIDE(jb.K);
+    if (jb.formula != BS_JOB_BBFG) {
+        // Ryser / Nijenhuis-Wilf (FP64): product column col is matrix row
+        // sc; digit j is matrix column dsrc[j], added with +1 when it enters
+        // the subset, so the packed row is -a (the walk subtracts rows of
+        // digits whose Delta is 1).  Start sums: 0 (Ryser) or
+        // x = a_(sc, n-1) - (sum_j a_(sc, j)) / 2 (Nijenhuis-Wilf).
+        cx<double>* out = static_cast<cx<double>*>(data) + jb.data_off;
+        for (int col = tid; col < KP; col += nthreads) {
+            if (col >= jb.K) {
+                for (int j = 0; j <= jb.nrows; ++j) out[(size_t)j * KP + col] = cx<double>{0.0, 0.0};
+                continue;
+            }
+            colexp[col] = 0;
+            const int sc = csrc[col];
+            ddv sre = {0.0, 0.0}, sim = {0.0, 0.0};
+            if (jb.formula == BS_JOB_NW) {
+                for (int j = 0; j < jb.n; ++j) {
+                    const double2 d = src_elem(src, jb, j, sc);
+                    sre = dd_add_d(sre, -0.5 * d.x);
+                    sim = dd_add_d(sim, -0.5 * d.y);
+                }
+                const double2 last = src_elem(src, jb, jb.n - 1, sc);
+                sre = dd_add_d(sre, last.x);
+                sim = dd_add_d(sim, last.y);
+            }
+            out[col] = cx<double>{sre.hi, sim.hi};
+            for (int j = 0; j < jb.nrows; ++j) {
+                const double2 d = src_elem(src, jb, dsrc[j], sc);
+                out[(size_t)(1 + j) * KP + col] = cx<double>{-d.x, -d.y};
+            }
+        }
+        return;
+    }
     for (int col = tid; col < KP; col += nthreads) {
-        if (col >= jb.K) {  // pad column: zeros
+        if (col >= jb.K) {  // pad column
             if (fp32) {
-                cx<float>* out = static_cast<cx<float>*>(data) + jb.data_off;
-                for (int j = 0; j <= jb.nrows; ++j) out[(size_t)j * KP + col] = cx<float>{0.f, 0.f};
+                put_f32(data, jb, KP, 0, col, 1.f, 0.f);
+                for (int j = 1; j <= jb.nrows; ++j) put_f32(data, jb, KP, j, col, 0.f, 0.f);
             } else {
                 cx<double>* out = static_cast<cx<double>*>(data) + jb.data_off;
                 for (int j = 0; j <= jb.nrows; ++j) out[(size_t)j * KP + col] = cx<double>{0.0, 0.0};
@@ -68,11 +111,10 @@ __device__ __forceinline__ void pack_job(const bs_job& jb, const double2* __rest
             sim = dd_add_d(dd_add_d(sim, pim), eim);
         }
         if (fp32) {
-            cx<float>* out = static_cast<cx<float>*>(data) + jb.data_off;
-            out[col] = cx<float>{(float)sre.hi, (float)sim.hi};
+            put_f32(data, jb, KP, 0, col, (float)sre.hi, (float)sim.hi);
             for (int j = 0; j < jb.nrows; ++j) {
                 double2 d = src_elem(src, jb, dsrc[j], sc);
-                out[(size_t)(1 + j) * KP + col] = cx<float>{(float)ldexp(d.x, 1 - e), (float)ldexp(d.y, 1 - e)};
+                put_f32(data, jb, KP, 1 + j, col, (float)ldexp(d.x, 1 - e), (float)ldexp(d.y, 1 - e));
             }
         } else {
             cx<double>* out = static_cast<cx<double>*>(data) + jb.data_off;

@@ -36,6 +36,31 @@ uint64_t pin_cost(const int* m, int cnt) {
     return c;
 }
 
+int plan_formula(int n, int formula, IntPlan& p) {
+    if (n < 0 || n > BS_MAX_N) return fail(BS_EINVAL, "matrix size %d outside [0, %d]", n, BS_MAX_N);
+    if (formula != BS_JOB_RYSER && formula != BS_JOB_NW) return fail(BS_EINVAL, "unknown formula %d", formula);
+    p = IntPlan();
+    p.kind = BS_KIND_PERM;
+    p.formula = formula;
+    p.n = n;
+    if (n == 0) {
+        p.trivial = true;
+        return BS_OK;
+    }
+    p.K = n;
+    p.nrows = formula == BS_JOB_RYSER ? n : n - 1;
+    p.nbin = p.nrows;
+    p.C = 1ull << p.nrows;
+    p.trans = true;
+    p.pinned_src = 0;  // unused: the start sums do not come from a pinned row
+    for (int j = 0; j < p.nrows; ++j) {
+        p.radix[j] = 2;
+        p.digit_src[j] = j;
+    }
+    for (int i = 0; i < n; ++i) p.col_src[i] = i;
+    return BS_OK;
+}
+
 // Canonicalisation without heap allocation (fixed capacities: at most
 // BS_MAX_N photons, so at most BS_MAX_N occupied rows or columns).
 int plan_job(int rows, int cols, const int* M, const int* N, int kind, IntPlan& p) {

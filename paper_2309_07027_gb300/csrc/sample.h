@@ -7,23 +7,39 @@
 #include <math.h>
 
 // Chunk length exponent of a job with C addends whose warp tasks cover `cpt`
-// chunks: aim at about `target` tasks per job, never below 2^6 addends per
-// chunk (decode cost) nor above 2^log2max (the re-seed interval).  Depends
-// only on (C, cpt, log2max, target), so a job is cut the same way alone or
-// inside any batch that uses the same target.  Jobs planned one call at a
-// time use BS_TARGET_TASKS_SINGLE (several tasks per resident warp, so one
-// job fills the GPU without a ragged tail); the sampler and the server, which always run many jobs together,
-// use BS_TARGET_TASKS_MANY (longer chunks, fewer tasks).
-#define BS_TARGET_TASKS_SINGLE 8192
+// chunks: aim at about `target` tasks per job, never below 2^log2min addends
+// per chunk (decode cost) nor above 2^log2max (the re-seed interval).
+// Depends only on (C, cpt, log2min, log2max, target), so a job is cut the
+// same way alone or inside any batch that uses the same rule.  Jobs planned
+// one call at a time use BS_TARGET_TASKS_SINGLE (several tasks per resident
+// warp, so one job fills the GPU without a ragged tail) and chunks of at
+// least 2^6.  The sampler and the server, which always run many jobs
+// together, use BS_TARGET_TASKS_MANY (longer chunks, fewer tasks) with a
+// floor of 2^3: their small jobs (early steps, heavy-collision chains sent to
+// FP64) are latency-bound, and short chunks spread them over more warps.
+#define BS_TARGET_TASKS_SINGLE 32768
 #define BS_TARGET_TASKS_MANY 64
-BS_HD int bs_choose_log2L(uint64_t C, int cpt, int log2max, int target) {
+#define BS_LOG2L_MIN_SINGLE 6
+#define BS_LOG2L_MIN_MANY 3
+BS_HD int bs_choose_log2L(uint64_t C, int cpt, int log2min, int log2max, int target) {
     uint64_t per = C / ((uint64_t)cpt * (uint64_t)target);
     int l = 0;
     while ((2ull << l) <= per) ++l;  // floor(log2(per)) for per >= 1
     if (per == 0) l = 0;
-    if (l < 6) l = 6;
+    if (l < log2min) l = log2min;
     if (l > log2max) l = log2max;
     return l;
+}
+
+// Lanes that walk one chunk together in the FP32 fused-minor kernel (each
+// owns a contiguous group of the bucket's column pairs): 4 for widths of a
+// multiple of 8 columns from 24 on, else 2, so every lane holds whole column
+// pairs.  A warp task of that kernel covers 32 / G chunks; every other kernel
+// gives each lane its own chunk (32 per task).
+#define BS_MINORS_FP32_GROUP_KB(KB) (((KB) % 8 == 0 && (KB) >= 24) ? 4 : 2)
+BS_HD int bs_minors_fp32_group(int K) { return BS_MINORS_FP32_GROUP_KB((K + 3) & ~3); }
+BS_HD int bs_chunks_per_task(int kind, int fp32, int K) {
+    return (fp32 && kind == BS_KIND_MINORS) ? 32 / bs_minors_fp32_group(K) : 32;
 }
 
 // Algorithmic flops of one addend (the roofline numerator):

@@ -562,8 +562,8 @@ int64_t bs_server_submit(bs_server* s, int kind, const bs_c128* A, int rows, int
     r->mat.resize((size_t)rows * cols);
     for (int i = 0; i < rows; ++i) std::memcpy(&r->mat[(size_t)i * cols], A + (size_t)i * ld, sizeof(bs_c128) * cols);
     r->fp32 = (s->mode == BS_MIXED && bs_mixed_uses_fp32(r->plan.radix, r->plan.nrows, r->plan.K, r->plan.n)) ? 1 : 0;
-    r->cpt = (r->fp32 && r->kind == BS_KIND_MINORS) ? 16 : 32;
-    r->log2L = bs_choose_log2L(r->plan.C, r->cpt, 12, BS_TARGET_TASKS_MANY);
+    r->cpt = bs_chunks_per_task(r->kind, r->fp32, r->plan.K);
+    r->log2L = bs_choose_log2L(r->plan.C, r->cpt, BS_LOG2L_MIN_MANY, 12, BS_TARGET_TASKS_MANY);
     const uint64_t per = (uint64_t)r->cpt << r->log2L;
     r->ntasks = (uint32_t)((r->plan.C + per - 1) / per);
     r->ncols = r->kind == BS_KIND_PERM ? 1 : r->plan.K;

@@ -178,16 +178,19 @@ __device__ __forceinline__ double unit_sign<double>(uint32_t neg) { return unit_
 // ones of s: the digit that moves at step s -> s + 1 is t = ctz(s + 1) < 12
 // when t < nbin (a binary flip, 32-bit arithmetic only), and otherwise every
 // binary digit is saturated and a repeated-row digit moves (general step).
+// The stepper itself holds only scalars (kept in registers); the full Gray
+// state g, whose repeated-row digit arrays are indexed at run time and so
+// live in local memory, is a separate object that only the general step
+// touches.
 struct ChunkStepper {
-    bs_gray g;
     uint64_t i0;
+    const uint64_t* binom;
     uint32_t dlo;   // Delta bits of binary digits 0..31
     int parity0;    // parity at the chunk start
     int nbin;
 
-    const uint64_t* binom;
-
-    __device__ __forceinline__ void init(uint64_t start, int nb, int nrows, const int* radix, const uint64_t* tab) {
+    __device__ __forceinline__ void init(bs_gray& g, uint64_t start, int nb, int nrows, const int* radix,
+                                         const uint64_t* tab) {
         binom = tab;
         bs_gray_decode(g, start, nb, nrows, radix, tab);
         i0 = start;
@@ -199,7 +202,7 @@ struct ChunkStepper {
     // when the column sums move by -2a_row (Delta rises), 0 for +2a_row;
     // *wch is 1 when the binomial weight changed (then g.w, g.parity are
     // current).
-    __device__ __forceinline__ int step(uint32_t s, const int* radix, uint32_t* neg, int* wch) {
+    __device__ __forceinline__ int step(bs_gray& g, uint32_t s, const int* radix, uint32_t* neg, int* wch) {
         const int t = __ffs((int)(s + 1u)) - 1;
         if (t < nbin) {
             const uint32_t was = (dlo >> t) & 1u;
@@ -218,12 +221,13 @@ struct ChunkStepper {
     }
 };
 
-// Padded row stride of the packed matrix: an even number of columns, so
-// FP32 rows load as 16-byte column pairs.
+// Padded row stride of the packed matrix: the bucket width KB (a multiple
+// of 4), so FP32 rows are whole 16-byte column pairs.
 __device__ __forceinline__ int row_stride(int K) { return BS_ROW_STRIDE(K); }
 
 // Column `col` of a bucket KB is live when col < K; K >= KB - 3 always, so
-// only the last three columns of a bucket need a runtime test.
+// only the last three columns of a bucket need a runtime test.  (The FP32
+// kernels need none: their pad columns are neutral, see walk_fp32.cuh.)
 #define BS_LIVE(col) ((col) < KB - 3 || (col) < K)
 
 // Seed the column sums of the decoded state: c = c0 - sum_j Delta_j * 2a_j
@@ -267,8 +271,7 @@ __device__ __forceinline__ cx<double> ldg_cx(const cx<double>* p) {
     return cx<double>{v.x, v.y};
 }
 
-// c_col += cf * row_col for the live columns (FP64: one 16-byte load per
-// column; FP32: one 16-byte load per column pair, rows padded to even K).
+// c_col += cf * row_col for the live columns (one 16-byte load per column).
 template <int KB>
 __device__ __forceinline__ void update_columns(cx<double> (&c)[KB], const cx<double>* __restrict__ row, double cf,
                                                int K) {
@@ -280,24 +283,6 @@ __device__ __forceinline__ void update_columns(cx<double> (&c)[KB], const cx<dou
             c[col].im = bfma(cf, a.im, c[col].im);
         }
 }
-template <int KB>
-__device__ __forceinline__ void update_columns(cx<float> (&c)[KB], const cx<float>* __restrict__ row, float cf,
-                                               int K) {
-#pragma unroll
-    for (int p = 0; p < KB / 2; ++p) {
-        const int col = 2 * p;
-        if (BS_LIVE(col)) {
-            const float4 v = __ldg(reinterpret_cast<const float4*>(row) + p);
-            c[col].re = bfma(cf, v.x, c[col].re);
-            c[col].im = bfma(cf, v.y, c[col].im);
-            if (BS_LIVE(col + 1)) {
-                c[col + 1].re = bfma(cf, v.z, c[col + 1].re);
-                c[col + 1].im = bfma(cf, v.w, c[col + 1].im);
-            }
-        }
-    }
-}
-
 // prod_col c_col with two interleaved chains (even / odd columns).
 template <typename T, int KB>
 __device__ __forceinline__ cx<T> product_columns(const cx<T> (&c)[KB], int K) {
@@ -350,11 +335,12 @@ __device__ void walk_task_perm(const bs_job& jb, const cx<T>* __restrict__ data,
     if (i0 < jb.C) {
         const uint64_t rem = jb.C - i0;
         const uint32_t len = (uint32_t)(rem < (1ull << jb.log2L) ? rem : (1ull << jb.log2L));
+        bs_gray g;
         ChunkStepper st;
-        st.init(i0, jb.nbin, jb.nrows, radix, reinterpret_cast<const uint64_t*>(radix + (BS_META_BINOM(jb) - jb.meta_off)));
+        st.init(g, i0, jb.nbin, jb.nrows, radix, reinterpret_cast<const uint64_t*>(radix + (BS_META_BINOM(jb) - jb.meta_off)));
         cx<T> c[KB];
-        seed_columns<T, KB>(c, st.g, c0, a2, K, KP, jb.nbin, jb.nrows);
-        T ws = signed_weight<T>(st.g.w, st.g.parity);
+        seed_columns<T, KB>(c, g, c0, a2, K, KP, jb.nbin, jb.nrows);
+        T ws = signed_weight<T>(g.w, g.parity);
         cx<T> acc = {(T)0, (T)0};
         uint32_t run = 0;
         for (uint32_t s = 0;; ++s) {
@@ -376,8 +362,8 @@ __device__ void walk_task_perm(const bs_job& jb, const cx<T>* __restrict__ data,
             if (s + 1 == len) break;
             uint32_t neg;
             int wch;
-            const int row = st.step(s, radix, &neg, &wch);
-            ws = wch ? signed_weight<T>(st.g.w, st.g.parity) : flip_sign(ws);
+            const int row = st.step(g, s, radix, &neg, &wch);
+            ws = wch ? signed_weight<T>(g.w, g.parity) : flip_sign(ws);
             update_columns<KB>(c, a2 + (size_t)row * KP, unit_sign<T>(neg), K);
         }
         if constexpr (F64) {
@@ -424,11 +410,12 @@ __device__ void walk_task_minors_fp64(const bs_job& jb, const cx<double>* __rest
     if (i0 < jb.C) {
         const uint64_t rem = jb.C - i0;
         const uint32_t len = (uint32_t)(rem < (1ull << jb.log2L) ? rem : (1ull << jb.log2L));
+        bs_gray g;
         ChunkStepper st;
-        st.init(i0, jb.nbin, jb.nrows, radix, reinterpret_cast<const uint64_t*>(radix + (BS_META_BINOM(jb) - jb.meta_off)));
+        st.init(g, i0, jb.nbin, jb.nrows, radix, reinterpret_cast<const uint64_t*>(radix + (BS_META_BINOM(jb) - jb.meta_off)));
         cx<double> c[KB];
-        seed_columns<double, KB>(c, st.g, c0, a2, K, KP, jb.nbin, jb.nrows);
-        double ws = signed_weight<double>(st.g.w, st.g.parity);
+        seed_columns<double, KB>(c, g, c0, a2, K, KP, jb.nbin, jb.nrows);
+        double ws = signed_weight<double>(g.w, g.parity);
         for (uint32_t s = 0;; ++s) {
             // suffix pass: suf[l] = ws * prod_{col > l} c_col
             cx<double> sfx = {ws, 0.0};
@@ -471,178 +458,26 @@ __device__ void walk_task_minors_fp64(const bs_job& jb, const cx<double>* __rest
             if (s + 1 == len) break;
             uint32_t neg;
             int wch;
-            const int row = st.step(s, radix, &neg, &wch);
-            ws = wch ? signed_weight<double>(st.g.w, st.g.parity) : flip_sign(ws);
+            const int row = st.step(g, s, radix, &neg, &wch);
+            ws = wch ? signed_weight<double>(g.w, g.parity) : flip_sign(ws);
             update_columns<KB>(c, a2 + (size_t)row * KP, unit_sign_d(neg), K);
         }
     }
+    // The 32 chunk sums of the task are plain-double running sums, so they
+    // are combined in plain double (fixed butterfly order, about 10 FP64
+    // operations per column instead of about 200 for a double-double
+    // combine); the partials of different tasks are summed in double-double
+    // by the reduce kernel.
     for (int col = 0; col < K; ++col) {
         cx<double> a = sm_acc[col * stride];
-        ddv re = {a.re, 0.0}, im = {a.im, 0.0};
-        warp_reduce_zdd(re, im);
-        if (lane == 0) store_partial(partials + jb.partial_off + (int64_t)local * K + col, re, im);
-    }
-}
-
-// ---------------------------------------------------------------- one task: minors, FP32
-// Two lanes share one chunk: lane (2p + h) owns columns [h*H, h*H + H),
-// H = KB/2.  Per addend each lane
-//   1. forms suffix products over its own columns, starting from 1; the
-//      last one is Q_own = prod of its own columns,
-//   2. swaps Q with its partner (one shuffle of a complex value),
-//   3. runs the prefix pass over its own columns starting from
-//      X = (+-W) * Q_partner:  acc[l] += X * prefix_l * suffix_l.
-// Both lanes run the same instructions, the arithmetic equals the one-lane
-// form, and each lane holds only H column sums, suffixes and accumulators.
-// A warp task therefore covers 16 chunks.  Float-float fold targets live in
-// shared memory, [col][thread]; the cross-lane sums stay in float-float.
-template <int KB>
-__device__ void walk_task_minors_fp32(const bs_job& jb, const cx<float>* __restrict__ data,
-                                      const int* __restrict__ radix, bs_zdd* __restrict__ partials, uint32_t local,
-                                      int lane, float4* __restrict__ sm_ff, int stride) {
-    constexpr uint32_t FOLD = 32;
-    constexpr int H = KB / 2;
-    const int K = jb.K;
-    const int KP = row_stride(K);
-    const int half = lane & 1;
-    const int cbase = half * H;
-    // live columns of this lane: t < KH (only the last 3 of a half can die)
-    const int KH = min(H, max(K - cbase, 0));
-    const unsigned pair_mask = 3u << (lane & ~1);
-#define BS_LIVEH(t) ((t) < H - 3 || (t) < KH)
-    const cx<float>* c0 = data + jb.data_off;
-    const cx<float>* a2 = c0 + KP;
 #pragma unroll
-    for (int t = 0; t < H; ++t)
-        if (BS_LIVEH(t)) sm_ff[t * stride] = make_float4(0.f, 0.f, 0.f, 0.f);
-    const uint64_t i0 = ((uint64_t)local * 16u + (uint64_t)(lane >> 1)) << jb.log2L;
-    // both lanes of a pair take the same branch
-    if (i0 < jb.C) {
-        const uint64_t rem = jb.C - i0;
-        const uint32_t len = (uint32_t)(rem < (1ull << jb.log2L) ? rem : (1ull << jb.log2L));
-        ChunkStepper st;
-        st.init(i0, jb.nbin, jb.nrows, radix, reinterpret_cast<const uint64_t*>(radix + (BS_META_BINOM(jb) - jb.meta_off)));
-        cx<float> c[H];
-        {
-            // seed own columns: c = c0 - sum_j Delta_j 2a_j
-#pragma unroll
-            for (int t = 0; t < H; ++t)
-                if (BS_LIVEH(t)) c[t] = c0[cbase + t];
-            uint64_t bits = st.g.dbin;
-            while (bits) {
-                int j = bs_ctz64(bits);
-                bits &= bits - 1;
-                const cx<float>* row = a2 + (size_t)j * KP + cbase;
-#pragma unroll
-                for (int t = 0; t < H; ++t)
-                    if (BS_LIVEH(t)) {
-                        c[t].re -= row[t].re;
-                        c[t].im -= row[t].im;
-                    }
-            }
-            for (int j = jb.nbin; j < jb.nrows; ++j) {
-                int d = st.g.del[j];
-                if (d == 0) continue;
-                float fd = (float)(-d);
-                const cx<float>* row = a2 + (size_t)j * KP + cbase;
-#pragma unroll
-                for (int t = 0; t < H; ++t)
-                    if (BS_LIVEH(t)) {
-                        c[t].re = bfma(fd, row[t].re, c[t].re);
-                        c[t].im = bfma(fd, row[t].im, c[t].im);
-                    }
-            }
+        for (int off = 16; off > 0; off >>= 1) {
+            a.re += __shfl_down_sync(0xffffffffu, a.re, off);
+            a.im += __shfl_down_sync(0xffffffffu, a.im, off);
         }
-        float ws = signed_weight<float>(st.g.w, st.g.parity);
-        cx<float> acc[H];
-#pragma unroll
-        for (int t = 0; t < H; ++t) acc[t] = cx<float>{0.f, 0.f};
-        uint32_t run = 0;
-        for (uint32_t s = 0;; ++s) {
-            // 1. suffix products over own columns, from 1
-            cx<float> suf[H];
-            cx<float> sfx = {1.f, 0.f};
-            bool first = true;
-#pragma unroll
-            for (int t = H - 1; t >= 0; --t)
-                if (BS_LIVEH(t)) {
-                    suf[t] = sfx;
-                    sfx = first ? c[t] : cmul(sfx, c[t]);
-                    first = false;
-                }
-            // a lane with no live columns contributes Q = 1
-            // 2. swap Q with the partner lane (pairs leave the loop at
-            //    different steps: only the pair syncs)
-            cx<float> q;
-            q.re = __shfl_xor_sync(pair_mask, sfx.re, 1);
-            q.im = __shfl_xor_sync(pair_mask, sfx.im, 1);
-            // 3. prefix pass from X = ws * Q_partner
-            cx<float> pre = {ws * q.re, ws * q.im};
-#pragma unroll
-            for (int t = 0; t < H; ++t)
-                if (BS_LIVEH(t)) {
-                    acc[t].re = bfma(pre.re, suf[t].re, acc[t].re);
-                    acc[t].re = bfma(-pre.im, suf[t].im, acc[t].re);
-                    acc[t].im = bfma(pre.re, suf[t].im, acc[t].im);
-                    acc[t].im = bfma(pre.im, suf[t].re, acc[t].im);
-                    if (t + 1 < H - 3 || t + 1 < KH) pre = cmul(pre, c[t]);
-                }
-            if (++run == FOLD) {
-                run = 0;
-#pragma unroll
-                for (int t = 0; t < H; ++t)
-                    if (BS_LIVEH(t)) {
-                        float4 f = sm_ff[t * stride];
-                        ffv re = {f.x, f.y}, im = {f.z, f.w};
-                        re = ff_add_f(re, acc[t].re);
-                        im = ff_add_f(im, acc[t].im);
-                        sm_ff[t * stride] = make_float4(re.hi, re.lo, im.hi, im.lo);
-                        acc[t] = cx<float>{0.f, 0.f};
-                    }
-            }
-            if (s + 1 == len) break;
-            uint32_t neg;
-            int wch;
-            const int row = st.step(s, radix, &neg, &wch);
-            ws = wch ? signed_weight<float>(st.g.w, st.g.parity) : flip_sign(ws);
-            const float4* rp = reinterpret_cast<const float4*>(a2 + (size_t)row * KP + cbase);
-            const float cf = unit_sign_f(neg);
-#pragma unroll
-            for (int p = 0; p < H / 2; ++p)
-                if (BS_LIVEH(2 * p)) {
-                    const float4 v = __ldg(rp + p);
-                    c[2 * p].re = bfma(cf, v.x, c[2 * p].re);
-                    c[2 * p].im = bfma(cf, v.y, c[2 * p].im);
-                    if (BS_LIVEH(2 * p + 1)) {
-                        c[2 * p + 1].re = bfma(cf, v.z, c[2 * p + 1].re);
-                        c[2 * p + 1].im = bfma(cf, v.w, c[2 * p + 1].im);
-                    }
-                }
-        }
-#pragma unroll
-        for (int t = 0; t < H; ++t)
-            if (BS_LIVEH(t)) {
-                float4 f = sm_ff[t * stride];
-                ffv re = {f.x, f.y}, im = {f.z, f.w};
-                re = ff_add_f(re, acc[t].re);
-                im = ff_add_f(im, acc[t].im);
-                sm_ff[t * stride] = make_float4(re.hi, re.lo, im.hi, im.lo);
-            }
+        if (lane == 0)
+            store_partial(partials + jb.partial_off + (int64_t)local * K + col, ddv{a.re, 0.0}, ddv{a.im, 0.0});
     }
-    // reduce over the 16 pairs in float-float: lanes of equal parity; lane 0
-    // / lane 1 end with the sums of columns [0, H) / [H, 2H)
-    for (int t = 0; t < H; ++t) {
-        const float4 f = (t < KH) ? sm_ff[t * stride] : make_float4(0.f, 0.f, 0.f, 0.f);
-        ffv re = {f.x, f.y}, im = {f.z, f.w};
-#pragma unroll
-        for (int off = 16; off > 1; off >>= 1) {
-            re = ff_add(re, shfl_down_ff(re, off));
-            im = ff_add(im, shfl_down_ff(im, off));
-        }
-        if (lane < 2 && t < KH)
-            store_partial(partials + jb.partial_off + (int64_t)local * K + cbase + t, dd_from_ff(re), dd_from_ff(im));
-    }
-#undef BS_LIVEH
 }
 
 #undef BS_LIVE
