@@ -279,8 +279,15 @@ def run_mine(args):
     fl = st["addend_flops"][p]
     peak = 2.0 * (fp32_rate if p == 1 else fp64_rate) / 1e12
     achieved = fl / walk_s / 1e12 if walk_s > 0 else 0.0
+    # DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) of the
+    # k = 30 FP32 fused-minor launch, from an ncu capture of 32 chains of
+    # this workload (1.42 MB + 0.24 MB), scaled to the step's chains: job
+    # data, metadata and task partials grow with the number of chains.  The
+    # kernel is compute-bound; the figure shows that it re-reads nothing.
+    traffic = 1.662e6 * S_ / 32 if p == 1 else None
     roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-            "frac": achieved / peak if peak else None, "traffic": None,
+            "frac": achieved / peak if peak else None, "traffic": traffic,
+            "traffic_launch": "the k = 30 launch (ncu capture of 32 chains, scaled)" if p == 1 else None,
             "kernel": "walk_fp32_minors_kernel" if p == 1 else "walk_fp64_minors_kernel",
             "peak_source": "measured on this GPU by bs_measure_fma_rates (2 flops per lane-FMA)",
             "walk_ms_per_step": st["walk_ms"][p] / args.steps, "walk_launches": int(st["timed_launches"][p]),
