@@ -76,12 +76,13 @@ struct bs_job {
 #define BS_META_BINOM(jb) ((jb).meta_off + 2 * (jb).nrows + 2 * (jb).K + 2)
 #define BS_META_SIZE(nrows, K, n) (2 * (nrows) + 2 * (K) + 2 + 2 * ((nrows) + (n)))
 
-// Row stride of the packed matrix c0 / 2a: K rounded up to a multiple of 4
-// (the column bucket KB of the walk kernels), so FP32 rows are whole 16-byte
-// column pairs and every bucket column has a slot.  Pad columns are neutral:
-// rows hold zeros, and in FP32 jobs c0 holds 1, so a pad column sum stays
-// exactly 1 and leaves every product unchanged (FP64 jobs keep c0 = 0 there
-// and test columns against K instead).
+// Row stride of the packed matrix c0 / 2a: K rounded up to a multiple of 4,
+// the width KB of the bucket kernel that walks the job (inside a kernel the
+// stride is the compile-time KB), so FP32 rows are whole 16-byte column pairs
+// and every bucket column has a slot.  Pad columns are neutral: rows hold
+// zeros, and in FP32 jobs c0 holds 1, so a pad column sum stays exactly 1 and
+// leaves every product unchanged (FP64 jobs keep c0 = 0 there and test
+// columns against K instead).
 #define BS_ROW_STRIDE(K) ((((K) + 3) / 4) * 4)
 
 // Double-double complex partial: re = (re_hi, re_lo), im = (im_hi, im_lo).

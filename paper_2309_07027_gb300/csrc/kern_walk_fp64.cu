@@ -26,7 +26,7 @@ __global__ void __launch_bounds__(kPermBlock) walk_fp64_perm_kernel(WalkArgs a) 
             if (lane == 0) atomicExch(a.status, BS_STATUS_BADJOB);
             continue;
         }
-        walk_task_perm<double, KB>(jb, data, a.meta + BS_META_RADIX(jb), a.partials,
+        walk_task_perm_fp64<KB>(jb, data, a.meta + BS_META_RADIX(jb), a.partials,
                                    (uint32_t)(t - jb.task_begin) + jb.task_offset, lane);
     }
 }

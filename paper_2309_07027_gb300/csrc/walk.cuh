@@ -166,12 +166,6 @@ __device__ __forceinline__ float unit_sign_f(uint32_t neg) { return __int_as_flo
 __device__ __forceinline__ double unit_sign_d(uint32_t neg) {
     return __longlong_as_double((long long)(0x3ff0000000000000ull | ((unsigned long long)neg << 63)));
 }
-template <typename T>
-__device__ __forceinline__ T unit_sign(uint32_t neg);
-template <>
-__device__ __forceinline__ float unit_sign<float>(uint32_t neg) { return unit_sign_f(neg); }
-template <>
-__device__ __forceinline__ double unit_sign<double>(uint32_t neg) { return unit_sign_d(neg); }
 
 // In-chunk stepper.  A chunk starts at a multiple i0 of L = 2^log2L and
 // takes fewer than L steps, so the index i0 + s has exactly the trailing
@@ -221,9 +215,11 @@ struct ChunkStepper {
     }
 };
 
-// Padded row stride of the packed matrix: the bucket width KB (a multiple
-// of 4), so FP32 rows are whole 16-byte column pairs.
-__device__ __forceinline__ int row_stride(int K) { return BS_ROW_STRIDE(K); }
+// The packed rows of a job with K columns have stride BS_ROW_STRIDE(K), the
+// width KB of the bucket kernel that walks it: inside a kernel the stride is
+// the compile-time KB.
+static_assert(BS_ROW_STRIDE(29) == 32 && BS_ROW_STRIDE(32) == 32 && BS_ROW_STRIDE(1) == 4,
+              "row stride must equal the 4-column bucket width");
 
 // Column `col` of a bucket KB is live when col < K; K >= KB - 3 always, so
 // only the last three columns of a bucket need a runtime test.  (The FP32
@@ -315,22 +311,21 @@ __device__ __forceinline__ void store_partial(bs_zdd* p, ddv re, ddv im) {
     *p = o;
 }
 
-// ---------------------------------------------------------------- one task: permanent
-// Each lane: plain-precision runs of FOLD addends folded into a compensated
-// sum (double-double in FP64, float-float in FP32); the 32 lanes are then
-// combined in the same compensated format (no FP64 instruction in the FP32
-// kernel) and lane 0 writes the task's double-double partial.
-template <typename T, int KB>
-__device__ void walk_task_perm(const bs_job& jb, const cx<T>* __restrict__ data, const int* __restrict__ radix,
-                               bs_zdd* __restrict__ partials, uint32_t local, int lane) {
-    constexpr bool F64 = sizeof(T) == 8;
-    constexpr uint32_t FOLD = F64 ? 64 : 32;
+// ---------------------------------------------------------------- one task: permanent, FP64
+// Each lane: plain double runs of FOLD addends folded into a double-double
+// sum; the 32 lanes are combined in double-double in a fixed shuffle order
+// and lane 0 writes the task's partial.  (The FP32 permanent runs on packed
+// pairs, walk_fp32.cuh.)
+template <int KB>
+__device__ void walk_task_perm_fp64(const bs_job& jb, const cx<double>* __restrict__ data,
+                                    const int* __restrict__ radix, bs_zdd* __restrict__ partials, uint32_t local,
+                                    int lane) {
+    constexpr uint32_t FOLD = 64;
     const int K = jb.K;
-    const int KP = row_stride(K);
-    const cx<T>* c0 = data + jb.data_off;
-    const cx<T>* a2 = c0 + KP;
+    constexpr int KP = KB;  // = BS_ROW_STRIDE(K) for every K of the bucket
+    const cx<double>* c0 = data + jb.data_off;
+    const cx<double>* a2 = c0 + KP;
     ddv sre = {0.0, 0.0}, sim = {0.0, 0.0};
-    ffv fre = {0.f, 0.f}, fim = {0.f, 0.f};
     const uint64_t i0 = ((uint64_t)local * 32u + (uint64_t)lane) << jb.log2L;
     if (i0 < jb.C) {
         const uint64_t rem = jb.C - i0;
@@ -338,55 +333,32 @@ __device__ void walk_task_perm(const bs_job& jb, const cx<T>* __restrict__ data,
         bs_gray g;
         ChunkStepper st;
         st.init(g, i0, jb.nbin, jb.nrows, radix, reinterpret_cast<const uint64_t*>(radix + (BS_META_BINOM(jb) - jb.meta_off)));
-        cx<T> c[KB];
-        seed_columns<T, KB>(c, g, c0, a2, K, KP, jb.nbin, jb.nrows);
-        T ws = signed_weight<T>(g.w, g.parity);
-        cx<T> acc = {(T)0, (T)0};
+        cx<double> c[KB];
+        seed_columns<double, KB>(c, g, c0, a2, K, KP, jb.nbin, jb.nrows);
+        double ws = signed_weight<double>(g.w, g.parity);
+        cx<double> acc = {0.0, 0.0};
         uint32_t run = 0;
         for (uint32_t s = 0;; ++s) {
-            const cx<T> p = product_columns<T, KB>(c, K);
+            const cx<double> p = product_columns<double, KB>(c, K);
             acc.re = bfma(ws, p.re, acc.re);
             acc.im = bfma(ws, p.im, acc.im);
             if (++run == FOLD) {
                 run = 0;
-                if constexpr (F64) {
-                    sre = dd_add_d(sre, (double)acc.re);
-                    sim = dd_add_d(sim, (double)acc.im);
-                } else {
-                    fre = ff_add_f(fre, (float)acc.re);
-                    fim = ff_add_f(fim, (float)acc.im);
-                }
-                acc.re = (T)0;
-                acc.im = (T)0;
+                sre = dd_add_d(sre, acc.re);
+                sim = dd_add_d(sim, acc.im);
+                acc = cx<double>{0.0, 0.0};
             }
             if (s + 1 == len) break;
             uint32_t neg;
             int wch;
             const int row = st.step(g, s, radix, &neg, &wch);
-            ws = wch ? signed_weight<T>(g.w, g.parity) : flip_sign(ws);
-            update_columns<KB>(c, a2 + (size_t)row * KP, unit_sign<T>(neg), K);
+            ws = wch ? signed_weight<double>(g.w, g.parity) : flip_sign(ws);
+            update_columns<KB>(c, a2 + (size_t)row * KP, unit_sign_d(neg), K);
         }
-        if constexpr (F64) {
-            sre = dd_add_d(sre, (double)acc.re);
-            sim = dd_add_d(sim, (double)acc.im);
-        } else {
-            fre = ff_add_f(fre, (float)acc.re);
-            fim = ff_add_f(fim, (float)acc.im);
-        }
+        sre = dd_add_d(sre, acc.re);
+        sim = dd_add_d(sim, acc.im);
     }
-    if constexpr (F64) {
-        warp_reduce_zdd(sre, sim);
-    } else {
-#pragma unroll
-        for (int off = 16; off > 0; off >>= 1) {
-            fre = ff_add(fre, shfl_down_ff(fre, off));
-            fim = ff_add(fim, shfl_down_ff(fim, off));
-        }
-        if (lane == 0) {
-            sre = dd_from_ff(fre);
-            sim = dd_from_ff(fim);
-        }
-    }
+    warp_reduce_zdd(sre, sim);
     if (lane == 0) store_partial(partials + jb.partial_off + local, sre, sim);
 }
 
@@ -400,7 +372,7 @@ __device__ void walk_task_minors_fp64(const bs_job& jb, const cx<double>* __rest
                                       int lane, cx<double>* __restrict__ sm_suf, cx<double>* __restrict__ sm_acc,
                                       int stride) {
     const int K = jb.K;
-    const int KP = row_stride(K);
+    constexpr int KP = KB;  // = BS_ROW_STRIDE(K) for every K of the bucket
     const cx<double>* c0 = data + jb.data_off;
     const cx<double>* a2 = c0 + KP;
 #pragma unroll

@@ -147,7 +147,7 @@ __device__ void walk_task_perm_fp32(const bs_job& jb, const void* __restrict__ d
     constexpr uint32_t FOLD = 32;
     constexpr int NP = KB / 2;
     const int K = jb.K;
-    const int KP2 = row_stride(K) / 2;
+    constexpr int KP2 = KB / 2;  // pairs per row: BS_ROW_STRIDE(K) = KB in the bucket
     const float4* c0 = static_cast<const float4*>(data_v) + jb.data_off / 2;
     const float4* a2 = c0 + KP2;
     ffv fre = {0.f, 0.f}, fim = {0.f, 0.f};
@@ -223,7 +223,7 @@ __device__ void walk_task_minors_fp32(const bs_job& jb, const void* __restrict__
     constexpr int CPT = 32 / G;
     static_assert(KB % (2 * G) == 0, "bucket must split into G groups of column pairs");
     const int K = jb.K;
-    const int KP2 = row_stride(K) / 2;
+    constexpr int KP2 = KB / 2;  // pairs per row: BS_ROW_STRIDE(K) = KB in the bucket
     const int q = lane & (G - 1);
     const int p0 = q * NP;         // first own pair
     const int cbase = 2 * p0;      // first own column

@@ -181,6 +181,62 @@ def test_minors_with_repeats_and_empty(ctx, mode):
     assert got[0] == 1
 
 
+MINOR_WIDTHS = [13, 17, 20, 21, 24, 25, 26, 28, 29, 31, 32, 33, 36, 37, 40, 41, 44, 45, 48]
+
+
+@pytest.mark.parametrize("K", MINOR_WIDTHS)
+def test_fp64_minors_every_width_against_oracle(ctx, K):
+    """FP64 fused minors of a (K-1)-photon row set over K columns, for every
+    column width up to 48: three distinct rows with large multiplicities keep
+    the oracle's term-by-term formula cheap; every minor is checked against
+    the oracle's permanent of the matrix with that column removed."""
+    g = S.rng(4000 + K)
+    R = 3
+    M = np.full(R, (K - 1) // R, dtype=np.int32)
+    M[: K - 1 - M.sum()] += 1
+    u = S.haar_unitary(64, 500 + K)
+    a = u[g.permutation(64)[:R]][:, g.permutation(64)[:K]]
+    N = np.ones(K, dtype=np.int32)
+    got = ctx.laplace_minors(a, M, N, mode=0)
+    for l in range(K):
+        keep = [j for j in range(K) if j != l]
+        ref = ref_perm(a[:, keep], M, N[keep])
+        bound = TOL[0] * minor_scale(a, M, N, l) + TOL_L1 * oracle.perm_mult_abs(a[:, keep], M, N[keep])
+        assert abs(got[l] - ref) <= bound, (K, l, got[l], ref, bound)
+
+
+@pytest.mark.parametrize("K", MINOR_WIDTHS)
+def test_fp32_minors_every_width(ctx, K):
+    """MIXED fused minors at every column width, with multiplicities light
+    enough that the MIXED rule keeps them in the FP32 kernel (checked from the
+    statistics): against the FP64 minors within the MIXED tolerance, and the
+    Laplace identity sum_l v_l minor_l = per([A; v]) against the FP64
+    permanent.  (The addend counts are far beyond the oracle here; the FP64
+    kernels are pinned to the oracle above and in the permanent tests.)"""
+    g = S.rng(4100 + K)
+    n = K - 1
+    m = 3 if K >= 24 else (2 if K >= 17 else 1)  # heaviest repeats the MIXED rule keeps in FP32
+    R = min(n, max(2, -(-n // m)))
+    M = np.full(R, n // R, dtype=np.int32)
+    M[: n - M.sum()] += 1
+    u = S.haar_unitary(64, 600 + K)
+    rows = g.permutation(64)[: R + 1]
+    cols = g.permutation(64)[:K]
+    a = u[rows[:R]][:, cols]
+    v = u[rows[R], cols]
+    N = np.ones(K, dtype=np.int32)
+    ctx.reset_stats()
+    got = ctx.laplace_minors(a, M, N, mode=1)
+    st = ctx.stats()
+    assert st["addends"][1] > 0 and st["addends"][0] == 0, "expected the FP32 kernel"
+    ref = ctx.laplace_minors(a, M, N, mode=0)
+    for l in range(K):
+        assert abs(got[l] - ref[l]) <= TOL[1] * minor_scale(a, M, N, l), (K, l, got[l], ref[l])
+    full = ctx.perm(np.vstack([a, v]), np.append(M, 1), N, mode=0)
+    lap = np.sum(v * got)
+    assert abs(lap - full) <= 10 * TOL[1] * scale(np.vstack([a, v]), np.append(M, 1), N), (K, lap, full)
+
+
 @pytest.mark.parametrize("mode", [0, 1])
 def test_batch_matches_oracle_and_single_calls(ctx, mode):
     items = S.config_batch(count=48, seed=7, kmin=6, kmax=18, m=60, group=16)
