@@ -420,9 +420,32 @@ def run_batch(args):
         v, t = oracle.perm_mult(a, M, N)
         orc["fp64_max"] = max(orc["fp64_max"], abs(res["fp64"][b_] - (v + t)) / sc[b_])
         orc["mixed_max"] = max(orc["mixed_max"], abs(res["mixed"][b_] - (v + t)) / sc[b_])
+    # a small batch, where host planning and launches dominate: per-call time
+    # with the captured graph replayed vs planned and launched every call
+    small = S.config_batch(count=64, seed=12, kmin=10, kmax=16)
+    sp, soffs, srows, scols, smults, sroff, scoff = ctx.pack_batch(small)
+    sdev = torch.from_numpy(sp).cuda()
+    so = torch.zeros(len(small), dtype=torch.complex128, device="cuda")
+    stream = torch.cuda.Stream()
+    ctx.set_stream(stream)
+    small_us = {}
+    for graphs in (True, False):
+        ctx.set_graphs(graphs)
+        for w in range(3):
+            ctx.perm_batch_dev(sdev, soffs, srows, scols, smults, sroff, scoff, bs.BS_MIXED, so)
+        ctx.sync()
+        reps = 50
+        t0 = time.perf_counter()
+        for r in range(reps):
+            ctx.perm_batch_dev(sdev, soffs, srows, scols, smults, sroff, scoff, bs.BS_MIXED, so)
+        ctx.sync()
+        small_us["graph" if graphs else "eager"] = (time.perf_counter() - t0) / reps * 1e6
+    ctx.set_graphs(True)
+    ctx.set_stream(None)
     line = {"workload": "batch_4096_k10_28", "metric": "permanents/s", "fp64": out["fp64"], "mixed": out["mixed"],
             "mixed_vs_fp64_err_over_prod_norms": {"max": float(rel.max()), "p99": float(np.percentile(rel, 99))},
-            "err_vs_oracle_over_prod_norms_16_cheapest": orc}
+            "err_vs_oracle_over_prod_norms_16_cheapest": orc,
+            "small_batch_64_k10_16_mixed_us_per_call": small_us}
     print(json.dumps(line), flush=True)
     return 0
 

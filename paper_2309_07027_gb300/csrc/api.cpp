@@ -79,6 +79,18 @@ struct bs_ctx {
     cudaGraphExec_t cc_exec = nullptr;
     std::vector<uint64_t> cc_key;
     uint64_t cc_graph_kernels = 0;
+    // captured device sequence of the last device-pointer batch, replayed
+    // while the batch's shapes, multiplicities, offsets, mode, chunk caps and
+    // deadline, its device pointers and the context buffers are unchanged
+    cudaGraphExec_t batch_exec = nullptr;
+    std::vector<int64_t> batch_key;
+    const void* batch_src = nullptr;
+    void* batch_out = nullptr;
+    uint64_t batch_gen = 0;
+    uint64_t batch_walks = 0, batch_kernels = 0, batch_adds[2] = {0, 0}, batch_flops[2] = {0, 0};
+    // bumped whenever the job/metadata buffers are rewritten or any buffer
+    // is reallocated (a captured graph refers to them)
+    uint64_t buf_gen = 1;
     void* h_stage = nullptr;
     size_t h_stage_n = 0;
     cudaEvent_t stage_ev = nullptr;
@@ -103,6 +115,7 @@ int ensure(bs_ctx* c, DevBuf& b, size_t bytes) {
             return fail(BS_ENOMEM, "device memory budget exceeded: need %zu more bytes (budget %zu, in use %zu)",
                         want - b.n, c->budget, c->used);
     }
+    c->buf_gen++;
     if (b.p) {
         cudaFree(b.p);
         c->used -= b.n;
@@ -187,8 +200,23 @@ int launch_walk(bs_ctx* c, const bs::WalkArgs& a, bool fp32, int kind) {
     return record_walk_end(c, e0, fp32);
 }
 
-int run_jobs(bs_ctx* c, std::vector<JobIn>& ins, const double2* d_src, bs_mode mode, double2* d_out,
-             double2* d_out_lo) {
+// A planned and uploaded set of jobs: what the device sequence needs.
+struct Prepared {
+    struct Group {
+        size_t first, last;
+        int fp32, kind, kmax;
+        unsigned long long tasks;
+    };
+    std::vector<Group> groups;
+    size_t njobs = 0, n64 = 0;
+    int max_cols = 1;
+    uint64_t adds[2] = {0, 0}, flops[2] = {0, 0};
+};
+
+// Host half of a walk: plan every job (precision, chunking, groups of equal
+// precision, kind and bucket, largest jobs first), size the device buffers
+// and upload the job descriptors and metadata.
+int plan_upload(bs_ctx* c, std::vector<JobIn>& ins, bs_mode mode, Prepared& P) {
     struct Row {
         JobIn in;
         int fp32, kind, bucket, log2L, cpt, ncols;
@@ -209,6 +237,7 @@ int run_jobs(bs_ctx* c, std::vector<JobIn>& ins, const double2* d_src, bs_mode m
         r.ncols = r.kind == BS_KIND_PERM ? 1 : in.p->K;
         rows.push_back(r);
     }
+    P = Prepared();
     if (rows.empty()) return BS_OK;
     // groups of equal (precision, kind, bucket); largest jobs first inside
     std::stable_sort(rows.begin(), rows.end(), [](const Row& a, const Row& b) {
@@ -230,8 +259,9 @@ int run_jobs(bs_ctx* c, std::vector<JobIn>& ins, const double2* d_src, bs_mode m
     std::vector<bs_job> jobs(rows.size());
     std::vector<int> meta;
     int64_t data_off[2] = {0, 0}, part_off = 0;
-    int max_cols = 1;
-    uint64_t adds[2] = {0, 0}, flops[2] = {0, 0};
+    int& max_cols = P.max_cols;
+    uint64_t* adds = P.adds;
+    uint64_t* flops = P.flops;
     for (auto& g : groups) {
         uint64_t tb = 0;
         for (size_t i = g.first; i < g.second; ++i) {
@@ -288,16 +318,38 @@ int run_jobs(bs_ctx* c, std::vector<JobIn>& ins, const double2* d_src, bs_mode m
     BS_CUDA(cudaMemcpyAsync(c->jobs.p, h, jobs_b, cudaMemcpyHostToDevice, c->stream));
     BS_CUDA(cudaMemcpyAsync(c->meta.p, h + jobs_b, meta_b, cudaMemcpyHostToDevice, c->stream));
     BS_CUDA(cudaEventRecord(c->stage_ev, c->stream));
+    c->buf_gen++;
+    P.njobs = rows.size();
+    // FP64 jobs come first (sorted by precision), then FP32 jobs
+    while (P.n64 < rows.size() && !rows[P.n64].fp32) ++P.n64;
+    for (auto& g : groups) {
+        Prepared::Group G;
+        G.first = g.first;
+        G.last = g.second;
+        G.fp32 = rows[g.first].fp32;
+        G.kind = rows[g.first].kind;
+        G.kmax = 0;
+        G.tasks = 0;
+        for (size_t i = g.first; i < g.second; ++i) {
+            G.tasks += rows[i].ntasks;
+            G.kmax = std::max(G.kmax, rows[i].in.p->K);
+        }
+        P.groups.push_back(G);
+    }
+    return BS_OK;
+}
+
+// Device half: counters, pack, one walk launch per group, reduce; nothing
+// that synchronises, so it can be captured into a graph.
+int enqueue_device(bs_ctx* c, const Prepared& P, const double2* d_src, double2* d_out, double2* d_out_lo) {
+    int rc;
     // counters, totals and status; the statistics slots are cleared only by
     // bs_ctx_reset_stats
     BS_CUDA(cudaMemsetAsync(c->ctl.p, 0, kCtlStats * 8, c->stream));
     BS_CUDA(cudaMemsetAsync(static_cast<unsigned long long*>(c->ctl.p) + kCtlListLen, 0, (kCtlSlots - kCtlListLen) * 8, c->stream));
     const bs_job* djobs = static_cast<const bs_job*>(c->jobs.p);
-    // FP64 jobs come first (sorted by precision), then FP32 jobs
-    size_t n64 = 0;
-    while (n64 < rows.size() && !rows[n64].fp32) ++n64;
     for (int prec = 0; prec < 2; ++prec) {
-        const size_t lo = prec ? n64 : 0, hi = prec ? rows.size() : n64;
+        const size_t lo = prec ? P.n64 : 0, hi = prec ? P.njobs : P.n64;
         if (hi == lo) continue;
         cudaError_t e = bs::launch_pack(djobs + lo, (int)(hi - lo), d_src, static_cast<int*>(c->meta.p),
                                         prec ? c->data32.p : c->data64.p, prec, c->stream);
@@ -305,38 +357,40 @@ int run_jobs(bs_ctx* c, std::vector<JobIn>& ins, const double2* d_src, bs_mode m
         c->stats.kernel_launches++;
     }
     unsigned long long* ctl = static_cast<unsigned long long*>(c->ctl.p);
-    for (size_t gi = 0; gi < groups.size(); ++gi) {
-        auto& g = groups[gi];
-        const int fp32 = rows[g.first].fp32;
+    for (size_t gi = 0; gi < P.groups.size(); ++gi) {
+        const Prepared::Group& g = P.groups[gi];
         bs::WalkArgs w;
         std::memset(&w, 0, sizeof(w));
         w.jobs = djobs + g.first;
-        w.njobs = (int)(g.second - g.first);
-        w.data = fp32 ? c->data32.p : c->data64.p;
+        w.njobs = (int)(g.last - g.first);
+        w.data = g.fp32 ? c->data32.p : c->data64.p;
         w.meta = static_cast<const int*>(c->meta.p);
         w.partials = static_cast<bs_zdd*>(c->partials.p);
-        unsigned long long tot = 0;
-        int kmax = 0;
-        for (size_t i = g.first; i < g.second; ++i) {
-            tot += rows[i].ntasks;
-            kmax = std::max(kmax, rows[i].in.p->K);
-        }
-        w.total_tasks = tot;
+        w.total_tasks = g.tasks;
         w.counter = ctl + gi;
         w.status = reinterpret_cast<int*>(ctl + kCtlStatus);
         w.deadline_rel_ns = c->deadline_s > 0 ? (unsigned long long)(c->deadline_s * 1e9) : 0ull;
-        w.max_K = kmax;
-        if ((rc = launch_walk(c, w, fp32 != 0, rows[g.first].kind))) return rc;
+        w.max_K = g.kmax;
+        if ((rc = launch_walk(c, w, g.fp32 != 0, g.kind))) return rc;
     }
     {
-        cudaError_t e = bs::launch_reduce(djobs, (int)jobs.size(), static_cast<const bs_zdd*>(c->partials.p),
-                                          static_cast<const int*>(c->meta.p), d_out, d_out_lo, max_cols, c->stream);
+        cudaError_t e = bs::launch_reduce(djobs, (int)P.njobs, static_cast<const bs_zdd*>(c->partials.p),
+                                          static_cast<const int*>(c->meta.p), d_out, d_out_lo, P.max_cols, c->stream);
         if (e != cudaSuccess) return fail(BS_ECUDA, "reduce launch failed: %s", cudaGetErrorString(e));
         c->stats.kernel_launches++;
     }
+    return BS_OK;
+}
+
+int run_jobs(bs_ctx* c, std::vector<JobIn>& ins, const double2* d_src, bs_mode mode, double2* d_out,
+             double2* d_out_lo) {
+    Prepared P;
+    int rc = plan_upload(c, ins, mode, P);
+    if (rc || P.njobs == 0) return rc;
+    if ((rc = enqueue_device(c, P, d_src, d_out, d_out_lo))) return rc;
     for (int p = 0; p < 2; ++p) {
-        c->stats.addends[p] += adds[p];
-        c->stats.addend_flops[p] += flops[p];
+        c->stats.addends[p] += P.adds[p];
+        c->stats.addend_flops[p] += P.flops[p];
     }
     return BS_OK;
 }
@@ -682,6 +736,7 @@ void bs_ctx_destroy(bs_ctx* c) {
                       &c->cc_jobs,   &c->cc_meta,  &c->cc_data,  &c->cc_partials, &c->cc_minors, &c->cc_out,
                       &c->cc_U, &c->cc_lists, &c->cc_args};
     if (c->cc_exec) cudaGraphExecDestroy(c->cc_exec);
+    if (c->batch_exec) cudaGraphExecDestroy(c->batch_exec);
     for (DevBuf* b : bufs) release(c, *b);
     if (c->h_stage) cudaFreeHost(c->h_stage);
     if (c->stage_ev) cudaEventDestroy(c->stage_ev);
@@ -815,6 +870,91 @@ static int batch_common(bs_ctx* c, int count, const bs_c128* A_packed, const int
     return BS_OK;
 }
 
+// Identity of a batch for graph replay: everything the plan and the device
+// sequence depend on except the device pointers (compared separately).
+static std::vector<int64_t> batch_key(const bs_ctx* c, int count, const int64_t* a_offset, const int* rows,
+                                      const int* cols, const int* mult_packed, const int64_t* row_mult_off,
+                                      const int64_t* col_mult_off, bs_mode mode) {
+    std::vector<int64_t> k;
+    int64_t dl = 0;
+    std::memcpy(&dl, &c->deadline_s, sizeof(dl));
+    k.insert(k.end(), {(int64_t)count, (int64_t)mode, (int64_t)c->log2max[0], (int64_t)c->log2max[1], dl});
+    for (int b = 0; b < count; ++b) {
+        k.insert(k.end(), {a_offset[b], (int64_t)rows[b], (int64_t)cols[b]});
+        for (int r = 0; r < rows[b]; ++r) k.push_back(mult_packed[row_mult_off[b] + r]);
+        for (int j = 0; j < cols[b]; ++j) k.push_back(mult_packed[col_mult_off[b] + j]);
+    }
+    return k;
+}
+
+// Walks a validated batch whose sources sit at d_src (+ each item's offset)
+// and writes item b to d_out[b].  The device sequence of the last batch is
+// kept as a captured CUDA graph: a batch with the same key, the same device
+// pointers and untouched context buffers replays it without planning,
+// uploading or launching anew.  Eager when graphs are off, when profiling, on
+// the legacy default stream and while the caller captures the stream.
+static int batch_walk(bs_ctx* c, std::vector<IntPlan>& plans, const std::vector<int64_t>& key,
+                      const int64_t* a_offset, const int* cols, const double2* d_src, double2* d_out, bs_mode mode) {
+    int rc;
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    if (c->stream != nullptr) BS_CUDA(cudaStreamIsCapturing(c->stream, &cap));
+    const bool graphs = c->use_graphs && !c->profiling && c->stream != nullptr && c->stream != cudaStreamPerThread &&
+                        cap == cudaStreamCaptureStatusNone;
+    if (graphs && c->batch_exec && c->batch_gen == c->buf_gen && c->batch_src == d_src && c->batch_out == d_out &&
+        c->batch_key == key) {
+        BS_CUDA(cudaGraphLaunch(c->batch_exec, c->stream));
+        c->stats.walk_launches += c->batch_walks;
+        c->stats.kernel_launches += c->batch_kernels;
+        for (int p = 0; p < 2; ++p) {
+            c->stats.addends[p] += c->batch_adds[p];
+            c->stats.addend_flops[p] += c->batch_flops[p];
+        }
+        return BS_OK;
+    }
+    std::vector<JobIn> ins;
+    for (size_t b = 0; b < plans.size(); ++b)
+        if (!plans[b].trivial) ins.push_back({&plans[b], a_offset[b], cols[b], (int)b});
+    Prepared P;
+    if ((rc = plan_upload(c, ins, mode, P))) return rc;
+    if (P.njobs == 0) return BS_OK;
+    if (!graphs) {
+        if ((rc = enqueue_device(c, P, d_src, d_out, nullptr))) return rc;
+    } else {
+        const uint64_t w0 = c->stats.walk_launches, k0 = c->stats.kernel_launches;
+        BS_CUDA(cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal));
+        rc = enqueue_device(c, P, d_src, d_out, nullptr);
+        cudaGraph_t g = nullptr;
+        cudaError_t e = cudaStreamEndCapture(c->stream, &g);
+        if (rc || e != cudaSuccess) {
+            if (g) cudaGraphDestroy(g);
+            cudaGetLastError();
+            return rc ? rc : fail(BS_ECUDA, "batch graph capture: %s", cudaGetErrorString(e));
+        }
+        cudaGraphExec_t exec = nullptr;
+        e = cudaGraphInstantiate(&exec, g, 0);
+        cudaGraphDestroy(g);
+        if (e != cudaSuccess) return fail(BS_ECUDA, "batch graph instantiate: %s", cudaGetErrorString(e));
+        if (c->batch_exec) cudaGraphExecDestroy(c->batch_exec);
+        c->batch_exec = exec;
+        c->batch_key = key;
+        c->batch_gen = c->buf_gen;
+        c->batch_src = d_src;
+        c->batch_out = d_out;
+        c->batch_walks = c->stats.walk_launches - w0;
+        c->batch_kernels = c->stats.kernel_launches - k0;
+        for (int p = 0; p < 2; ++p) {
+            c->batch_adds[p] = P.adds[p];
+            c->batch_flops[p] = P.flops[p];
+        }
+        BS_CUDA(cudaGraphLaunch(c->batch_exec, c->stream));
+    }
+    for (int p = 0; p < 2; ++p) {
+        c->stats.addends[p] += P.adds[p];
+        c->stats.addend_flops[p] += P.flops[p];
+    }
+    return BS_OK;
+}
+
 int bs_perm_batch(bs_ctx* c, int count, const bs_c128* A_packed, const int64_t* a_offset, const int* rows,
                   const int* cols, const int* mult_packed, const int64_t* row_mult_off, const int64_t* col_mult_off,
                   bs_mode mode, bs_c128* out) {
@@ -836,15 +976,15 @@ int bs_perm_batch(bs_ctx* c, int count, const bs_c128* A_packed, const int64_t* 
     if ((rc = ensure(c, c->out, count * sizeof(double2)))) return rc;
     bs_c128* h = static_cast<bs_c128*>(stage(c, total * sizeof(bs_c128)));
     if (!h) return fail(BS_ENOMEM, "pinned host staging allocation failed");
-    std::vector<JobIn> ins;
-    for (int b = 0; b < count; ++b) {
-        if (plans[b].trivial) continue;
-        copy_matrix(h + off[b], A_packed + a_offset[b], rows[b], cols[b], cols[b]);
-        ins.push_back({&plans[b], off[b], cols[b], b});
-    }
+    for (int b = 0; b < count; ++b)
+        if (!plans[b].trivial) copy_matrix(h + off[b], A_packed + a_offset[b], rows[b], cols[b], cols[b]);
     BS_CUDA(cudaMemcpyAsync(c->src.p, h, total * sizeof(bs_c128), cudaMemcpyHostToDevice, c->stream));
     BS_CUDA(cudaEventRecord(c->stage_ev, c->stream));
-    rc = run_jobs(c, ins, static_cast<const double2*>(c->src.p), mode, static_cast<double2*>(c->out.p), nullptr);
+    // the staged sources are contiguous: the key uses their offsets
+    const std::vector<int64_t> key =
+        batch_key(c, count, off.data(), rows, cols, mult_packed, row_mult_off, col_mult_off, mode);
+    rc = batch_walk(c, plans, key, off.data(), cols, static_cast<const double2*>(c->src.p),
+                    static_cast<double2*>(c->out.p), mode);
     if (rc) return rc;
     std::vector<double2> res(count);
     BS_CUDA(cudaMemcpyAsync(res.data(), c->out.p, count * sizeof(double2), cudaMemcpyDeviceToHost, c->stream));
@@ -872,16 +1012,13 @@ int bs_perm_batch_dev(bs_ctx* c, int count, const bs_c128* A_packed_dev, const i
     if (!out_dev) return fail(BS_EINVAL, "out is NULL");
     std::lock_guard<std::mutex> lk(c->mu);
     BS_CUDA(cudaSetDevice(c->device));
-    std::vector<JobIn> ins;
     std::vector<int> trivial;
-    for (int b = 0; b < count; ++b) {
-        if (plans[b].trivial)
-            trivial.push_back(b);
-        else
-            ins.push_back({&plans[b], a_offset[b], cols[b], b});
-    }
-    rc = run_jobs(c, ins, reinterpret_cast<const double2*>(A_packed_dev), mode, reinterpret_cast<double2*>(out_dev),
-                  nullptr);
+    for (int b = 0; b < count; ++b)
+        if (plans[b].trivial) trivial.push_back(b);
+    const std::vector<int64_t> key =
+        batch_key(c, count, a_offset, rows, cols, mult_packed, row_mult_off, col_mult_off, mode);
+    rc = batch_walk(c, plans, key, a_offset, cols, reinterpret_cast<const double2*>(A_packed_dev),
+                    reinterpret_cast<double2*>(out_dev), mode);
     if (rc) return rc;
     if (!trivial.empty()) {
         static const double2 one = {1.0, 0.0};

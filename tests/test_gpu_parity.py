@@ -283,6 +283,56 @@ def test_batch_device_pointers(ctx):
     assert np.array_equal(out.cpu().numpy(), host)
 
 
+@pytest.mark.parametrize("mode", [0, 1])
+def test_batch_graph_replay(ctx, mode):
+    """A repeated batch replays its captured device sequence: the results
+    equal the eager launches bit for bit, new matrix data in the same buffer
+    is read at replay, and a call that rewrites the context buffers in
+    between forces a fresh capture (same results again)."""
+    import torch
+    items = S.config_batch(count=48, seed=21, kmin=8, kmax=18)
+    packed, offs, rows, cols, mults, roff, coff = ctx.pack_batch(items)
+    phase = np.exp(0.3j)
+    orig = torch.from_numpy(packed).cuda()
+    dev = orig.clone()
+    torch.cuda.synchronize()
+    out = torch.zeros(len(items), dtype=torch.complex128, device="cuda")
+    stream = torch.cuda.Stream()
+    ctx.set_stream(stream)
+
+    def run():
+        ctx.perm_batch_dev(dev, offs, rows, cols, mults, roff, coff, mode, out)
+        ctx.sync()
+        return out.cpu().numpy().copy()
+
+    try:
+        ctx.set_graphs(False)
+        eager = run()
+        dev.mul_(phase)
+        torch.cuda.synchronize()
+        eager_phase = run()
+        dev.copy_(orig)
+        torch.cuda.synchronize()
+        ctx.set_graphs(True)
+        first = run()  # capture
+        k0 = ctx.stats()["kernel_launches"]
+        second = run()  # replay
+        assert ctx.stats()["kernel_launches"] > k0
+        assert np.array_equal(first, eager) and np.array_equal(second, eager)
+        dev.mul_(phase)
+        torch.cuda.synchronize()
+        assert np.array_equal(run(), eager_phase)  # replay reads the new data
+        dev.copy_(orig)
+        torch.cuda.synchronize()
+        ctx.perm(items[0][0], items[0][1], items[0][2], mode=mode)  # rewrites the job buffers
+        assert np.array_equal(run(), eager)
+    finally:
+        ctx.set_graphs(True)
+        ctx.set_stream(None)
+    host = ctx.perm_batch(items, mode=mode)
+    assert np.array_equal(host, eager)
+
+
 def test_autotuner_picks_a_valid_chunk_and_results_stay_exact(ctx, bslib):
     saved = (ctx.chunk_log2(0), ctx.chunk_log2(1))
     try:
