@@ -242,34 +242,50 @@ def run_mine(args):
     for w in range(args.warmup):
         ctx.sample_dev(u_dev, occ, S_, seed_base + w, out_dev, mode=mode)
         ctx.sync()
+    def timed_steps(profile):
+        """args.steps sampler steps (seeds fixed per step), each between CUDA
+        events on the stream, the L2 flushed before each; returns the step
+        times (ms)."""
+        ctx.set_profiling(profile)
+        evs = []
+        for i in range(args.steps):
+            flush.zero_()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            ctx.sample_dev(u_dev, occ, S_, seed_base + 100 + i, out_dev, mode=mode)
+            e1.record(stream)
+            evs.append((e0, e1))
+            if profile:
+                # a profiled graph replay is read back before the next one
+                # starts: wait here, outside the timed events
+                stream.synchronize()
+        torch.cuda.synchronize()
+        ctx.set_profiling(False)
+        return [a.elapsed_time(b) for a, b in evs]
+
+    # timed region: the production path (graph replay, no per-walk events)
     ctx.reset_stats()
-    ctx.set_profiling(True)
     clocks = start_clocks(local)
     barrier()
     torch.cuda.synchronize()
-    evs = []
     wall0 = time.perf_counter()
-    for i in range(args.steps):
-        flush.zero_()
-        e0 = torch.cuda.Event(enable_timing=True)
-        e1 = torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
-        ctx.sample_dev(u_dev, occ, S_, seed_base + 100 + i, out_dev, mode=mode)
-        e1.record(stream)
-        evs.append((e0, e1))
-    torch.cuda.synchronize()
+    step_ms = timed_steps(False)
     barrier()
     wall = time.perf_counter() - wall0
     clk = stop_clocks(clocks)
     ctx.sync()
-    st = ctx.stats()
-    ctx.set_profiling(False)
-    step_ms = [a.elapsed_time(b) for a, b in evs]
+    launches = int(ctx.stats()["kernel_launches"])
     counts = out_dev.cpu().numpy()
     assert np.all(counts.sum(axis=1) == N_PHOTONS), "sampler returned a wrong photon count"
     t_max = max_over_ranks(sum(step_ms) / 1000.0, dist)
     value = aggregate_rate(world, S_ * args.steps, t_max)
-    launches = int(st["kernel_launches"])
+    # the same steps again with CUDA events around every walk launch (on the
+    # launching stream, inside the replayed graph): kernel times for the
+    # roofline; the events add about 3 % to a step
+    ctx.reset_stats()
+    prof_step_ms = timed_steps(True)
+    st = ctx.stats()
 
     # roofline of the dominant walk kernel (fused minors in the run's
     # precision; MIXED sends heavy-collision chains to the FP64 kernel, whose
@@ -291,6 +307,8 @@ def run_mine(args):
             "kernel": "walk_fp32_minors_kernel" if p == 1 else "walk_fp64_minors_kernel",
             "peak_source": "measured on this GPU by bs_measure_fma_rates (2 flops per lane-FMA)",
             "walk_ms_per_step": st["walk_ms"][p] / args.steps, "walk_launches": int(st["timed_launches"][p]),
+            "measured_over": f"{args.steps} profiled steps of the same workload and seeds, right after the timed "
+                             f"ones ({statistics.mean(prof_step_ms):.1f} ms per profiled step)",
             "addends_per_s": st["addends"][p] / walk_s if walk_s > 0 else 0.0,
             "other_precision": {"walk_ms_per_step": st["walk_ms"][1 - p] / args.steps,
                                 "addends": st["addends"][1 - p]}}

@@ -289,14 +289,17 @@ typedef struct {
     uint64_t timed_launches[2]; /* walk launches included in walk_ms */
 } bs_stats;
 
-/* Sampling replays its per-step kernel sequence from a captured CUDA graph
- * (re-captured when shapes, buffers, deadline or stream change) when on != 0
- * (the default); 0 launches every kernel directly.  Profiling always runs
- * without the graph so that every walk launch is timed. */
+/* Sampling and batches replay their kernel sequence from a captured CUDA
+ * graph (re-captured when shapes, buffers, deadline, stream or the profiling
+ * switch change) when on != 0 (the default); 0 launches every kernel
+ * directly.  With profiling on, a sampling graph carries the walk timing
+ * events (read before its next replay); batches then launch directly. */
 int bs_ctx_set_graphs(bs_ctx* ctx, int on);
 
 /* Record CUDA events around every walk launch (on its stream) when on != 0;
- * bs_ctx_get_stats() then reports their summed durations. */
+ * bs_ctx_get_stats() then reports their summed durations.  A profiled
+ * sampling graph replay waits for the previous replay's events before it is
+ * launched. */
 int bs_ctx_set_profiling(bs_ctx* ctx, int on);
 
 /* Durations (ms) of the walk launches timed since the last call, oldest

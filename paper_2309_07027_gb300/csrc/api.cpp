@@ -79,6 +79,10 @@ struct bs_ctx {
     cudaGraphExec_t cc_exec = nullptr;
     std::vector<uint64_t> cc_key;
     uint64_t cc_graph_kernels = 0;
+    // walk timing events captured into the sampler graph (profiling): owned
+    // by the graph, re-recorded at every replay and read before the next one
+    std::vector<Timed> cc_graph_timed;
+    bool cc_timing_pending = false;
     // captured device sequence of the last device-pointer batch, replayed
     // while the batch's shapes, multiplicities, offsets, mode, chunk caps and
     // deadline, its device pointers and the context buffers are unchanged
@@ -168,11 +172,51 @@ struct JobIn {
     int out_index;
 };
 
+// Reads the walk durations of the last profiled sampler-graph replay into the
+// statistics (waits for that replay to finish).
+void harvest_graph_timing(bs_ctx* c) {
+    if (!c->cc_timing_pending || c->cc_graph_timed.empty()) return;
+    cudaEventSynchronize(c->cc_graph_timed.back().e1);
+    for (auto& t : c->cc_graph_timed) {
+        float ms = 0.f;
+        if (cudaEventElapsedTime(&ms, t.e0, t.e1) == cudaSuccess) {
+            c->stats.walk_ms[t.fp32] += ms;
+            c->stats.timed_launches[t.fp32]++;
+            c->walk_log.push_back(ms);
+        } else {
+            cudaGetLastError();  // leave no stale error for the next launch check
+        }
+    }
+    c->cc_timing_pending = false;
+}
+
+void drop_graph_timing(bs_ctx* c) {
+    for (auto& t : c->cc_graph_timed) {
+        cudaEventDestroy(t.e0);
+        cudaEventDestroy(t.e1);
+    }
+    c->cc_graph_timed.clear();
+    c->cc_timing_pending = false;
+}
+
+// Records a timing event on the context stream; while the stream is being
+// captured the record becomes an event-record node of the graph (a plain
+// record there would only order work inside the graph).
+cudaError_t record_timing_event(bs_ctx* c, cudaEvent_t e) {
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    if (c->stream != nullptr) {
+        cudaError_t err = cudaStreamIsCapturing(c->stream, &cap);
+        if (err != cudaSuccess) return err;
+    }
+    return cap == cudaStreamCaptureStatusActive ? cudaEventRecordWithFlags(e, c->stream, cudaEventRecordExternal)
+                                                : cudaEventRecord(e, c->stream);
+}
+
 int record_walk_start(bs_ctx* c, cudaEvent_t* e0) {
     *e0 = nullptr;
     if (!c->profiling) return BS_OK;
     BS_CUDA(cudaEventCreate(e0));
-    BS_CUDA(cudaEventRecord(*e0, c->stream));
+    BS_CUDA(record_timing_event(c, *e0));
     return BS_OK;
 }
 
@@ -180,7 +224,7 @@ int record_walk_end(bs_ctx* c, cudaEvent_t e0, bool fp32) {
     if (!c->profiling || !e0) return BS_OK;
     cudaEvent_t e1;
     BS_CUDA(cudaEventCreate(&e1));
-    BS_CUDA(cudaEventRecord(e1, c->stream));
+    BS_CUDA(record_timing_event(c, e1));
     c->timed.push_back({e0, e1, fp32 ? 1 : 0});
     return BS_OK;
 }
@@ -623,13 +667,13 @@ int sample_dev(bs_ctx* c, const double2* dU, int m_rows, int m_cols, int ld, con
         // the kernels read the arguments from device memory (pageable copy:
         // staged before cudaMemcpyAsync returns, so `a` may go out of scope)
         BS_CUDA(cudaMemcpyAsync(da, &a, sizeof(a), cudaMemcpyHostToDevice, c->stream));
-        // eager launches when graphs are off, when profiling (every walk is
-        // timed), on the legacy default stream (it cannot be captured), and
-        // when the caller is already capturing this stream (the caller's
-        // graph then records these launches)
+        // eager launches when graphs are off, on the legacy default stream
+        // (it cannot be captured), and when the caller is already capturing
+        // this stream (the caller's graph then records these launches); with
+        // profiling on, the graph carries the walk timing events
         cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
         if (c->stream != nullptr) BS_CUDA(cudaStreamIsCapturing(c->stream, &cap));
-        if (!c->use_graphs || c->profiling || c->stream == nullptr || c->stream == cudaStreamPerThread ||
+        if (!c->use_graphs || c->stream == nullptr || c->stream == cudaStreamPerThread ||
             cap != cudaStreamCaptureStatusNone) {
             uint64_t kernels = 0;
             if ((rc = enqueue_sampler_batch(c, a, da, mixed, &kernels))) return rc;
@@ -645,12 +689,18 @@ int sample_dev(bs_ctx* c, const double2* dU, int m_rows, int m_cols, int ld, con
                                      (uint64_t)(uintptr_t)c->cc_meta.p, (uint64_t)(uintptr_t)c->cc_data.p,
                                      (uint64_t)(uintptr_t)c->cc_partials.p, (uint64_t)(uintptr_t)c->cc_minors.p,
                                      (uint64_t)(uintptr_t)c->cc_lists.p, (uint64_t)(uintptr_t)c->ctl.p,
-                                     (uint64_t)(uintptr_t)da, tasks_stride, dl, (uint64_t)(uintptr_t)c->stream};
+                                     (uint64_t)(uintptr_t)da, tasks_stride, dl, (uint64_t)(uintptr_t)c->stream,
+                                     (uint64_t)c->profiling};
+        harvest_graph_timing(c);
         if (!c->cc_exec || key != c->cc_key) {
             if (c->cc_exec) {
                 cudaGraphExecDestroy(c->cc_exec);
                 c->cc_exec = nullptr;
             }
+            drop_graph_timing(c);
+            // with profiling on, the walk timing events are captured as
+            // event-record nodes: they move from the eager list to the graph
+            const size_t timed_before = c->timed.size();
             BS_CUDA(cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal));
             uint64_t kernels = 0;
             const uint64_t walks_before = c->stats.walk_launches;
@@ -658,8 +708,11 @@ int sample_dev(bs_ctx* c, const double2* dU, int m_rows, int m_cols, int ld, con
             c->stats.walk_launches = walks_before;  // counted per replay below
             cudaGraph_t g = nullptr;
             cudaError_t e = cudaStreamEndCapture(c->stream, &g);
+            c->cc_graph_timed.assign(c->timed.begin() + timed_before, c->timed.end());
+            c->timed.resize(timed_before);
             if (rc) {
                 if (g) cudaGraphDestroy(g);
+                drop_graph_timing(c);
                 return rc;
             }
             if (e != cudaSuccess) return fail(BS_ECUDA, "sampler graph capture: %s", cudaGetErrorString(e));
@@ -673,6 +726,7 @@ int sample_dev(bs_ctx* c, const double2* dU, int m_rows, int m_cols, int ld, con
             c->cc_graph_kernels = kernels;
         }
         BS_CUDA(cudaGraphLaunch(c->cc_exec, c->stream));
+        c->cc_timing_pending = !c->cc_graph_timed.empty();
         c->stats.kernel_launches += c->cc_graph_kernels;
         c->stats.walk_launches += kernels_walks(n, mixed);
     }
@@ -736,6 +790,7 @@ void bs_ctx_destroy(bs_ctx* c) {
                       &c->cc_jobs,   &c->cc_meta,  &c->cc_data,  &c->cc_partials, &c->cc_minors, &c->cc_out,
                       &c->cc_U, &c->cc_lists, &c->cc_args};
     if (c->cc_exec) cudaGraphExecDestroy(c->cc_exec);
+    drop_graph_timing(c);
     if (c->batch_exec) cudaGraphExecDestroy(c->batch_exec);
     for (DevBuf* b : bufs) release(c, *b);
     if (c->h_stage) cudaFreeHost(c->h_stage);
@@ -1089,12 +1144,15 @@ int bs_ctx_set_profiling(bs_ctx* c, int on) {
 
 // Converts recorded walk event pairs into durations (stream must be idle).
 static void collect_timed(bs_ctx* c) {
+    harvest_graph_timing(c);
     for (auto& t : c->timed) {
         float ms = 0.f;
         if (cudaEventElapsedTime(&ms, t.e0, t.e1) == cudaSuccess) {
             c->stats.walk_ms[t.fp32] += ms;
             c->stats.timed_launches[t.fp32]++;
             c->walk_log.push_back(ms);
+        } else {
+            cudaGetLastError();
         }
         cudaEventDestroy(t.e0);
         cudaEventDestroy(t.e1);
@@ -1140,6 +1198,7 @@ int bs_ctx_reset_stats(bs_ctx* c) {
         cudaEventDestroy(t.e1);
     }
     c->timed.clear();
+    c->cc_timing_pending = false;
     c->walk_log.clear();
     c->stats = bs_stats();
     if (c->ctl.p) cudaMemset(static_cast<unsigned long long*>(c->ctl.p) + kCtlStats, 0, 32);

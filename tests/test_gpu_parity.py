@@ -391,6 +391,36 @@ def test_sampler_graph_replay_equals_eager(ctx):
             assert np.array_equal(e, g)
 
 
+def test_profiled_sampler_graph_times_every_walk(ctx):
+    """With profiling on, the replayed sampler graph carries the walk timing
+    events: every walk of every replay is timed, the draws equal the eager
+    ones, and a context call after it sees no stale error."""
+    import torch
+    u, occ = S.config_cc(n=10, m=20, seed=8)
+    n = int(np.sum(occ))
+    stream = torch.cuda.Stream()
+    ctx.set_stream(stream)
+    try:
+        ctx.set_graphs(False)
+        eager = ctx.sample(u, occ, 32, seed=5, mode=1)
+        ctx.set_graphs(True)
+        ctx.set_profiling(True)
+        ctx.walk_times()
+        got = []
+        for rep in range(3):
+            got.append(ctx.sample(u, occ, 32, seed=5, mode=1))
+            t = ctx.walk_times()
+            assert len(t) == 2 * (n - 1), (rep, len(t))  # FP64 and FP32 walk per step k = 2..n
+            assert np.all(t >= 0) and np.sum(t) > 0
+        for g in got:
+            assert np.array_equal(g, eager)
+    finally:
+        ctx.set_profiling(False)
+        ctx.set_graphs(True)
+        ctx.set_stream(None)
+    assert np.array_equal(ctx.sample(u, occ, 32, seed=5, mode=1), eager)
+
+
 def test_sampler_seed_and_batch_independence(ctx):
     u, occ = S.config_cc(n=8, m=16, seed=4)
     a = ctx.sample(u, occ, 40, seed=11, mode=0)
