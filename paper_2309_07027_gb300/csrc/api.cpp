@@ -596,7 +596,7 @@ int sample_dev(bs_ctx* c, const double2* dU, int m_rows, int m_cols, int ld, con
     // length is capped, and then at most C / (cpt 2^log2max) + 1)
     uint64_t cmax = n >= 2 ? (1ull << (n - 2)) : 1ull;
     uint64_t tasks_stride = 2 * BS_TARGET_TASKS_MANY + 1;
-    tasks_stride = std::max<uint64_t>(tasks_stride, cmax / (32ull << c->log2max[0]) + 2);
+    tasks_stride = std::max<uint64_t>(tasks_stride, cmax / (16ull << c->log2max[0]) + 2);
     if (mixed) tasks_stride = std::max<uint64_t>(tasks_stride, cmax / (8ull << c->log2max[1]) + 2);
     // a step-k job has <= k - 1 digit rows, K = k <= n columns, n' = k - 1
     const int64_t meta_stride = BS_META_SIZE(n, n, n), data_stride = (int64_t)n * BS_ROW_STRIDE(n);

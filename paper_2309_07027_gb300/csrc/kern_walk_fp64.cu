@@ -36,8 +36,7 @@ __global__ void __launch_bounds__(kMinorsBlock) walk_fp64_minors_kernel(WalkArgs
     extern __shared__ double2 smem_fp64[];
     const int lane = threadIdx.x & 31;
     const int stride = blockDim.x;
-    cx<double>* sm_suf = reinterpret_cast<cx<double>*>(smem_fp64) + threadIdx.x;
-    cx<double>* sm_acc = sm_suf + (size_t)KB * stride;
+    cx<double>* sm_acc = reinterpret_cast<cx<double>*>(smem_fp64) + threadIdx.x;
     const bs_job* __restrict__ jobs = a.jobs;
     const cx<double>* __restrict__ data = static_cast<const cx<double>*>(a.data);
     const unsigned long long total = task_total(a);
@@ -52,7 +51,7 @@ __global__ void __launch_bounds__(kMinorsBlock) walk_fp64_minors_kernel(WalkArgs
             continue;
         }
         walk_task_minors_fp64<KB>(jb, data, a.meta + BS_META_RADIX(jb), a.partials, (uint32_t)(t - jb.task_begin) + jb.task_offset,
-                                  lane, sm_suf, sm_acc, stride);
+                                  lane, sm_acc, stride);
     }
 }
 
@@ -82,7 +81,7 @@ static cudaError_t run_perm(const WalkArgs& a, cudaStream_t s) {
 
 template <int KB>
 static cudaError_t run_minors(const WalkArgs& a, cudaStream_t s) {
-    size_t smem = (size_t)kMinorsBlock * 2 * KB * sizeof(cx<double>);
+    size_t smem = (size_t)kMinorsBlock * (KB / 2) * sizeof(cx<double>);
     cudaError_t e =
         cudaFuncSetAttribute(walk_fp64_minors_kernel<KB>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;

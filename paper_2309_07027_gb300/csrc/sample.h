@@ -34,12 +34,14 @@ BS_HD int bs_choose_log2L(uint64_t C, int cpt, int log2min, int log2max, int tar
 // Lanes that walk one chunk together in the FP32 fused-minor kernel (each
 // owns a contiguous group of the bucket's column pairs): 4 for widths of a
 // multiple of 8 columns from 24 on, else 2, so every lane holds whole column
-// pairs.  A warp task of that kernel covers 32 / G chunks; every other kernel
-// gives each lane its own chunk (32 per task).
+// pairs.  A warp task of that kernel covers 32 / G chunks, one of the FP64
+// fused-minor kernel 16 (lane pairs); the permanent kernels give each lane its
+// own chunk (32 per task).
 #define BS_MINORS_FP32_GROUP_KB(KB) (((KB) % 8 == 0 && (KB) >= 24) ? 4 : 2)
 BS_HD int bs_minors_fp32_group(int K) { return BS_MINORS_FP32_GROUP_KB((K + 3) & ~3); }
 BS_HD int bs_chunks_per_task(int kind, int fp32, int K) {
-    return (fp32 && kind == BS_KIND_MINORS) ? 32 / bs_minors_fp32_group(K) : 32;
+    if (kind != BS_KIND_MINORS) return 32;
+    return fp32 ? 32 / bs_minors_fp32_group(K) : 16;  // FP64 minors: lane pairs
 }
 
 // Algorithmic flops of one addend (the roofline numerator):

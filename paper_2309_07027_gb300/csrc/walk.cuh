@@ -363,93 +363,145 @@ __device__ void walk_task_perm_fp64(const bs_job& jb, const cx<double>* __restri
 }
 
 // ---------------------------------------------------------------- one task: minors, FP64
-// Suffix products and per-column accumulators live in shared memory, laid
-// out [col][thread] (conflict-free); the column sums stay in registers.  The
-// FP64 pipe is the bottleneck, so the extra shared-memory traffic is free.
+// Two lanes share one chunk: lane (2p + h) owns the columns
+// [h Hr, h Hr + KH), Hr = ceil(K / 2), KH = Hr (h = 0) or K - Hr (h = 1), so
+// both lanes run the same number of columns except one for odd K.  Per
+// addend each lane
+//   1. forms suffix products over its own columns (in registers), the last
+//      one being Q_own, the product of its columns,
+//   2. swaps Q_own with its partner (one shuffle of a complex double),
+//   3. runs the prefix pass from X = (+-W) Q_partner:
+//          acc[l] += X * prefix_l * suffix_l,
+// with the per-column accumulators in shared memory, [col][thread].  Each
+// lane holds half the column sums and suffixes of the one-lane form, so twice
+// as many warps fit on an SM and the dependent product chains are half as
+// long, for the same FP64 work plus one real-by-complex product per lane and
+// addend.  All lanes run the warp's longest chunk length (a finished or
+// absent chunk continues with weight 0), so the shuffle has the full warp.  A
+// warp task covers 16 chunks.
 template <int KB>
 __device__ void walk_task_minors_fp64(const bs_job& jb, const cx<double>* __restrict__ data,
                                       const int* __restrict__ radix, bs_zdd* __restrict__ partials, uint32_t local,
-                                      int lane, cx<double>* __restrict__ sm_suf, cx<double>* __restrict__ sm_acc,
-                                      int stride) {
+                                      int lane, cx<double>* __restrict__ sm_acc, int stride) {
+    constexpr int H = KB / 2;  // most columns a lane can own
     const int K = jb.K;
     constexpr int KP = KB;  // = BS_ROW_STRIDE(K) for every K of the bucket
+    const int half = lane & 1;
+    const int Hr = (K + 1) >> 1;
+    const int cbase = half * Hr;
+    const int KH = half ? K - Hr : Hr;  // own columns, >= 1 for K >= 2
     const cx<double>* c0 = data + jb.data_off;
     const cx<double>* a2 = c0 + KP;
+#define BS_OWN(t) ((t) < H - 2 || (t) < KH)
 #pragma unroll
-    for (int col = 0; col < KB; ++col)
-        if (BS_LIVE(col)) sm_acc[col * stride] = cx<double>{0.0, 0.0};
-    const uint64_t i0 = ((uint64_t)local * 32u + (uint64_t)lane) << jb.log2L;
-    if (i0 < jb.C) {
+    for (int t = 0; t < H; ++t)
+        if (BS_OWN(t)) sm_acc[t * stride] = cx<double>{0.0, 0.0};
+    const uint64_t i0_own = ((uint64_t)local * 16u + (uint64_t)(lane >> 1)) << jb.log2L;
+    const bool has = i0_own < jb.C;
+    const uint64_t i0 = has ? i0_own : 0ull;
+    uint32_t len = 0;
+    if (has) {
         const uint64_t rem = jb.C - i0;
-        const uint32_t len = (uint32_t)(rem < (1ull << jb.log2L) ? rem : (1ull << jb.log2L));
-        bs_gray g;
-        ChunkStepper st;
-        st.init(g, i0, jb.nbin, jb.nrows, radix, reinterpret_cast<const uint64_t*>(radix + (BS_META_BINOM(jb) - jb.meta_off)));
-        cx<double> c[KB];
-        seed_columns<double, KB>(c, g, c0, a2, K, KP, jb.nbin, jb.nrows);
-        double ws = signed_weight<double>(g.w, g.parity);
-        for (uint32_t s = 0;; ++s) {
-            // suffix pass: suf[l] = ws * prod_{col > l} c_col
-            cx<double> sfx = {ws, 0.0};
-            bool top = true;
+        len = (uint32_t)(rem < (1ull << jb.log2L) ? rem : (1ull << jb.log2L));
+    }
+    const uint32_t steps = __reduce_max_sync(0xffffffffu, len);
+    bs_gray g;
+    ChunkStepper st;
+    st.init(g, i0, jb.nbin, jb.nrows, radix, reinterpret_cast<const uint64_t*>(radix + (BS_META_BINOM(jb) - jb.meta_off)));
+    cx<double> c[H];
+    {
+        // seed own columns: c = c0 - sum_j Delta_j 2a_j
 #pragma unroll
-            for (int col = KB - 1; col >= 0; --col)
-                if (BS_LIVE(col)) {
-                    sm_suf[col * stride] = sfx;
-                    if (col > 0) {
-                        if (top) {
-                            sfx.re = ws * c[col].re;
-                            sfx.im = ws * c[col].im;
-                        } else {
-                            sfx = cmul(sfx, c[col]);
-                        }
-                    }
-                    top = false;
-                }
-            // forward pass: acc[l] += (prod_{col < l} c_col) * suf[l]
-            cx<double> pre = c[0];
-            {
-                cx<double> a = sm_acc[0];
-                cx<double> f = sm_suf[0];
-                a.re += f.re;
-                a.im += f.im;
-                sm_acc[0] = a;
-            }
+        for (int t = 0; t < H; ++t)
+            if (BS_OWN(t)) c[t] = c0[cbase + t];
+        uint64_t bits = g.dbin;
+        while (bits) {
+            const int j = bs_ctz64(bits);
+            bits &= bits - 1;
+            const cx<double>* row = a2 + (size_t)j * KP + cbase;
 #pragma unroll
-            for (int col = 1; col < KB; ++col)
-                if (BS_LIVE(col)) {
-                    cx<double> a = sm_acc[col * stride];
-                    cx<double> f = sm_suf[col * stride];
-                    a.re = bfma(pre.re, f.re, a.re);
-                    a.re = bfma(-pre.im, f.im, a.re);
-                    a.im = bfma(pre.re, f.im, a.im);
-                    a.im = bfma(pre.im, f.re, a.im);
-                    sm_acc[col * stride] = a;
-                    if (col + 1 < KB - 3 || col + 1 < K) pre = cmul(pre, c[col]);
+            for (int t = 0; t < H; ++t)
+                if (BS_OWN(t)) {
+                    c[t].re -= row[t].re;
+                    c[t].im -= row[t].im;
                 }
-            if (s + 1 == len) break;
-            uint32_t neg;
-            int wch;
-            const int row = st.step(g, s, radix, &neg, &wch);
-            ws = wch ? signed_weight<double>(g.w, g.parity) : flip_sign(ws);
-            update_columns<KB>(c, a2 + (size_t)row * KP, unit_sign_d(neg), K);
+        }
+        for (int j = jb.nbin; j < jb.nrows; ++j) {
+            const int d = g.del[j];
+            if (d == 0) continue;
+            const double fd = (double)(-d);
+            const cx<double>* row = a2 + (size_t)j * KP + cbase;
+#pragma unroll
+            for (int t = 0; t < H; ++t)
+                if (BS_OWN(t)) {
+                    c[t].re = bfma(fd, row[t].re, c[t].re);
+                    c[t].im = bfma(fd, row[t].im, c[t].im);
+                }
         }
     }
-    // The 32 chunk sums of the task are plain-double running sums, so they
-    // are combined in plain double (fixed butterfly order, about 10 FP64
-    // operations per column instead of about 200 for a double-double
-    // combine); the partials of different tasks are summed in double-double
-    // by the reduce kernel.
-    for (int col = 0; col < K; ++col) {
-        cx<double> a = sm_acc[col * stride];
+    double ws = has ? signed_weight<double>(g.w, g.parity) : 0.0;
+    for (uint32_t s = 0; s < steps; ++s) {
+        // 1. suffix products over own columns (suf[t] = prod_{own u > t} c_u)
+        cx<double> suf[H];
+        cx<double> sfx = {1.0, 0.0};
+        bool first = true;
 #pragma unroll
-        for (int off = 16; off > 0; off >>= 1) {
+        for (int t = H - 1; t >= 0; --t)
+            if (BS_OWN(t)) {
+                suf[t] = sfx;
+                sfx = first ? c[t] : cmul(sfx, c[t]);
+                first = false;
+            }
+        // 2. swap Q_own with the partner lane
+        cx<double> q;
+        q.re = __shfl_xor_sync(0xffffffffu, sfx.re, 1);
+        q.im = __shfl_xor_sync(0xffffffffu, sfx.im, 1);
+        // 3. prefix pass from X = ws Q_partner
+        cx<double> pre = {ws * q.re, ws * q.im};
+#pragma unroll
+        for (int t = 0; t < H; ++t)
+            if (BS_OWN(t)) {
+                cx<double> a = sm_acc[t * stride];
+                a.re = bfma(pre.re, suf[t].re, a.re);
+                a.re = bfma(-pre.im, suf[t].im, a.re);
+                a.im = bfma(pre.re, suf[t].im, a.im);
+                a.im = bfma(pre.im, suf[t].re, a.im);
+                sm_acc[t * stride] = a;
+                if (BS_OWN(t + 1)) pre = cmul(pre, c[t]);
+            }
+        if (s + 1 >= len) {  // this lane's chunk is done: weight 0 from here on
+            ws = 0.0;
+            continue;
+        }
+        uint32_t neg;
+        int wch;
+        const int row = st.step(g, s, radix, &neg, &wch);
+        ws = wch ? signed_weight<double>(g.w, g.parity) : flip_sign(ws);
+        const cx<double>* rp = a2 + (size_t)row * KP + cbase;
+        const double cf = unit_sign_d(neg);
+#pragma unroll
+        for (int t = 0; t < H; ++t)
+            if (BS_OWN(t)) {
+                const cx<double> v = ldg_cx(rp + t);
+                c[t].re = bfma(cf, v.re, c[t].re);
+                c[t].im = bfma(cf, v.im, c[t].im);
+            }
+    }
+    // The 16 chunk sums per column are plain-double running sums, combined in
+    // plain double over lanes of equal parity (fixed butterfly order); the
+    // partials of different tasks are summed in twice double precision by
+    // the reduce kernel.  Lane h < 2 ends with the sums of its columns.
+    for (int t = 0; t < H; ++t) {
+        cx<double> a = BS_OWN(t) ? sm_acc[t * stride] : cx<double>{0.0, 0.0};
+#pragma unroll
+        for (int off = 16; off > 1; off >>= 1) {
             a.re += __shfl_down_sync(0xffffffffu, a.re, off);
             a.im += __shfl_down_sync(0xffffffffu, a.im, off);
         }
-        if (lane == 0)
-            store_partial(partials + jb.partial_off + (int64_t)local * K + col, ddv{a.re, 0.0}, ddv{a.im, 0.0});
+        if (lane < 2 && t < KH)
+            store_partial(partials + jb.partial_off + (int64_t)local * K + cbase + t, ddv{a.re, 0.0}, ddv{a.im, 0.0});
     }
+#undef BS_OWN
 }
 
 #undef BS_LIVE

@@ -243,8 +243,12 @@ __device__ void walk_task_minors_fp32(const bs_job& jb, const void* __restrict__
     bs_gray g;
     ChunkStepper st;
     st.init(g, i0, jb.nbin, jb.nrows, radix, reinterpret_cast<const uint64_t*>(radix + (BS_META_BINOM(jb) - jb.meta_off)));
-    colsum<true> c[NP];
-    seed_pairs<NP, true>(c, g, c0, a2, KP2, p0, jb.nbin, jb.nrows);
+    // 4-lane groups carry the negated imaginary parts (faster there); 2-lane
+    // groups, whose lanes hold twice the columns, save those registers and
+    // fit one more CTA per SM
+    constexpr bool NIM = G == 4;
+    colsum<NIM> c[NP];
+    seed_pairs<NP, NIM>(c, g, c0, a2, KP2, p0, jb.nbin, jb.nrows);
     float ws = has ? signed_weight<float>(g.w, g.parity) : 0.f;
     // accumulators: re = rr - ii (differenced at the fold), im
     float2 arr[NP], aii[NP], aim[NP];
@@ -282,7 +286,10 @@ __device__ void walk_task_minors_fp32(const bs_job& jb, const void* __restrict__
 #pragma unroll
         for (int p = 0; p < NP; ++p) {
             arr[p] = f2fma(pre.re, suf[p].re, arr[p]);
-            aii[p] = f2fma(pre.im, suf[p].im, aii[p]);
+            if constexpr (NIM)
+                aii[p] = f2fma(pre.im, suf[p].im, aii[p]);
+            else
+                arr[p] = f2fma(f2neg(pre.im), suf[p].im, arr[p]);
             aim[p] = f2fma(pre.re, suf[p].im, aim[p]);
             aim[p] = f2fma(pre.im, suf[p].re, aim[p]);
             if (p + 1 < NP) pre = cmul2(pre, c[p]);
@@ -311,7 +318,7 @@ __device__ void walk_task_minors_fp32(const bs_job& jb, const void* __restrict__
         int wch;
         const int row = st.step(g, s, radix, &neg, &wch);
         ws = wch ? signed_weight<float>(g.w, g.parity) : flip_sign(ws);
-        update_pairs<NP, true>(c, a2 + (size_t)row * KP2, p0, unit_sign_f(neg));
+        update_pairs<NP, NIM>(c, a2 + (size_t)row * KP2, p0, unit_sign_f(neg));
     }
 #pragma unroll
     for (int p = 0; p < NP; ++p) {
