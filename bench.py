@@ -56,6 +56,7 @@ def parse():
     ap.add_argument("--workload", default="cc", choices=["cc", "batch", "serving", "lossy", "formulas"],
                     help="cc: the headline line; the others print their own line for the other configs")
     ap.add_argument("--chains", type=int, default=64)
+    ap.add_argument("--lossy-samples", type=int, default=20, help="samples of the lossy workload")
     return ap.parse_args()
 
 
@@ -501,7 +502,7 @@ def run_lossy(args):
     import synthetic as S
     v, mdet = S.config_lossy()
     ctx = bs.Context(0)
-    ns = max(1, args.samples)
+    ns = max(1, args.lossy_samples)
     t0 = time.perf_counter()
     counts = ctx.sample_ex(v, np.ones(v.shape[1], np.int32), ns, seed=5, m_detected=mdet, mode=bs.BS_MIXED)
     dt = time.perf_counter() - t0
