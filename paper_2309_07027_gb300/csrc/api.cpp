@@ -275,7 +275,8 @@ int plan_upload(bs_ctx* c, std::vector<JobIn>& ins, bs_mode mode, Prepared& P) {
         r.kind = in.p->kind;
         r.bucket = (in.p->K + 3) >> 2;
         r.cpt = bs_chunks_per_task(r.kind, r.fp32, in.p->K);
-        r.log2L = bs_choose_log2L(in.p->C, r.cpt, BS_LOG2L_MIN_SINGLE, c->log2max[r.fp32], BS_TARGET_TASKS_SINGLE);
+        r.log2L = bs_choose_log2L(in.p->C, r.cpt, BS_LOG2L_MIN_SINGLE, c->log2max[r.fp32],
+                                  r.fp32 ? BS_TARGET_TASKS_SINGLE_FP32 : BS_TARGET_TASKS_SINGLE);
         uint64_t per = (uint64_t)r.cpt << r.log2L;
         r.ntasks = (uint32_t)((in.p->C + per - 1) / per);
         r.ncols = r.kind == BS_KIND_PERM ? 1 : in.p->K;

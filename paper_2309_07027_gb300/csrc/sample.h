@@ -18,6 +18,10 @@
 // floor of 2^3: their small jobs (early steps, heavy-collision chains sent to
 // FP64) are latency-bound, and short chunks spread them over more warps.
 #define BS_TARGET_TASKS_SINGLE 32768
+// FP32 jobs planned one call at a time aim at fewer, longer chunks: the FP32
+// walks are bound by the L1 delivery of rows, and every chunk start re-reads
+// about half the rows (4096-item batch: 3.6 % faster than with 32768).
+#define BS_TARGET_TASKS_SINGLE_FP32 8192
 #define BS_TARGET_TASKS_MANY 64
 #define BS_LOG2L_MIN_SINGLE 6
 #define BS_LOG2L_MIN_MANY 3
