@@ -180,6 +180,16 @@ def run_reference(args):
 
 
 # ---------------------------------------------------------------- multi-rank helpers
+def paper_model(samples_per_s, n=N_PHOTONS, m=M_MODES):
+    """The portable figure of the paper's performance model (Sec. 4, Eq.
+    performance): T_sampling = T0 [n (m + n) / m C(2m + n, n + 1) / C(m + n,
+    n + 1) + n^2 m]; T0 of this run (one GPU) beside the paper's fit for its
+    4-FPGA system, as context."""
+    from math import comb
+    bracket = n * (m + n) / m * comb(2 * m + n, n + 1) / comb(m + n, n + 1) + n * n * m
+    return {"T0_s": 1.0 / samples_per_s / bracket, "paper_T0_s_4_fpga": 7.5e-11, "bracket": bracket}
+
+
 def rank_seed_base(rank):
     """Seed of a rank's sample stream: ranks draw disjoint, independent
     sample sets (the samples of Sec. 4 are independent; no collective on the
@@ -380,6 +390,7 @@ def run_mine(args):
                    "parallelism": f"replicas x{world} (independent samples)"},
         "latency_ms": {"p50": statistics.median(step_ms), "p99": sorted(step_ms)[max(0, int(0.99 * len(step_ms)) - 1)],
                        "what": "per batch of samples (all chains of a batch finish together)"},
+        "paper_model": paper_model(value / world),
         "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
         "clocks": clk, "fp64_form": fp64_form, "fp64_kernels_k30": fp64_k30, "wall_s": wall,
         "fma_rates_measured": {"fp64_per_s": fp64_rate, "fp32_per_s": fp32_rate},
