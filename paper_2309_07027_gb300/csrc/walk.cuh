@@ -4,7 +4,9 @@
 // Work decomposition (Sec. 2.1: contiguous index ranges walked
 // independently, each seeded by decoding its first index):
 //   * a job's index range [0, C) is cut into chunks of L = 2^log2L addends;
-//   * a warp task is 32 consecutive chunks, one per lane;
+//   * a warp task is a run of consecutive chunks: one per lane for the
+//     permanents, one per lane pair (FP64) or per group of 2 or 4 lanes
+//     (FP32) for the Laplace minors, the group's lanes splitting the columns;
 //   * persistent warps pull tasks from a global counter (largest jobs are
 //     planned first), so uneven jobs share one launch;
 //   * every lane decodes its chunk start (re-seeding its column sums from the
@@ -25,8 +27,8 @@
 //
 // Accumulation: each lane sums its addends in plain precision for a short
 // run, folds the run into a compensated accumulator (double-double in FP64
-// mode, float-float in FP32 mode), and the 32 lanes of a task are combined in
-// double-double in a fixed shuffle order.  Tasks write one partial each; the
+// mode, float-float in FP32 mode), and the lanes of a task are combined in a
+// fixed shuffle order.  Tasks write one partial per output; the
 // reduce kernel sums them in a fixed order, so results do not depend on which
 // warp ran which task or on what else was in the launch.
 #pragma once
