@@ -15,8 +15,9 @@ minors, compensated accumulation and the weighted draw.
   roofline  the fused-minors walk kernel: algorithmic flops (per-addend count
             22K - 22, K columns) / summed kernel time (CUDA events on the
             launching stream) vs 2 x the FP32 FMA rate measured on this GPU
-  cpu_baseline  the oracle (single-threaded double-double C) on a bounded
-            prefix of one chain, scaled to samples/s by its own operation count
+  cpu_baseline  the oracle (double-double C, one process per host core) on
+            a bounded prefix of one chain per core, scaled to samples/s by its
+            own operation count; the one-core figure beside it
 
 ``--impl reference`` runs the oracle as the reference arm (CPU only).
 Multi-GPU: samples are independent, so ranks draw disjoint sample sets
@@ -117,62 +118,112 @@ def full_sample_ops(n):
     return sum(k * (k - 1) * 2.0 ** (k - 2) for k in range(2, n + 1))
 
 
-def oracle_baseline(budget_s):
-    """Time the oracle on a growing prefix of chain 0 until one run takes
-    ~budget_s / 3; report samples/s = (ops/s) / (ops of a full sample)."""
+def host_cores():
+    try:
+        return len(os.sched_getaffinity(0))
+    except AttributeError:
+        return os.cpu_count() or 1
+
+
+def _oracle_chain_prefix(job):
+    """One oracle chain prefix (pool worker; module-level so that a spawned
+    process can import it): returns (addend-column ops, seconds)."""
+    steps, seed = job
     import oracle
     import synthetic as S
     u, occ = S.config_cc(N_PHOTONS, M_MODES, SEED)
-    steps, total_t, total_ops, last = 12, 0.0, 0.0, None
+    t0 = time.perf_counter()
+    _, _, ops = oracle.cc_sample(u, occ, 1, seed=seed, max_steps=steps)
+    return ops, time.perf_counter() - t0
+
+
+def calibrate_prefix(target_s):
+    """Longest chain prefix (steps 1..s, s >= 12) whose single-threaded
+    oracle run stays under about target_s; returns (s, ops, seconds)."""
+    steps, last = 12, None
     while steps <= N_PHOTONS:
-        t0 = time.perf_counter()
-        _, _, ops = oracle.cc_sample(u, occ, 1, seed=7, max_steps=steps)
-        dt = time.perf_counter() - t0
-        total_t += dt
-        total_ops += ops
-        last = (steps, dt, ops)
-        if dt > budget_s / 3 or total_t > budget_s:
+        ops, dt = _oracle_chain_prefix((steps, 7))
+        last = (steps, ops, dt)
+        if dt > target_s:
             break
         steps += 1
-    rate = last[2] / last[1]
-    value = rate / full_sample_ops(N_PHOTONS)
-    return {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": (f"steps 1..{last[0]} of one n=30 m=60 chain (double-double C oracle, minors by direct "
-                       f"Gray BB/FG permanents) in {last[1]:.2f} s = {last[2]:.3g} addend-column ops; scaled by "
-                       f"the {full_sample_ops(N_PHOTONS):.3g} ops of a full collision-free sample")}
+    return last
+
+
+class OraclePool:
+    """One single-threaded oracle process per host core, started with spawn
+    (never fork a process that has touched the GPU).  Each run draws one
+    chain prefix per process with its own seed and reports the total
+    operations over the wall time of the whole run."""
+
+    def __init__(self, procs):
+        import multiprocessing as mp
+        self.procs = procs
+        self.pool = mp.get_context("spawn").Pool(procs)
+        self.pool.map(_oracle_chain_prefix, [(2, 7 + i) for i in range(procs)], chunksize=1)  # imports
+
+    def run(self, steps):
+        t0 = time.perf_counter()
+        res = self.pool.map(_oracle_chain_prefix, [(steps, 7 + i) for i in range(self.procs)], chunksize=1)
+        return sum(r[0] for r in res), time.perf_counter() - t0
+
+    def close(self):
+        self.pool.close()
+        self.pool.join()
+
+
+def oracle_baseline(budget_s):
+    """The oracle on the host: one core on a chain prefix calibrated to about
+    budget_s / 3, then every core at once on the same prefix length (one
+    chain per core).  samples/s = (ops/s) / (ops of a full sample)."""
+    steps, ops1, dt1 = calibrate_prefix(budget_s / 3)
+    full = full_sample_ops(N_PHOTONS)
+    one = {"value": ops1 / dt1 / full, "cores": 1}
+    procs = host_cores()
+    pool = OraclePool(procs)
+    try:
+        ops, wall = pool.run(steps)
+    finally:
+        pool.close()
+    return {"value": ops / wall / full, "unit": UNIT, "cores": procs, "kind": "oracle",
+            "one_core": one,
+            "sample": (f"steps 1..{steps} of one n=30 m=60 chain per core, {procs} cores in parallel (double-double "
+                       f"C oracle, minors by direct Gray BB/FG permanents): {ops:.3g} addend-column ops in "
+                       f"{wall:.2f} s; scaled by the {full:.3g} ops of a full collision-free sample")}
 
 
 def run_reference(args):
-    """Reference arm: the oracle on the host cores.  Warm-up calibrates a chain
-    prefix that takes about --cpu-seconds / 4; each timed step reruns it."""
+    """Reference arm: the oracle on every host core.  Warm-up calibrates a
+    chain prefix that takes about --cpu-seconds / 4 on one core; each timed
+    step runs that prefix on every core at once (one chain per core)."""
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return 0
-    import oracle
-    import synthetic as S
-    u, occ = S.config_cc(N_PHOTONS, M_MODES, SEED)
-    steps = 12
-    while steps < N_PHOTONS:
-        t0 = time.perf_counter()
-        oracle.cc_sample(u, occ, 1, seed=7, max_steps=steps)
-        if time.perf_counter() - t0 > max(args.cpu_seconds, 2.0) / 4:
-            break
-        steps += 1
-    times, ops = [], 0.0
-    for i in range(max(args.steps, 1)):
-        t0 = time.perf_counter()
-        _, _, ops = oracle.cc_sample(u, occ, 1, seed=7, max_steps=steps)
-        times.append(time.perf_counter() - t0)
-    value = (ops / statistics.mean(times)) / full_sample_ops(N_PHOTONS)
-    cb = {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
-          "sample": (f"steps 1..{steps} of one n=30 m=60 chain per step ({ops:.3g} addend-column ops), scaled by "
-                     f"the {full_sample_ops(N_PHOTONS):.3g} ops of a full collision-free sample")}
+    steps, _, _ = calibrate_prefix(max(args.cpu_seconds, 2.0) / 4)
+    procs = host_cores()
+    pool = OraclePool(procs)
+    times, ops_sum = [], 0.0
+    try:
+        for _ in range(max(args.warmup, 0)):
+            pool.run(steps)
+        for _ in range(max(args.steps, 1)):
+            ops, wall = pool.run(steps)
+            times.append(wall)
+            ops_sum += ops
+    finally:
+        pool.close()
+    full = full_sample_ops(N_PHOTONS)
+    value = ops_sum / sum(times) / full
+    cb = {"value": value, "unit": UNIT, "cores": procs, "kind": "oracle",
+          "sample": (f"steps 1..{steps} of one n=30 m=60 chain per core and step, {procs} cores in parallel "
+                     f"({ops_sum / len(times):.3g} addend-column ops per step), scaled by the {full:.3g} ops of a "
+                     f"full collision-free sample")}
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000 * statistics.mean(times),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64x2 (double-double)",
             "data": "synthetic (seeded Haar-random 60-mode unitary)",
             "config": {"workload": "cc_sampling_n30_m60", "n": N_PHOTONS, "m": M_MODES,
-                       "samples_per_step": "bounded chain prefix on the host (oracle)"},
+                       "samples_per_step": f"bounded chain prefix per host core (oracle, {procs} cores)"},
             "cpu_baseline": cb,
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)

@@ -1,0 +1,34 @@
+"""The benchmark's reference arm (the oracle on the host cores) on CPU: one
+JSON line from rank 0 with the contract's keys, nothing from other ranks."""
+import json
+import os
+import subprocess
+import sys
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+CMD = [sys.executable, os.path.join(ROOT, "bench.py"), "--impl", "reference", "--steps", "1", "--warmup", "0",
+       "--cpu-seconds", "0.5"]
+
+
+def _run(rank):
+    env = dict(os.environ, RANK=str(rank))
+    return subprocess.run(CMD, cwd=ROOT, env=env, capture_output=True, text=True, timeout=300)
+
+
+def test_reference_arm_prints_one_line():
+    r = _run(0)
+    assert r.returncode == 0, r.stderr[-2000:]
+    lines = [l for l in r.stdout.splitlines() if l.strip()]
+    assert len(lines) == 1
+    d = json.loads(lines[0])
+    assert d["impl"] == "reference" and d["unit"] == "samples/s" and d["higher_is_better"] is True
+    assert d["value"] > 0 and d["cpu_baseline"]["value"] == d["value"]
+    assert d["cpu_baseline"]["kind"] == "oracle" and d["cpu_baseline"]["cores"] >= 1
+    assert d["e2e"] == {"value": d["value"], "unit": "samples/s", "h2d_bytes_per_step": 0,
+                        "d2h_bytes_per_step": 0}
+    assert d["config"]["workload"] == "cc_sampling_n30_m60"
+
+
+def test_reference_arm_other_ranks_are_silent():
+    r = _run(1)
+    assert r.returncode == 0 and r.stdout.strip() == ""
