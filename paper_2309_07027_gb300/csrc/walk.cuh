@@ -194,6 +194,15 @@ struct ChunkStepper {
         parity0 = g.parity;
         nbin = nb;
     }
+    // The step to index i0 + u when it moves a binary digit (ctz(u) < nbin,
+    // which the caller guarantees): returns the row, *neg as in step().
+    __device__ __forceinline__ int step_bin(uint32_t u, uint32_t* neg) {
+        const int t = __ffs((int)u) - 1;
+        const uint32_t was = (dlo >> t) & 1u;
+        dlo ^= 1u << t;
+        *neg = was ^ 1u;
+        return t;
+    }
     // Move from index i0 + s to i0 + s + 1.  Returns the digit row; *neg is 1
     // when the column sums move by -2a_row (Delta rises), 0 for +2a_row;
     // *wch is 1 when the binomial weight changed (then g.w, g.parity are

@@ -209,19 +209,101 @@ __device__ void walk_task_perm_fp32(const bs_job& jb, const void* __restrict__ d
 // The lanes run the same instructions; a warp task covers 32 / G chunks.  Pad
 // columns are neutral (sum 1), so every lane runs all its pairs without
 // tests.  All lanes run the warp's longest chunk length: a lane whose chunk is
-// shorter (the job's last chunk) or absent stops stepping and continues with
-// weight 0, so the shuffles always have the full warp.  Float-float fold
-// targets live in shared memory, [col][thread]; the cross-lane sums stay in
-// float-float.
+// shorter (the job's last chunk) or absent continues with weight 0, so the
+// shuffles always have the full warp.  Float-float fold targets live in
+// shared memory, [col][thread]; the cross-lane sums stay in float-float.
+//
+// Schedule.  Chunk starts are multiples of L, so at step s every lane moves
+// the same digit: a binary digit (row ctz(s + 1)) unless s + 1 is a multiple
+// of 2^nbin.  The walk therefore runs in blocks that end at every such step
+// and at every fold point (s + 1 a multiple of FOLD); inside a block the loop
+// body is branch-free and software-pipelined: the prefix pass of addend s
+// (which reads the column sums of s) and the step plus steps 1-2 of addend
+// s + 1 are independent, so the scheduler can overlap the shuffles and the
+// dependent product chains of one addend with the arithmetic of the other.
+// A lane past the end of its chunk keeps stepping binary digits inside a
+// block (any row < nbin is a valid row; its weight is 0) and stops stepping
+// at block ends, where the mixed-radix step is taken.
+
+// Steps 1-2 for the current column sums: suffix products, {Q_even, Q_odd} and
+// the other lanes' product Q'.
+template <int NP, int G, bool NIM>
+__device__ __forceinline__ void minors_suffix(const colsum<NIM> (&c)[NP], cx2 (&suf)[NP], cx<float>& qe,
+                                              cx<float>& qo, cx<float>& qx) {
+    suf[NP - 1] = cx2{make_float2(1.f, 1.f), make_float2(0.f, 0.f)};
+    cx2 sfx = as_cx2(c[NP - 1]);
+#pragma unroll
+    for (int p = NP - 2; p >= 0; --p) {
+        suf[p] = sfx;
+        sfx = cmul2(sfx, c[p]);
+    }
+    qe = cx<float>{sfx.re.x, sfx.im.x};
+    qo = cx<float>{sfx.re.y, sfx.im.y};
+    const cx<float> qown = cmul(qe, qo);
+    qx.re = __shfl_xor_sync(0xffffffffu, qown.re, 1);
+    qx.im = __shfl_xor_sync(0xffffffffu, qown.im, 1);
+    if constexpr (G == 4) {
+        const cx<float> pair = cmul(qown, qx);
+        cx<float> q2;
+        q2.re = __shfl_xor_sync(0xffffffffu, pair.re, 2);
+        q2.im = __shfl_xor_sync(0xffffffffu, pair.im, 2);
+        qx = cmul(qx, q2);
+    }
+}
+
+// Step 3: the packed prefix pass from {X Q_odd, X Q_even}, X = ws Q'.  The
+// accumulators hold re = rr - ii as two sums when NIM (differenced at the
+// fold), else as one.
+template <int NP, bool NIM>
+__device__ __forceinline__ void minors_prefix(const colsum<NIM> (&c)[NP], const cx2 (&suf)[NP], cx<float> qe,
+                                              cx<float> qo, cx<float> qx, float ws, float2 (&arr)[NP],
+                                              float2 (&aii)[NP], float2 (&aim)[NP]) {
+    const cx<float> x = {ws * qx.re, ws * qx.im};
+    const cx<float> xe = cmul(x, qo), xo = cmul(x, qe);
+    cx2 pre = {make_float2(xe.re, xo.re), make_float2(xe.im, xo.im)};
+#pragma unroll
+    for (int p = 0; p < NP; ++p) {
+        arr[p] = f2fma(pre.re, suf[p].re, arr[p]);
+        if constexpr (NIM)
+            aii[p] = f2fma(pre.im, suf[p].im, aii[p]);
+        else
+            arr[p] = f2fma(f2neg(pre.im), suf[p].im, arr[p]);
+        aim[p] = f2fma(pre.re, suf[p].im, aim[p]);
+        aim[p] = f2fma(pre.im, suf[p].re, aim[p]);
+        if (p + 1 < NP) pre = cmul2(pre, c[p]);
+    }
+}
+
+// Fold the plain-float runs into the float-float sums in shared memory.
+template <int NP>
+__device__ __forceinline__ void minors_fold(float4* __restrict__ sm_ff, int stride, float2 (&arr)[NP],
+                                            float2 (&aii)[NP], float2 (&aim)[NP]) {
+#pragma unroll
+    for (int p = 0; p < NP; ++p) {
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            float4* slot = sm_ff + (2 * p + h) * stride;
+            float4 f = *slot;
+            ffv re = {f.x, f.y}, im = {f.z, f.w};
+            re = ff_add_f(re, h ? arr[p].y - aii[p].y : arr[p].x - aii[p].x);
+            im = ff_add_f(im, h ? aim[p].y : aim[p].x);
+            *slot = make_float4(re.hi, re.lo, im.hi, im.lo);
+        }
+        arr[p] = aii[p] = aim[p] = make_float2(0.f, 0.f);
+    }
+}
+
 template <int KB>
 __device__ void walk_task_minors_fp32(const bs_job& jb, const void* __restrict__ data_v,
                                       const int* __restrict__ radix, bs_zdd* __restrict__ partials, uint32_t local,
                                       int lane, float4* __restrict__ sm_ff, int stride) {
     constexpr uint32_t FOLD = 32;
+    constexpr int LOG2_FOLD = 5;
     constexpr int G = BS_MINORS_FP32_GROUP_KB(KB);
     constexpr int NP = KB / (2 * G);
     constexpr int CPT = 32 / G;
     static_assert(KB % (2 * G) == 0, "bucket must split into G groups of column pairs");
+    static_assert(FOLD == 1u << LOG2_FOLD, "fold length is a power of two");
     const int K = jb.K;
     constexpr int KP2 = KB / 2;  // pairs per row: BS_ROW_STRIDE(K) = KB in the bucket
     const int q = lane & (G - 1);
@@ -239,7 +321,7 @@ __device__ void walk_task_minors_fp32(const bs_job& jb, const void* __restrict__
         const uint64_t rem = jb.C - i0;
         len = (uint32_t)(rem < (1ull << jb.log2L) ? rem : (1ull << jb.log2L));
     }
-    const uint32_t steps = __reduce_max_sync(0xffffffffu, len);
+    const uint32_t steps = __reduce_max_sync(0xffffffffu, len);  // >= 1: a task's first chunk exists
     bs_gray g;
     ChunkStepper st;
     st.init(g, i0, jb.nbin, jb.nrows, radix, reinterpret_cast<const uint64_t*>(radix + (BS_META_BINOM(jb) - jb.meta_off)));
@@ -250,88 +332,41 @@ __device__ void walk_task_minors_fp32(const bs_job& jb, const void* __restrict__
     colsum<NIM> c[NP];
     seed_pairs<NP, NIM>(c, g, c0, a2, KP2, p0, jb.nbin, jb.nrows);
     float ws = has ? signed_weight<float>(g.w, g.parity) : 0.f;
-    // accumulators: re = rr - ii (differenced at the fold), im
     float2 arr[NP], aii[NP], aim[NP];
 #pragma unroll
     for (int p = 0; p < NP; ++p) arr[p] = aii[p] = aim[p] = make_float2(0.f, 0.f);
-    uint32_t run = 0;
-    for (uint32_t s = 0; s < steps; ++s) {
-        // 1. packed suffix products over own pairs, from 1
-        cx2 suf[NP];
-        suf[NP - 1] = cx2{make_float2(1.f, 1.f), make_float2(0.f, 0.f)};
-        cx2 sfx = as_cx2(c[NP - 1]);
-#pragma unroll
-        for (int p = NP - 2; p >= 0; --p) {
-            suf[p] = sfx;
-            sfx = cmul2(sfx, c[p]);
+    cx2 suf[NP];
+    cx<float> qe, qo, qx;
+    minors_suffix<NP, G, NIM>(c, suf, qe, qo, qx);
+    // blocks end where s + 1 is a multiple of min(FOLD, 2^nbin)
+    const uint32_t block_mask = (1u << min(jb.nbin, LOG2_FOLD)) - 1u;
+    uint32_t s = 0;
+    for (;;) {
+        const uint32_t e = min(steps - 1u, s | block_mask);
+        for (; s < e; ++s) {
+            minors_prefix<NP, NIM>(c, suf, qe, qo, qx, ws, arr, aii, aim);
+            uint32_t neg;
+            const int row = st.step_bin(s + 1u, &neg);
+            ws = s + 1u < len ? flip_sign(ws) : 0.f;
+            update_pairs<NP, NIM>(c, a2 + (size_t)row * KP2, p0, unit_sign_f(neg));
+            minors_suffix<NP, G, NIM>(c, suf, qe, qo, qx);
         }
-        // {Q_even, Q_odd} = sfx; Q = Q_even Q_odd
-        const cx<float> qe = {sfx.re.x, sfx.im.x}, qo = {sfx.re.y, sfx.im.y};
-        const cx<float> qown = cmul(qe, qo);
-        // 2. product of the other lanes' column groups
-        cx<float> qx;
-        qx.re = __shfl_xor_sync(0xffffffffu, qown.re, 1);
-        qx.im = __shfl_xor_sync(0xffffffffu, qown.im, 1);
-        if constexpr (G == 4) {
-            const cx<float> pair = cmul(qown, qx);
-            cx<float> q2;
-            q2.re = __shfl_xor_sync(0xffffffffu, pair.re, 2);
-            q2.im = __shfl_xor_sync(0xffffffffu, pair.im, 2);
-            qx = cmul(qx, q2);
-        }
-        // 3. packed prefix pass from {X Q_odd, X Q_even}, X = ws Q'
-        const cx<float> x = {ws * qx.re, ws * qx.im};
-        const cx<float> xe = cmul(x, qo), xo = cmul(x, qe);
-        cx2 pre = {make_float2(xe.re, xo.re), make_float2(xe.im, xo.im)};
-#pragma unroll
-        for (int p = 0; p < NP; ++p) {
-            arr[p] = f2fma(pre.re, suf[p].re, arr[p]);
-            if constexpr (NIM)
-                aii[p] = f2fma(pre.im, suf[p].im, aii[p]);
-            else
-                arr[p] = f2fma(f2neg(pre.im), suf[p].im, arr[p]);
-            aim[p] = f2fma(pre.re, suf[p].im, aim[p]);
-            aim[p] = f2fma(pre.im, suf[p].re, aim[p]);
-            if (p + 1 < NP) pre = cmul2(pre, c[p]);
-        }
-        if (++run == FOLD) {
-            run = 0;
-#pragma unroll
-            for (int p = 0; p < NP; ++p) {
-#pragma unroll
-                for (int h = 0; h < 2; ++h) {
-                    float4* slot = sm_ff + (2 * p + h) * stride;
-                    float4 f = *slot;
-                    ffv re = {f.x, f.y}, im = {f.z, f.w};
-                    re = ff_add_f(re, h ? arr[p].y - aii[p].y : arr[p].x - aii[p].x);
-                    im = ff_add_f(im, h ? aim[p].y : aim[p].x);
-                    *slot = make_float4(re.hi, re.lo, im.hi, im.lo);
-                }
-                arr[p] = aii[p] = aim[p] = make_float2(0.f, 0.f);
-            }
-        }
-        if (s + 1 >= len) {  // this lane's chunk is done: weight 0 from here on
+        minors_prefix<NP, NIM>(c, suf, qe, qo, qx, ws, arr, aii, aim);
+        if (((s + 1u) & (FOLD - 1u)) == 0) minors_fold<NP>(sm_ff, stride, arr, aii, aim);
+        if (s + 1u >= steps) break;
+        if (s + 1u < len) {
+            uint32_t neg;
+            int wch;
+            const int row = st.step(g, s, radix, &neg, &wch);
+            ws = wch ? signed_weight<float>(g.w, g.parity) : flip_sign(ws);
+            update_pairs<NP, NIM>(c, a2 + (size_t)row * KP2, p0, unit_sign_f(neg));
+        } else {
             ws = 0.f;
-            continue;
         }
-        uint32_t neg;
-        int wch;
-        const int row = st.step(g, s, radix, &neg, &wch);
-        ws = wch ? signed_weight<float>(g.w, g.parity) : flip_sign(ws);
-        update_pairs<NP, NIM>(c, a2 + (size_t)row * KP2, p0, unit_sign_f(neg));
+        minors_suffix<NP, G, NIM>(c, suf, qe, qo, qx);
+        ++s;
     }
-#pragma unroll
-    for (int p = 0; p < NP; ++p) {
-#pragma unroll
-        for (int h = 0; h < 2; ++h) {
-            float4* slot = sm_ff + (2 * p + h) * stride;
-            float4 f = *slot;
-            ffv re = {f.x, f.y}, im = {f.z, f.w};
-            re = ff_add_f(re, h ? arr[p].y - aii[p].y : arr[p].x - aii[p].x);
-            im = ff_add_f(im, h ? aim[p].y : aim[p].x);
-            *slot = make_float4(re.hi, re.lo, im.hi, im.lo);
-        }
-    }
+    minors_fold<NP>(sm_ff, stride, arr, aii, aim);
     // reduce over the chunks of the task in float-float (lanes of equal q);
     // lane q < G ends with the sums of its columns
     const int KH = min(2 * NP, max(K - cbase, 0));
