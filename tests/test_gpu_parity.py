@@ -181,6 +181,50 @@ def test_minors_with_repeats_and_empty(ctx, mode):
     assert got[0] == 1
 
 
+# (row multiplicities, binary digits after pinning one M = 1 row): binary
+# digit counts 1..6 with chunks of 64 addends, so the FP32 minors walk ends
+# its branch-free blocks every 2^nbin steps (nbin < 5) or at every fold
+# point, takes the mixed-radix step at each block end, and (C not a multiple
+# of 64) lets a lane run past the end of a short last chunk inside a block.
+# Each case stays in FP32 under the MIXED rule (predicted error at least
+# 2^0.05 below its threshold); with no binary digit (M >= 2 everywhere after
+# pinning) the rule keeps no case of more than one row in FP32.
+BLOCK_CASES = [
+    ([1, 1] + [2] * 7, 1),
+    ([1] * 3 + [2] * 6, 2),
+    ([1] * 4 + [2] * 5, 3),
+    ([1] * 5 + [2] * 4, 4),
+    ([1] * 6 + [2] * 3, 5),
+    ([1] * 7, 6),
+    ([1, 1] + [2] * 6 + [3], 1),
+    ([1] * 3 + [2] * 6 + [3], 2),
+    ([1] * 4 + [2] * 5 + [3], 3),
+    ([1] * 7 + [2, 2, 3], 6),
+]
+
+
+@pytest.mark.parametrize("M,nbin", BLOCK_CASES)
+def test_fp32_minors_block_schedule(ctx, M, nbin):
+    """MIXED fused minors in the FP32 kernel (checked from the statistics)
+    against the oracle's permanent of each column-deleted matrix."""
+    M = np.array(M, dtype=np.int32)
+    K = int(M.sum()) + 1
+    ones = int((M == 1).sum())
+    assert nbin == ones - 1
+    u = S.haar_unitary(32, 700 + nbin)
+    g = S.rng(710 + nbin)
+    a = u[g.permutation(32)[: len(M)]][:, g.permutation(32)[:K]]
+    N = np.ones(K, dtype=np.int32)
+    ctx.reset_stats()
+    got = ctx.laplace_minors(a, M, N, mode=1)
+    st = ctx.stats()
+    assert st["addends"][1] > 0 and st["addends"][0] == 0, "expected the FP32 kernel"
+    for l in range(K):
+        keep = [j for j in range(K) if j != l]
+        ref = ref_perm(a[:, keep], M, N[keep])
+        assert abs(got[l] - ref) <= TOL[1] * minor_scale(a, M, N, l), (nbin, l, got[l], ref)
+
+
 MINOR_WIDTHS = [13, 17, 20, 21, 24, 25, 26, 28, 29, 31, 32, 33, 36, 37, 40, 41, 44, 45, 48]
 
 
