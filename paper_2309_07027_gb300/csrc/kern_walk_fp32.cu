@@ -34,12 +34,11 @@ __global__ void __launch_bounds__(kPermBlock) walk_fp32_perm_kernel(WalkArgs a) 
 }
 
 // Resident CTAs per SM the fused-minor kernel is compiled for: the most
-// that still needs no register spills.  4-lane groups of up to 3 column
-// pairs: 96 registers, 5 CTAs; of 4 pairs: 128 registers, 4 CTAs.  2-lane
-// groups (no negated imaginary copies): up to 20 columns 128 registers, 4
-// CTAs; 28 columns 168 registers, 3 CTAs; wider ones are left to the
-// compiler.  (Width 28 at 3 CTAs instead of 2: k = 25..28 sampler steps
-// 15-18 % faster.)
+// that measured fastest.  4-lane groups of up to 3 column pairs: 96
+// registers, 5 CTAs; of 4 pairs: 128 registers, 4 CTAs.  2-lane groups: up
+// to 20 columns 128 registers, 4 CTAs; 28 columns 168 registers, 3 CTAs
+// (8 bytes spilled; at 2 CTAs the k = 25..28 sampler steps are 15-18 %
+// slower); wider ones are left to the compiler.
 template <int KB>
 struct MinorsMinBlocks {
     static constexpr int G = BS_MINORS_FP32_GROUP_KB(KB);

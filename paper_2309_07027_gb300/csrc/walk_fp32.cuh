@@ -11,14 +11,10 @@
 // scheduler independent work.
 //
 // The one minus sign of a complex product, re(a b) = re a re b - im a im b,
-// is handled two ways, each where it measured faster.  In the fused minors
-// the column sums carry it: each column keeps nim = -im next to im (one extra
-// packed FMA per pair and step), so re(a c) = re a re c + im a nim c, and the
-// accumulators keep re(pre suf) as two sums (re re and im im) differenced
-// when they are folded into float-float.  In the permanent the product is
-// written with the negation (no nim: one packed FMA less per pair and step,
-// 7 % more permanents/s on the 4096-item batch; the minors were 1 % slower
-// that way).
+// is a negation of the packed product im a im b before the packed FMA.
+// (Carrying nim = -im beside every column sum instead costs one packed FMA
+// per pair and step on the FMA pipe, which bounds these kernels: without it
+// the permanent runs 7 % and the sampler's fused minors 1.4 % faster.)
 //
 // Rounding: every product, update and accumulation rounds exactly as the
 // scalar single-precision form of the same expression order (packed
@@ -41,35 +37,20 @@ struct cx2 {
 
 __device__ __forceinline__ float2 f2neg(float2 x) { return make_float2(-x.x, -x.y); }
 
-// A pair of column sums; NIM: with their negated imaginary parts.
-template <bool NIM>
-struct colsum;
-template <>
-struct colsum<true> {
-    float2 re, im, nim;
-};
-template <>
-struct colsum<false> {
+// A pair of column sums.
+struct colsum {
     float2 re, im;
 };
 
-// a * c for both halves.  With nim no negation is written; without it the
-// product a.im c.im is negated before the packed FMA.
-__device__ __forceinline__ cx2 cmul2(cx2 a, const colsum<true>& c) {
-    cx2 r;
-    r.re = f2fma(a.re, c.re, f2mul(a.im, c.nim));
-    r.im = f2fma(a.re, c.im, f2mul(a.im, c.re));
-    return r;
-}
-__device__ __forceinline__ cx2 cmul2(cx2 a, const colsum<false>& c) {
+// a * c for both halves.
+__device__ __forceinline__ cx2 cmul2(cx2 a, const colsum& c) {
     cx2 r;
     r.re = f2fma(a.re, c.re, f2neg(f2mul(a.im, c.im)));
     r.im = f2fma(a.re, c.im, f2mul(a.im, c.re));
     return r;
 }
 
-template <bool NIM>
-__device__ __forceinline__ cx2 as_cx2(const colsum<NIM>& c) { return cx2{c.re, c.im}; }
+__device__ __forceinline__ cx2 as_cx2(const colsum& c) { return cx2{c.re, c.im}; }
 
 // Scalar complex product of the two halves (even * odd).
 __device__ __forceinline__ cx<float> halves_product(cx2 a) {
@@ -84,8 +65,8 @@ __device__ __forceinline__ void load_pair(const float4* __restrict__ row, int p,
 }
 
 // c[p] += cf * row pair p for the NP pairs starting at pair p0.
-template <int NP, bool NIM>
-__device__ __forceinline__ void update_pairs(colsum<NIM> (&c)[NP], const float4* __restrict__ row, int p0, float cf) {
+template <int NP>
+__device__ __forceinline__ void update_pairs(colsum (&c)[NP], const float4* __restrict__ row, int p0, float cf) {
     const float2 f = f2splat(cf);
 #pragma unroll
     for (int p = 0; p < NP; ++p) {
@@ -93,14 +74,13 @@ __device__ __forceinline__ void update_pairs(colsum<NIM> (&c)[NP], const float4*
         load_pair(row, p0 + p, re, im);
         c[p].re = f2fma(f, re, c[p].re);
         c[p].im = f2fma(f, im, c[p].im);
-        if constexpr (NIM) c[p].nim = f2fma(f2splat(-cf), im, c[p].nim);
     }
 }
 
 // Seed NP column pairs (from pair p0) of the decoded state:
 // c = c0 - sum_j Delta_j 2a_j; rows have KP / 2 pairs.
-template <int NP, bool NIM>
-__device__ __forceinline__ void seed_pairs(colsum<NIM> (&c)[NP], const bs_gray& g, const float4* __restrict__ c0,
+template <int NP>
+__device__ __forceinline__ void seed_pairs(colsum (&c)[NP], const bs_gray& g, const float4* __restrict__ c0,
                                            const float4* __restrict__ a2, int KP2, int p0, int nbin, int nrows) {
 #pragma unroll
     for (int p = 0; p < NP; ++p) load_pair(c0, p0 + p, c[p].re, c[p].im);
@@ -130,10 +110,6 @@ __device__ __forceinline__ void seed_pairs(colsum<NIM> (&c)[NP], const bs_gray& 
             c[p].im = f2fma(fd, im, c[p].im);
         }
     }
-    if constexpr (NIM) {
-#pragma unroll
-        for (int p = 0; p < NP; ++p) c[p].nim = f2neg(c[p].im);
-    }
 }
 
 // ---------------------------------------------------------------- one task: permanent
@@ -158,8 +134,8 @@ __device__ void walk_task_perm_fp32(const bs_job& jb, const void* __restrict__ d
         bs_gray g;
         ChunkStepper st;
         st.init(g, i0, jb.nbin, jb.nrows, radix, reinterpret_cast<const uint64_t*>(radix + (BS_META_BINOM(jb) - jb.meta_off)));
-        colsum<false> c[NP];
-        seed_pairs<NP, false>(c, g, c0, a2, KP2, 0, jb.nbin, jb.nrows);
+        colsum c[NP];
+        seed_pairs<NP>(c, g, c0, a2, KP2, 0, jb.nbin, jb.nrows);
         float ws = signed_weight<float>(g.w, g.parity);
         cx<float> acc = {0.f, 0.f};
         uint32_t run = 0;
@@ -181,7 +157,7 @@ __device__ void walk_task_perm_fp32(const bs_job& jb, const void* __restrict__ d
             int wch;
             const int row = st.step(g, s, radix, &neg, &wch);
             ws = wch ? signed_weight<float>(g.w, g.parity) : flip_sign(ws);
-            update_pairs<NP, false>(c, a2 + (size_t)row * KP2, 0, unit_sign_f(neg));
+            update_pairs<NP>(c, a2 + (size_t)row * KP2, 0, unit_sign_f(neg));
         }
         fre = ff_add_f(fre, acc.re);
         fim = ff_add_f(fim, acc.im);
@@ -227,8 +203,8 @@ __device__ void walk_task_perm_fp32(const bs_job& jb, const void* __restrict__ d
 
 // Steps 1-2 for the current column sums: suffix products, {Q_even, Q_odd} and
 // the other lanes' product Q'.
-template <int NP, int G, bool NIM>
-__device__ __forceinline__ void minors_suffix(const colsum<NIM> (&c)[NP], cx2 (&suf)[NP], cx<float>& qe,
+template <int NP, int G>
+__device__ __forceinline__ void minors_suffix(const colsum (&c)[NP], cx2 (&suf)[NP], cx<float>& qe,
                                               cx<float>& qo, cx<float>& qx) {
     suf[NP - 1] = cx2{make_float2(1.f, 1.f), make_float2(0.f, 0.f)};
     cx2 sfx = as_cx2(c[NP - 1]);
@@ -251,23 +227,18 @@ __device__ __forceinline__ void minors_suffix(const colsum<NIM> (&c)[NP], cx2 (&
     }
 }
 
-// Step 3: the packed prefix pass from {X Q_odd, X Q_even}, X = ws Q'.  The
-// accumulators hold re = rr - ii as two sums when NIM (differenced at the
-// fold), else as one.
-template <int NP, bool NIM>
-__device__ __forceinline__ void minors_prefix(const colsum<NIM> (&c)[NP], const cx2 (&suf)[NP], cx<float> qe,
-                                              cx<float> qo, cx<float> qx, float ws, float2 (&arr)[NP],
-                                              float2 (&aii)[NP], float2 (&aim)[NP]) {
+// Step 3: the packed prefix pass from {X Q_odd, X Q_even}, X = ws Q'.
+template <int NP>
+__device__ __forceinline__ void minors_prefix(const colsum (&c)[NP], const cx2 (&suf)[NP], cx<float> qe,
+                                              cx<float> qo, cx<float> qx, float ws, float2 (&are)[NP],
+                                              float2 (&aim)[NP]) {
     const cx<float> x = {ws * qx.re, ws * qx.im};
     const cx<float> xe = cmul(x, qo), xo = cmul(x, qe);
     cx2 pre = {make_float2(xe.re, xo.re), make_float2(xe.im, xo.im)};
 #pragma unroll
     for (int p = 0; p < NP; ++p) {
-        arr[p] = f2fma(pre.re, suf[p].re, arr[p]);
-        if constexpr (NIM)
-            aii[p] = f2fma(pre.im, suf[p].im, aii[p]);
-        else
-            arr[p] = f2fma(f2neg(pre.im), suf[p].im, arr[p]);
+        are[p] = f2fma(pre.re, suf[p].re, are[p]);
+        are[p] = f2fma(f2neg(pre.im), suf[p].im, are[p]);
         aim[p] = f2fma(pre.re, suf[p].im, aim[p]);
         aim[p] = f2fma(pre.im, suf[p].re, aim[p]);
         if (p + 1 < NP) pre = cmul2(pre, c[p]);
@@ -276,8 +247,8 @@ __device__ __forceinline__ void minors_prefix(const colsum<NIM> (&c)[NP], const 
 
 // Fold the plain-float runs into the float-float sums in shared memory.
 template <int NP>
-__device__ __forceinline__ void minors_fold(float4* __restrict__ sm_ff, int stride, float2 (&arr)[NP],
-                                            float2 (&aii)[NP], float2 (&aim)[NP]) {
+__device__ __forceinline__ void minors_fold(float4* __restrict__ sm_ff, int stride, float2 (&are)[NP],
+                                            float2 (&aim)[NP]) {
 #pragma unroll
     for (int p = 0; p < NP; ++p) {
 #pragma unroll
@@ -285,11 +256,11 @@ __device__ __forceinline__ void minors_fold(float4* __restrict__ sm_ff, int stri
             float4* slot = sm_ff + (2 * p + h) * stride;
             float4 f = *slot;
             ffv re = {f.x, f.y}, im = {f.z, f.w};
-            re = ff_add_f(re, h ? arr[p].y - aii[p].y : arr[p].x - aii[p].x);
+            re = ff_add_f(re, h ? are[p].y : are[p].x);
             im = ff_add_f(im, h ? aim[p].y : aim[p].x);
             *slot = make_float4(re.hi, re.lo, im.hi, im.lo);
         }
-        arr[p] = aii[p] = aim[p] = make_float2(0.f, 0.f);
+        are[p] = aim[p] = make_float2(0.f, 0.f);
     }
 }
 
@@ -325,48 +296,44 @@ __device__ void walk_task_minors_fp32(const bs_job& jb, const void* __restrict__
     bs_gray g;
     ChunkStepper st;
     st.init(g, i0, jb.nbin, jb.nrows, radix, reinterpret_cast<const uint64_t*>(radix + (BS_META_BINOM(jb) - jb.meta_off)));
-    // 4-lane groups carry the negated imaginary parts (faster there); 2-lane
-    // groups, whose lanes hold twice the columns, save those registers and
-    // fit one more CTA per SM
-    constexpr bool NIM = G == 4;
-    colsum<NIM> c[NP];
-    seed_pairs<NP, NIM>(c, g, c0, a2, KP2, p0, jb.nbin, jb.nrows);
+    colsum c[NP];
+    seed_pairs<NP>(c, g, c0, a2, KP2, p0, jb.nbin, jb.nrows);
     float ws = has ? signed_weight<float>(g.w, g.parity) : 0.f;
-    float2 arr[NP], aii[NP], aim[NP];
+    float2 are[NP], aim[NP];
 #pragma unroll
-    for (int p = 0; p < NP; ++p) arr[p] = aii[p] = aim[p] = make_float2(0.f, 0.f);
+    for (int p = 0; p < NP; ++p) are[p] = aim[p] = make_float2(0.f, 0.f);
     cx2 suf[NP];
     cx<float> qe, qo, qx;
-    minors_suffix<NP, G, NIM>(c, suf, qe, qo, qx);
+    minors_suffix<NP, G>(c, suf, qe, qo, qx);
     // blocks end where s + 1 is a multiple of min(FOLD, 2^nbin)
     const uint32_t block_mask = (1u << min(jb.nbin, LOG2_FOLD)) - 1u;
     uint32_t s = 0;
     for (;;) {
         const uint32_t e = min(steps - 1u, s | block_mask);
         for (; s < e; ++s) {
-            minors_prefix<NP, NIM>(c, suf, qe, qo, qx, ws, arr, aii, aim);
+            minors_prefix<NP>(c, suf, qe, qo, qx, ws, are, aim);
             uint32_t neg;
             const int row = st.step_bin(s + 1u, &neg);
             ws = s + 1u < len ? flip_sign(ws) : 0.f;
-            update_pairs<NP, NIM>(c, a2 + (size_t)row * KP2, p0, unit_sign_f(neg));
-            minors_suffix<NP, G, NIM>(c, suf, qe, qo, qx);
+            update_pairs<NP>(c, a2 + (size_t)row * KP2, p0, unit_sign_f(neg));
+            minors_suffix<NP, G>(c, suf, qe, qo, qx);
         }
-        minors_prefix<NP, NIM>(c, suf, qe, qo, qx, ws, arr, aii, aim);
-        if (((s + 1u) & (FOLD - 1u)) == 0) minors_fold<NP>(sm_ff, stride, arr, aii, aim);
+        minors_prefix<NP>(c, suf, qe, qo, qx, ws, are, aim);
+        if (((s + 1u) & (FOLD - 1u)) == 0) minors_fold<NP>(sm_ff, stride, are, aim);
         if (s + 1u >= steps) break;
         if (s + 1u < len) {
             uint32_t neg;
             int wch;
             const int row = st.step(g, s, radix, &neg, &wch);
             ws = wch ? signed_weight<float>(g.w, g.parity) : flip_sign(ws);
-            update_pairs<NP, NIM>(c, a2 + (size_t)row * KP2, p0, unit_sign_f(neg));
+            update_pairs<NP>(c, a2 + (size_t)row * KP2, p0, unit_sign_f(neg));
         } else {
             ws = 0.f;
         }
-        minors_suffix<NP, G, NIM>(c, suf, qe, qo, qx);
+        minors_suffix<NP, G>(c, suf, qe, qo, qx);
         ++s;
     }
-    minors_fold<NP>(sm_ff, stride, arr, aii, aim);
+    minors_fold<NP>(sm_ff, stride, are, aim);
     // reduce over the chunks of the task in float-float (lanes of equal q);
     // lane q < G ends with the sums of its columns
     const int KH = min(2 * NP, max(K - cbase, 0));
