@@ -33,17 +33,18 @@ __global__ void __launch_bounds__(kPermBlock) walk_fp32_perm_kernel(WalkArgs a) 
     }
 }
 
-// Resident CTAs per SM the fused-minor kernel is compiled for: the most
-// that measured fastest.  4-lane groups of up to 3 column pairs: 96
-// registers, 5 CTAs; of 4 pairs: 128 registers, 4 CTAs.  2-lane groups: up
-// to 20 columns 128 registers, 4 CTAs; 28 columns 168 registers, 3 CTAs
-// (8 bytes spilled; at 2 CTAs the k = 25..28 sampler steps are 15-18 %
-// slower); wider ones are left to the compiler.
+// Resident CTAs per SM the fused-minor kernel is compiled for: the count
+// that measured fastest.  4-lane groups: width 24 at 96 registers, 5 CTAs;
+// width 48 left to the compiler (232 registers, 2 CTAs).  2-lane groups: up
+// to 20 columns 128 registers, 4 CTAs; 28 and 32 columns 168 registers, 3
+// CTAs (8 and 132 bytes spilled, outside the inner loop by the timings: at
+// 2 CTAs the k = 25..28 sampler steps are 15-18 % and the k = 29, 30 steps
+// 12 % slower); 36 to 44 columns 2 CTAs.
 template <int KB>
 struct MinorsMinBlocks {
     static constexpr int G = BS_MINORS_FP32_GROUP_KB(KB);
     static constexpr int NP = KB / (2 * G);
-    static constexpr int value = G == 4 ? (NP <= 3 ? 5 : (NP == 4 ? 4 : 1)) : (KB <= 20 ? 4 : (KB <= 28 ? 3 : 1));
+    static constexpr int value = G == 4 ? (NP <= 3 ? 5 : 1) : (KB <= 20 ? 4 : (KB <= 32 ? 3 : 2));
 };
 
 template <int KB>

@@ -36,12 +36,15 @@ BS_HD int bs_choose_log2L(uint64_t C, int cpt, int log2min, int log2max, int tar
 }
 
 // Lanes that walk one chunk together in the FP32 fused-minor kernel (each
-// owns a contiguous group of the bucket's column pairs): 4 for widths of a
-// multiple of 8 columns from 24 on, else 2, so every lane holds whole column
-// pairs.  A warp task of that kernel covers 32 / G chunks, one of the FP64
-// fused-minor kernel 16 (lane pairs); the permanent kernels give each lane its
-// own chunk (32 per task).
-#define BS_MINORS_FP32_GROUP_KB(KB) (((KB) % 8 == 0 && (KB) >= 24) ? 4 : 2)
+// owns a contiguous group of the bucket's column pairs, so G divides KB / 2):
+// 4 at widths 24 and 48, else 2.  Two lanes do less redundant exchange work
+// per addend (one shuffle round instead of two, each lane's product chains
+// twice as long) and measured faster wherever their registers allow 2-3
+// CTAs per SM: widths 32 and 40 by 6-12 %; at 24 four lanes at 5 CTAs per SM
+// are faster, and at 48 two lanes would spill.  A warp task of that kernel
+// covers 32 / G chunks, one of the FP64 fused-minor kernel 16 (lane pairs);
+// the permanent kernels give each lane its own chunk (32 per task).
+#define BS_MINORS_FP32_GROUP_KB(KB) (((KB) == 24 || (KB) == 48) ? 4 : 2)
 BS_HD int bs_minors_fp32_group(int K) { return BS_MINORS_FP32_GROUP_KB((K + 3) & ~3); }
 BS_HD int bs_chunks_per_task(int kind, int fp32, int K) {
     if (kind != BS_KIND_MINORS) return 32;
