@@ -403,8 +403,9 @@ def run_mine(args):
         fp64_form = {"samples_per_s": args.fp64_samples / (ms / 1000.0), "samples": args.fp64_samples,
                      "fp64_fma_per_s_measured": fp64_rate}
 
-    # the plain FP64 kernels on single k = 30 jobs (spec target: >= 60 %
-    # of the FP64 peak for k >= 30): permanent 30 x 30, minors 29 x 30
+    # the plain FP64 kernels on single k = 30 jobs, as fractions of the FP64
+    # peak (the FP64 form is meant to keep the FP64 pipe >= 60 % busy for
+    # k >= 30): permanent 30 x 30, minors 29 x 30
     fp64_k30 = {}
     ctx.set_profiling(True)
     u60 = S.haar_unitary(60, 77)
