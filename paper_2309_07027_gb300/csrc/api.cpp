@@ -216,15 +216,28 @@ int record_walk_start(bs_ctx* c, cudaEvent_t* e0) {
     *e0 = nullptr;
     if (!c->profiling) return BS_OK;
     BS_CUDA(cudaEventCreate(e0));
-    BS_CUDA(record_timing_event(c, *e0));
+    const cudaError_t e = record_timing_event(c, *e0);
+    if (e != cudaSuccess) {
+        cudaEventDestroy(*e0);
+        *e0 = nullptr;
+        BS_CUDA(e);
+    }
     return BS_OK;
 }
 
+// Takes ownership of e0 (recorded by record_walk_start).
 int record_walk_end(bs_ctx* c, cudaEvent_t e0, bool fp32) {
     if (!c->profiling || !e0) return BS_OK;
     cudaEvent_t e1;
-    BS_CUDA(cudaEventCreate(&e1));
-    BS_CUDA(record_timing_event(c, e1));
+    cudaError_t e = cudaEventCreate(&e1);
+    if (e == cudaSuccess) {
+        e = record_timing_event(c, e1);
+        if (e != cudaSuccess) cudaEventDestroy(e1);
+    }
+    if (e != cudaSuccess) {
+        cudaEventDestroy(e0);
+        BS_CUDA(e);
+    }
     c->timed.push_back({e0, e1, fp32 ? 1 : 0});
     return BS_OK;
 }
@@ -238,7 +251,10 @@ int launch_walk(bs_ctx* c, const bs::WalkArgs& a, bool fp32, int kind) {
         e = kind == BS_KIND_PERM ? bs::launch_walk_fp32_perm(a, c->stream) : bs::launch_walk_fp32_minors(a, c->stream);
     else
         e = kind == BS_KIND_PERM ? bs::launch_walk_fp64_perm(a, c->stream) : bs::launch_walk_fp64_minors(a, c->stream);
-    if (e != cudaSuccess) return fail(BS_ECUDA, "walk launch failed: %s", cudaGetErrorString(e));
+    if (e != cudaSuccess) {
+        if (e0) cudaEventDestroy(e0);
+        return fail(BS_ECUDA, "walk launch failed: %s", cudaGetErrorString(e));
+    }
     c->stats.walk_launches++;
     c->stats.kernel_launches++;
     return record_walk_end(c, e0, fp32);
@@ -763,11 +779,12 @@ int bs_ctx_create(bs_ctx** out, int device, size_t mem_budget_bytes) {
     e = cudaSetDevice(device);
     if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&c->own, cudaStreamNonBlocking);
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&c->stage_ev, cudaEventDisableTiming);
+    c->stream = c->own;
     if (e != cudaSuccess) {
-        delete c;
+        cudaGetLastError();
+        bs_ctx_destroy(c);  // releases whatever was created
         return fail(BS_ECUDA, "context setup: %s", cudaGetErrorString(e));
     }
-    c->stream = c->own;
     // control words (task counters, status, statistics) start at zero
     if (ensure(c, c->ctl, kCtlSlots * 8) != BS_OK || cudaMemset(c->ctl.p, 0, kCtlSlots * 8) != cudaSuccess) {
         cudaGetLastError();
