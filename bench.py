@@ -220,7 +220,7 @@ def run_reference(args):
                      f"full collision-free sample")}
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000 * statistics.mean(times),
-            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64x2 (double-double)",
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "dtype_detail": "double-double (pairs of f64) throughout",
             "data": "synthetic (seeded Haar-random 60-mode unitary)",
             "config": {"workload": "cc_sampling_n30_m60", "n": N_PHOTONS, "m": M_MODES,
                        "samples_per_step": f"bounded chain prefix per host core (oracle, {procs} cores)"},
@@ -435,7 +435,9 @@ def run_mine(args):
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": statistics.mean(step_ms), "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None,
-        "dtype": "f32 products / f64 accumulation" if mode == bs.BS_MIXED else "f64",
+        "dtype": "f32" if mode == bs.BS_MIXED else "f64",
+        "dtype_detail": ("f32 column sums and products, float-float runs folded into double-double partials"
+                         if mode == bs.BS_MIXED else "f64 column sums and products, double-double partials"),
         "data": "synthetic (seeded Haar-random 60-mode unitary)",
         "config": {"workload": "cc_sampling_n30_m60", "n": N_PHOTONS, "m": M_MODES, "samples_per_step": S_,
                    "mode": args.mode, "l2": "flushed between steps (256 MiB write)",
