@@ -420,8 +420,16 @@ def run_mine(args):
                 ctx.laplace_minors(a, M, N, mode=bs.BS_FP64)
             s2 = ctx.stats()
         secs = s2["walk_ms"][0] / 1000.0
-        fp64_k30[kind] = {"addends_per_s": s2["addends"][0] / secs,
-                          "frac_of_fp64_peak": s2["addend_flops"][0] / secs / (2.0 * fp64_rate)}
+        rate = s2["addends"][0] / secs
+        # FP64-pipe operations the walk needs per addend at K = 30 columns:
+        # permanent 2K (update) + 4(K - 1) (product) + 2 (weighted sum);
+        # lane-pair minors about 14K (each lane: update K, suffix and prefix
+        # chains 2K - 4 each, accumulate 2K, exchange and weight about 6)
+        ops = 6 * 30 - 2 if kind == "perm" else 14 * 30
+        fp64_k30[kind] = {"addends_per_s": rate,
+                          "frac_of_fp64_peak": s2["addend_flops"][0] / secs / (2.0 * fp64_rate),
+                          "fp64_pipe_ops_per_addend": ops,
+                          "frac_of_fp64_pipe": rate * ops / fp64_rate}
     ctx.set_profiling(False)
     if rank != 0:
         ctx.close()
