@@ -363,11 +363,18 @@ def run_mine(args):
     # data, metadata and task partials grow with the number of chains.  The
     # kernel is compute-bound; the figure shows that it re-reads nothing.
     traffic = 1.121e6 * S_ / 32 if p == 1 else None
+    # nominal peak from unit counts and clocks: FMA lanes per SM per clock
+    # (128 FP32, 2 FP64 on this part) x SMs x maximum SM clock x 2 flops
+    sms = torch.cuda.get_device_properties(local).multi_processor_count
+    max_mhz = (clk or {}).get("sm_max_mhz") or 2070.0
+    peak_nominal = 2.0 * (128 if p == 1 else 2) * sms * max_mhz * 1e6 / 1e12
     roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
             "frac": achieved / peak if peak else None, "traffic": traffic,
             "traffic_launch": "the k = 30 launch (ncu capture of 32 chains, scaled)" if p == 1 else None,
             "kernel": "walk_fp32_minors_kernel" if p == 1 else "walk_fp64_minors_kernel",
             "peak_source": "measured on this GPU by bs_measure_fma_rates (2 flops per lane-FMA)",
+            "peak_nominal": peak_nominal, "frac_of_nominal": achieved / peak_nominal,
+            "peak_nominal_source": f"{128 if p == 1 else 2} FMA lanes / SM / clock x {sms} SMs x {max_mhz:.0f} MHz x 2",
             "walk_ms_per_step": st["walk_ms"][p] / args.steps, "walk_launches": int(st["timed_launches"][p]),
             "measured_over": f"{args.steps} profiled steps of the same workload and seeds, right after the timed "
                              f"ones ({statistics.mean(prof_step_ms):.1f} ms per profiled step)",

@@ -34,6 +34,7 @@ def test_bench_line_has_the_contract_keys():
     roof = d["roofline"]
     assert roof["bound"] == "alu" and roof["unit"] == "TFLOP/s"
     assert 0 < roof["frac"] < 1.2 and abs(roof["frac"] - roof["achieved"] / roof["peak"]) < 1e-9
+    assert 0 < roof["frac_of_nominal"] < 1.2 and roof["peak_nominal"] > 0
     e2e = d["e2e"]
     assert e2e["value"] > 0 and e2e["h2d_bytes_per_step"] > 0 and e2e["d2h_bytes_per_step"] > 0
     assert d["gpu_launches"] > 0
