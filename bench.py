@@ -54,7 +54,7 @@ def parse():
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
-    ap.add_argument("--workload", default="cc", choices=["cc", "batch", "serving", "lossy", "formulas"],
+    ap.add_argument("--workload", default="cc", choices=["cc", "single", "batch", "serving", "lossy", "formulas"],
                     help="cc: the headline line; the others print their own line for the other configs")
     ap.add_argument("--chains", type=int, default=64)
     ap.add_argument("--lossy-samples", type=int, default=20, help="samples of the lossy workload")
@@ -118,6 +118,11 @@ def full_sample_ops(n):
     return sum(k * (k - 1) * 2.0 ** (k - 2) for k in range(2, n + 1))
 
 
+# bound on any wait for the host-core oracle processes (a worker that cannot
+# start would otherwise leave the pool waiting forever)
+POOL_TIMEOUT_S = 600
+
+
 def host_cores():
     try:
         return len(os.sched_getaffinity(0))
@@ -160,15 +165,17 @@ class OraclePool:
         import multiprocessing as mp
         self.procs = procs
         self.pool = mp.get_context("spawn").Pool(procs)
-        self.pool.map(_oracle_chain_prefix, [(2, 7 + i) for i in range(procs)], chunksize=1)  # imports
+        self.pool.map_async(_oracle_chain_prefix, [(2, 7 + i) for i in range(procs)],
+                            chunksize=1).get(timeout=POOL_TIMEOUT_S)  # imports
 
     def run(self, steps):
         t0 = time.perf_counter()
-        res = self.pool.map(_oracle_chain_prefix, [(steps, 7 + i) for i in range(self.procs)], chunksize=1)
+        res = self.pool.map_async(_oracle_chain_prefix, [(steps, 7 + i) for i in range(self.procs)],
+                                  chunksize=1).get(timeout=POOL_TIMEOUT_S)
         return sum(r[0] for r in res), time.perf_counter() - t0
 
     def close(self):
-        self.pool.close()
+        self.pool.terminate()
         self.pool.join()
 
 
@@ -472,6 +479,82 @@ def run_mine(args):
 
 
 # ---------------------------------------------------------------- other configs
+def oracle_work(M, N):
+    """Inner operations of the oracle's term-by-term walk for one item: its
+    term count (row 0 pinned, the rest of its copies a digit) x formula rows
+    x product columns (each term rebuilds every column sum)."""
+    occ = [int(m) for m in M if m > 0]
+    if not occ:
+        return 1
+    terms = occ[0] if occ[0] > 1 else 1
+    for m in occ[1:]:
+        terms *= m + 1
+    rows = len(occ) + (1 if occ[0] > 1 else 0)
+    cols = sum(1 for x in N if x > 0)
+    return terms * rows * cols
+
+
+def _oracle_item(job):
+    """Pool worker (module level, for spawn): time one item with the oracle
+    in double-double (plain=False) or in plain double (plain=True)."""
+    a, M, N, plain = job
+    import oracle
+    t0 = time.perf_counter()
+    if plain:
+        oracle.perm_mult_fp64(a, M, N)
+    else:
+        oracle.perm_mult(a, M, N)
+    return time.perf_counter() - t0
+
+
+def oracle_batch_timing(items, budget_s):
+    """The oracle on a seeded subset of the batch: items in a seeded order,
+    each predicted (from a calibration on the cheapest items) to take at
+    most budget_s / 8, until about budget_s of one-core work.  The time per
+    inner operation, tau, fitted on the subset, projects the whole batch;
+    the same subset then runs on every host core at once (spawned processes,
+    the subset once per core, items handed out one at a time) and in plain
+    double on one core."""
+    import numpy as np
+    work = np.array([oracle_work(M, N) for _, M, N in items], dtype=np.float64)
+    by_work = np.argsort(work)
+    cheap = by_work[len(items) // 20: len(items) // 20 + 8]   # small but not call-overhead bound
+    t_cal = sum(_oracle_item((*items[i], False)) for i in cheap)
+    tau0 = t_cal / work[cheap].sum()
+    order = np.random.default_rng(2024).permutation(len(items))
+    subset, spent = [], 0.0
+    for i in order:
+        pred = tau0 * work[i]
+        if pred > budget_s / 8:
+            continue
+        subset.append(int(i))
+        spent += pred
+        if spent >= budget_s:
+            break
+    w_sub = work[subset].sum()
+    t1 = sum(_oracle_item((*items[i], False)) for i in subset)
+    tf = sum(_oracle_item((*items[i], True)) for i in subset)
+    procs = host_cores()
+    import multiprocessing as mp
+    with mp.get_context("spawn").Pool(procs) as pool:
+        pool.map_async(_oracle_item, [(*items[i], False) for i in cheap[:procs]],
+                       chunksize=1).get(timeout=POOL_TIMEOUT_S)  # imports
+        t0 = time.perf_counter()
+        jobs = [(*items[i], False) for i in subset for _ in range(procs)]   # a full share per core
+        pool.map_async(_oracle_item, jobs, chunksize=1).get(timeout=POOL_TIMEOUT_S)
+        tall = (time.perf_counter() - t0) / procs
+    total = work.sum()
+    return {"subset_items": len(subset), "subset_work_fraction": float(w_sub / total),
+            "one_core": {"tau_s_per_op": t1 / w_sub, "projected_batch_s": t1 / w_sub * total,
+                         "permanents_per_s": len(items) / (t1 / w_sub * total)},
+            "all_cores": {"cores": procs, "projected_batch_s": tall / w_sub * total,
+                          "permanents_per_s": len(items) / (tall / w_sub * total)},
+            "plain_fp64_one_core": {"projected_batch_s": tf / w_sub * total,
+                                    "permanents_per_s": len(items) / (tf / w_sub * total)},
+            "what": ("oracle: Eq. bbfgrepeated term by term in double-double; plain FP64: the same walk in "
+                     "double; projected over the whole batch by inner operations (terms x rows x columns)")}
+
+
 def run_batch(args):
     """4096 uneven permanents (k ~ U[10, 28], binomially collapsed outputs):
     FP64 and MIXED throughput, MIXED error against FP64 on every item and
@@ -544,7 +627,8 @@ def run_batch(args):
     line = {"workload": "batch_4096_k10_28", "metric": "permanents/s", "fp64": out["fp64"], "mixed": out["mixed"],
             "mixed_vs_fp64_err_over_prod_norms": {"max": float(rel.max()), "p99": float(np.percentile(rel, 99))},
             "err_vs_oracle_over_prod_norms_16_cheapest": orc,
-            "small_batch_64_k10_16_mixed_us_per_call": small_us}
+            "small_batch_64_k10_16_mixed_us_per_call": small_us,
+            "cpu_oracle": None if args.no_cpu_baseline else oracle_batch_timing(items, args.cpu_seconds)}
     print(json.dumps(line), flush=True)
     return 0
 
@@ -636,12 +720,83 @@ def run_formulas(args):
     return 0
 
 
+def addend_count(M):
+    """Addends of Eq. bbfgrepeated with one copy of a smallest-multiplicity
+    row pinned: prod over the other rows of (M + 1), times M_p for the M_p - 1
+    remaining copies of the pinned row."""
+    ms = sorted(int(m) for m in M if m > 0)
+    if not ms:
+        return 1
+    c = ms[0] if ms[0] > 1 else 1
+    for m in ms[1:]:
+        c *= m + 1
+    return c
+
+
+def _time_calls(fn, reps):
+    """Median wall time of reps calls (each returns host results, so the
+    call includes the copies and the synchronisation)."""
+    fn()
+    ts = []
+    for _ in range(reps):
+        t0 = time.perf_counter()
+        fn()
+        ts.append(time.perf_counter() - t0)
+    return statistics.median(ts)
+
+
+def run_single(args):
+    """The 12-photon configuration: A = 8 distinct output rows (multiplicities
+    3,2,2,1,1,1,1,1) x 12 input columns of a Haar 24 x 24 unitary; its
+    permanent and the 12 Laplace minors of the 11 x 12 matrix left after one
+    copy of the last row is removed.  GPU call latency per mode and error
+    against the double-double oracle, beside the oracle's own times (double-
+    double and plain FP64, one host core)."""
+    import numpy as np
+    import oracle
+    import paper_2309_07027_gb300 as bs
+    import synthetic as S
+    a, M, N, _, _ = S.config_single(seed=1)
+    M2 = M.copy()
+    M2[-1] -= 1
+    ref = sum(oracle.perm_mult(a, M, N))
+    mv, mt = oracle.minors(a, M2, N)
+    ref_minors = mv + mt
+    norms = np.sqrt((np.abs(a) ** 2 * M[:, None]).sum(axis=0))
+    scale = float(np.prod(norms ** N))
+    ctx = bs.Context(0)
+    reps = max(args.steps, 1) * 20
+    out = {}
+    for mode, name in ((bs.BS_FP64, "fp64"), (bs.BS_MIXED, "mixed")):
+        p = ctx.perm(a, M, N, mode=mode)
+        mi = ctx.laplace_minors(a, M2, N, mode=mode)
+        out[name] = {"perm_us": 1e6 * _time_calls(lambda: ctx.perm(a, M, N, mode=mode), reps),
+                     "minors_us": 1e6 * _time_calls(lambda: ctx.laplace_minors(a, M2, N, mode=mode), reps),
+                     "perm_err_over_prod_norms": abs(p - ref) / scale,
+                     "minors_max_err_over_prod_norms": float(np.max(np.abs(mi - ref_minors))) / scale}
+    ctx.close()
+    cpu = {"cores": 1,
+           "perm_dd_us": 1e6 * _time_calls(lambda: oracle.perm_mult(a, M, N), 5),
+           "minors_dd_us": 1e6 * _time_calls(lambda: oracle.minors(a, M2, N), 3),
+           "perm_fp64_us": 1e6 * _time_calls(lambda: oracle.perm_mult_fp64(a, M, N), 5),
+           "what": ("oracle: Eq. bbfgrepeated term by term in double-double (perm) and the expanded-matrix "
+                    "Gray walk per minor; plain FP64: the same term-by-term walk in double")}
+    print(json.dumps({"workload": "single_12_photons_rows_3_2_2_1_1_1_1_1", "metric": "us per call",
+                      "addends": addend_count(M),
+                      "gpu": out, "cpu_oracle": cpu,
+                      "calls_timed": reps, "timing": "median wall time per call, host inputs and outputs"}),
+          flush=True)
+    return 0
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         return run_reference(args)
     from paper_2309_07027_gb300 import _build
     _build.build()
+    if args.workload == "single":
+        return run_single(args)
     if args.workload == "batch":
         return run_batch(args)
     if args.workload == "serving":

@@ -7,7 +7,9 @@ double-double); this module marshals numpy arrays through ctypes.
 
 Every function returns complex results as ``(value, tail)`` pairs where
 ``value`` is the double-double rounded to complex128 and ``tail`` is the low
-part (so value + tail carries ~106 bits).
+part (so value + tail carries ~106 bits) -- except ``perm_mult_fp64``, the
+same term-by-term walk in plain double (a timing baseline), which returns
+one complex128.
 """
 from __future__ import annotations
 
@@ -31,7 +33,7 @@ def lib():
         for name in ("orc_bbfg_gray", "orc_bbfg_direct"):
             getattr(L, name).argtypes = [C.c_int, C.c_int, dp, C.c_int, dp]
         for name in ("orc_perm_mult", "orc_perm_expanded", "orc_minors", "orc_bbfg_mult_extremes",
-                     "orc_perm_mult_abs"):
+                     "orc_perm_mult_abs", "orc_perm_mult_fp64"):
             getattr(L, name).argtypes = [C.c_int, C.c_int, dp, C.c_int, ip, ip, dp]
         L.orc_gray_sequence.argtypes = [C.c_int, C.POINTER(C.c_uint64)]
         L.orc_ryser_exact_gauss.argtypes = [C.c_int, C.POINTER(C.c_int64), C.POINTER(C.c_int64)]
@@ -197,6 +199,13 @@ def minors(a, row_mult, col_mult):
     val = out[:, 0] + 1j * out[:, 2]
     tail = out[:, 1] + 1j * out[:, 3]
     return val, tail
+
+
+def perm_mult_fp64(a, row_mult, col_mult):
+    """Eq. (bbfgrepeated) term by term in plain double arithmetic: the
+    plain-FP64 CPU form of the method (a timing baseline)."""
+    out = _mult_call("orc_perm_mult_fp64", a, row_mult, col_mult, 2)
+    return complex(out[0], out[1])
 
 
 def perm_mult_abs(a, row_mult, col_mult):

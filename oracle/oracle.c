@@ -482,6 +482,47 @@ int orc_perm_mult(int R, int K, const double* A, int ld, const int* M, const int
     return 0;
 }
 
+/* The same term-by-term evaluation of Eq. (bbfgrepeated) in plain double
+ * arithmetic (no compensation): the plain-FP64 CPU form of the method, a
+ * timing baseline beside the double-double oracle above.  out = {re, im}. */
+int orc_perm_mult_fp64(int R, int K, const double* A, int ld, const int* M, const int* N, double* out) {
+    mult_problem p;
+    int rc = mult_setup(R, K, M, N, &p);
+    if (rc) return rc;
+    if (p.n == 0) { out[0] = 1.0; out[1] = 0.0; return 0; }
+    int D[64];
+    memset(D, 0, sizeof(D));
+    double acc_re = 0.0, acc_im = 0.0;
+    for (;;) {
+        double w = 1.0;
+        int parity = 0;
+        for (int k = 1; k < p.R; ++k) { w *= binom_exact(p.M[k], D[k]); parity ^= (D[k] & 1); }
+        double pr = 1.0, pi = 0.0;
+        for (int j = 0; j < p.K; ++j) {
+            double sr = 0.0, si = 0.0;
+            for (int k = 0; k < p.R; ++k) {
+                const double c = (double)(p.M[k] - 2 * D[k]);
+                sr += c * A[2 * (p.rows[k] * ld + p.cols[j])];
+                si += c * A[2 * (p.rows[k] * ld + p.cols[j]) + 1];
+            }
+            for (int e = 0; e < p.N[j]; ++e) {
+                const double t = pr * sr - pi * si;
+                pi = pr * si + pi * sr;
+                pr = t;
+            }
+        }
+        if (parity) { acc_re -= w * pr; acc_im -= w * pi; }
+        else { acc_re += w * pr; acc_im += w * pi; }
+        int k = 1;
+        while (k < p.R && D[k] == p.M[k]) { D[k] = 0; ++k; }
+        if (k >= p.R) break;
+        D[k]++;
+    }
+    out[0] = ldexp(acc_re, 1 - p.n);
+    out[1] = ldexp(acc_im, 1 - p.n);
+    return 0;
+}
+
 /* S_abs = 2^(1-n) sum over Delta of prod_k C(M_k, Delta_k) |prod_j c_j^N_j|,
  * the modulus-sum of the addends of Eq. (bbfgrepeated): the scale of the
  * rounding error of any evaluation of the sum (each addend carries a

@@ -283,6 +283,37 @@ def test_multiplicity_formula_exact_gaussian_integers():
         assert Fraction(v.imag) + Fraction(tail.imag) == im
 
 
+def test_plain_fp64_walk_against_exact_and_double_double():
+    """The plain-double twin of the multiplicity walk (the CPU timing
+    baseline): exact on small Gaussian-integer cases (every sum and product
+    is an exact double), within plain FP64 rounding of the double-double
+    oracle on random cases, per(J_n) = n! and the empty permanent."""
+    g = S.rng(13)
+    for trial in range(10):
+        R, K, n = 3, 4, 7
+        a = S.gaussian_integer_matrix(max(R, K), 1200 + trial, bound=2)[:R, :K]
+        M = np.zeros(R, dtype=np.int32)
+        N = np.zeros(K, dtype=np.int32)
+        for _ in range(n):
+            M[g.integers(0, R)] += 1
+            N[g.integers(0, K)] += 1
+        rows = np.repeat(np.arange(R), M)
+        cols = np.repeat(np.arange(K), N)
+        re, im = oracle.ryser_exact_gauss(a[np.ix_(rows, cols)])
+        got = oracle.perm_mult_fp64(a, M, N)
+        assert (Fraction(got.real), Fraction(got.imag)) == (re, im), trial
+    for trial in range(20):
+        a, M, N = _random_mult_case(g, int(g.integers(1, 6)), int(g.integers(1, 6)), int(g.integers(1, 11)),
+                                    1300 + trial)
+        v, t = oracle.perm_mult(a, M, N)
+        got = oracle.perm_mult_fp64(a, M, N)
+        scale = oracle.perm_mult_abs(a, M, N)
+        assert abs(got - (v + t)) <= 1e-13 * scale + 1e-300, (trial, M, N)
+    for n in range(1, 13):
+        assert oracle.perm_mult_fp64(np.ones((1, 1)), [n], [n]) == math.factorial(n)
+    assert oracle.perm_mult_fp64(np.zeros((2, 2)), [0, 0], [0, 0]) == 1
+
+
 def test_mult_no_photons_and_bad_input():
     assert oracle.perm_mult(np.zeros((2, 2)), [0, 0], [0, 0])[0] == 1
     with pytest.raises(oracle.OracleError):
