@@ -322,9 +322,11 @@ int bs_debug_gray_walk(int ndigits, int nbin, const int* radix, uint64_t start, 
                        int* moved, uint64_t* weights);
 
 /* Host-only planner summary for a permanent (kind 0) or minors (kind 1)
- * problem: info[0] = addends C, info[1] = digit rows, info[2] = binary digits,
- * info[3] = product columns, info[4] = 1 if transposed, info[5] = pinned source
- * row.  Returns BS_EINVAL on invalid multiplicities. */
+ * problem (info holds 8 entries): info[0] = addends C, info[1] = digit rows,
+ * info[2] = binary digits, info[3] = product columns, info[4] = 1 if
+ * transposed, info[5] = pinned source row, info[6] = log2 of the chunk length
+ * and info[7] = warp tasks when the job runs alone in FP64 mode.  Returns
+ * BS_EINVAL on invalid multiplicities. */
 int bs_debug_plan(int rows, int cols, const int* row_mult, const int* col_mult, int kind, int64_t* info);
 
 #ifdef __cplusplus

@@ -456,11 +456,12 @@ def debug_gray_walk(radix, nbin, start, steps):
 
 
 def debug_plan(row_mult, col_mult, kind=0):
-    """Planner summary: dict(C, nrows, nbin, K, transposed, pinned)."""
+    """Planner summary: dict(C, nrows, nbin, K, transposed, pinned, log2L,
+    tasks), the last two for the job run alone in FP64 mode."""
     L = load()
     M = _i32(row_mult)
     N = _i32(col_mult)
-    info = np.zeros(6, dtype=np.int64)
+    info = np.zeros(8, dtype=np.int64)
     _check(L.bs_debug_plan(len(M), len(N), _ip(M), _ip(N), int(kind), _i64p(info)))
     return dict(C=int(info[0]), nrows=int(info[1]), nbin=int(info[2]), K=int(info[3]),
-                transposed=bool(info[4]), pinned=int(info[5]))
+                transposed=bool(info[4]), pinned=int(info[5]), log2L=int(info[6]), tasks=int(info[7]))

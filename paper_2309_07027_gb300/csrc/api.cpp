@@ -97,6 +97,8 @@ struct bs_ctx {
     uint64_t buf_gen = 1;
     void* h_stage = nullptr;
     size_t h_stage_n = 0;
+    void* h_back = nullptr;  // pinned read-back buffer of single calls
+    size_t h_back_n = 0;
     cudaEvent_t stage_ev = nullptr;
     double deadline_s = 0.0;
     int log2max[2] = {12, 12};
@@ -291,8 +293,8 @@ int plan_upload(bs_ctx* c, std::vector<JobIn>& ins, bs_mode mode, Prepared& P) {
         r.kind = in.p->kind;
         r.bucket = (in.p->K + 3) >> 2;
         r.cpt = bs_chunks_per_task(r.kind, r.fp32, in.p->K);
-        r.log2L = bs_choose_log2L(in.p->C, r.cpt, BS_LOG2L_MIN_SINGLE, c->log2max[r.fp32],
-                                  r.fp32 ? BS_TARGET_TASKS_SINGLE_FP32 : BS_TARGET_TASKS_SINGLE);
+        r.log2L = bs_choose_log2L_single(in.p->C, r.cpt, c->log2max[r.fp32],
+                                         r.fp32 ? BS_TARGET_TASKS_SINGLE_FP32 : BS_TARGET_TASKS_SINGLE);
         uint64_t per = (uint64_t)r.cpt << r.log2L;
         r.ntasks = (uint32_t)((in.p->C + per - 1) / per);
         r.ncols = r.kind == BS_KIND_PERM ? 1 : in.p->K;
@@ -466,6 +468,35 @@ int check_status(bs_ctx* c) {
     return BS_OK;
 }
 
+// Reads nout results (hi, lo) and the walk status word back through one
+// pinned buffer and one stream synchronisation.
+int read_back_and_check(bs_ctx* c, double2* hi, double2* lo, int nout) {
+    const size_t out_b = (size_t)nout * sizeof(double2);
+    const size_t need = 2 * out_b + sizeof(unsigned long long);
+    if (c->h_back_n < need) {
+        if (c->h_back) cudaFreeHost(c->h_back);
+        c->h_back = nullptr;
+        c->h_back_n = 0;
+        const size_t want = std::max(need, (size_t)4096);
+        BS_CUDA(cudaHostAlloc(&c->h_back, want, cudaHostAllocDefault));
+        c->h_back_n = want;
+    }
+    char* h = static_cast<char*>(c->h_back);
+    BS_CUDA(cudaMemcpyAsync(h, c->out.p, out_b, cudaMemcpyDeviceToHost, c->stream));
+    BS_CUDA(cudaMemcpyAsync(h + out_b, c->out_lo.p, out_b, cudaMemcpyDeviceToHost, c->stream));
+    BS_CUDA(cudaMemcpyAsync(h + 2 * out_b, static_cast<unsigned long long*>(c->ctl.p) + kCtlStatus,
+                            sizeof(unsigned long long), cudaMemcpyDeviceToHost, c->stream));
+    cudaError_t e = cudaStreamSynchronize(c->stream);
+    if (e != cudaSuccess) return fail(BS_ECUDA, "stream synchronize: %s", cudaGetErrorString(e));
+    std::memcpy(hi, h, out_b);
+    std::memcpy(lo, h + out_b, out_b);
+    int st = 0;
+    std::memcpy(&st, h + 2 * out_b, sizeof(int));
+    if (st == BS_STATUS_TIMEOUT) return fail(BS_ETIMEOUT, "a walk kernel passed its deadline");
+    if (st == BS_STATUS_BADJOB) return fail(BS_ECUDA, "a walk kernel received a job of the wrong bucket");
+    return BS_OK;
+}
+
 int sync_and_check(bs_ctx* c) {
     cudaError_t e = cudaStreamSynchronize(c->stream);
     if (e != cudaSuccess) return fail(BS_ECUDA, "stream synchronize: %s", cudaGetErrorString(e));
@@ -515,9 +546,7 @@ int run_single(bs_ctx* c, const bs_c128* A, int rows, int cols, int ld, int kind
     rc = run_jobs(c, ins, static_cast<const double2*>(c->src.p), mode, static_cast<double2*>(c->out.p),
                   static_cast<double2*>(c->out_lo.p));
     if (rc) return rc;
-    BS_CUDA(cudaMemcpyAsync(hi.data(), c->out.p, nout * sizeof(double2), cudaMemcpyDeviceToHost, c->stream));
-    BS_CUDA(cudaMemcpyAsync(lo.data(), c->out_lo.p, nout * sizeof(double2), cudaMemcpyDeviceToHost, c->stream));
-    return sync_and_check(c);
+    return read_back_and_check(c, hi.data(), lo.data(), nout);
 }
 
 int single_job(bs_ctx* c, const bs_c128* A, int rows, int cols, int ld, const int* M, const int* N, int kind,
@@ -812,6 +841,7 @@ void bs_ctx_destroy(bs_ctx* c) {
     if (c->batch_exec) cudaGraphExecDestroy(c->batch_exec);
     for (DevBuf* b : bufs) release(c, *b);
     if (c->h_stage) cudaFreeHost(c->h_stage);
+    if (c->h_back) cudaFreeHost(c->h_back);
     if (c->stage_ev) cudaEventDestroy(c->stage_ev);
     if (c->own) cudaStreamDestroy(c->own);
     delete c;
@@ -1339,6 +1369,13 @@ int bs_debug_plan(int rows, int cols, const int* row_mult, const int* col_mult, 
     info[3] = p.K;
     info[4] = p.trans ? 1 : 0;
     info[5] = p.pinned_src;
+    // chunking of this job planned alone in FP64 mode (default maximum 2^12)
+    const int kd = kind == 1 ? BS_KIND_MINORS : BS_KIND_PERM;
+    const int cpt = bs_chunks_per_task(kd, 0, p.K);
+    const int l = p.trivial ? 0 : bs_choose_log2L_single(p.C, cpt, 12, BS_TARGET_TASKS_SINGLE);
+    const uint64_t per = (uint64_t)cpt << l;
+    info[6] = l;
+    info[7] = p.trivial ? 0 : (int64_t)((p.C + per - 1) / per);
     return BS_OK;
 }
 

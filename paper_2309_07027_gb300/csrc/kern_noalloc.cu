@@ -120,8 +120,8 @@ extern "C" int bs_perm_noalloc(const bs_c128* A, int rows, int cols, int ld, con
     if (ld < cols) return bs::fail(BS_EINVAL, "leading dimension %d < columns %d", ld, cols);
     const int fp32 = (mode == BS_MIXED && bs_mixed_uses_fp32(p.radix, p.nrows, p.K, p.n)) ? 1 : 0;
     const int cpt = bs_chunks_per_task(BS_KIND_PERM, fp32, p.K);
-    const int log2L = bs_choose_log2L(p.C, cpt, BS_LOG2L_MIN_SINGLE, 12,
-                                      fp32 ? BS_TARGET_TASKS_SINGLE_FP32 : BS_TARGET_TASKS_SINGLE);
+    const int log2L = bs_choose_log2L_single(p.C, cpt, 12,
+                                             fp32 ? BS_TARGET_TASKS_SINGLE_FP32 : BS_TARGET_TASKS_SINGLE);
     const uint64_t per = (uint64_t)cpt << log2L;
     const uint64_t ntasks = (p.C + per - 1) / per;
     if (ntasks > kPartSlots)

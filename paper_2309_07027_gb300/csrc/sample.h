@@ -13,7 +13,8 @@
 // same way alone or inside any batch that uses the same rule.  Jobs planned
 // one call at a time use BS_TARGET_TASKS_SINGLE (several tasks per resident
 // warp, so one job fills the GPU without a ragged tail) and chunks of at
-// least 2^6.  The sampler and the server, which always run many jobs
+// least 2^6, shorter only for jobs too small to fill the GPU
+// (bs_choose_log2L_single).  The sampler and the server, which always run many jobs
 // together, use BS_TARGET_TASKS_MANY (longer chunks, fewer tasks) with a
 // floor of 2^3: their small jobs (early steps, heavy-collision chains sent to
 // FP64) are latency-bound, and short chunks spread them over more warps.
@@ -25,14 +26,34 @@
 #define BS_TARGET_TASKS_MANY 64
 #define BS_LOG2L_MIN_SINGLE 6
 #define BS_LOG2L_MIN_MANY 3
-BS_HD int bs_choose_log2L(uint64_t C, int cpt, int log2min, int log2max, int target) {
-    uint64_t per = C / ((uint64_t)cpt * (uint64_t)target);
+// Tasks that fill the GPU once (resident warps of the walk kernels: about
+// 1200-2400 on 152 SMs).
+#define BS_TARGET_TASKS_FILL 2048
+BS_HD int bs_floor_log2(uint64_t x) {  // floor(log2(x)) for x >= 1, 0 for x = 0
     int l = 0;
-    while ((2ull << l) <= per) ++l;  // floor(log2(per)) for per >= 1
-    if (per == 0) l = 0;
+    while ((2ull << l) <= x) ++l;
+    return l;
+}
+BS_HD int bs_choose_log2L(uint64_t C, int cpt, int log2min, int log2max, int target) {
+    const uint64_t per = C / ((uint64_t)cpt * (uint64_t)target);
+    int l = bs_floor_log2(per);
     if (l < log2min) l = log2min;
     if (l > log2max) l = log2max;
     return l;
+}
+// The rule for jobs planned one call at a time: bs_choose_log2L with the
+// single-call target and floor 2^6, except that a job too small to give
+// BS_TARGET_TASKS_FILL tasks at that floor gets shorter chunks (down to the
+// 2^3 floor of the sampler) until it does: such a job is latency-bound, and
+// its walk time is one lane's chunk, not the total work (a 576-addend FP64
+// job in one warp of 9 chunks of 64 runs at one scheduler's FP64 rate).
+BS_HD int bs_choose_log2L_single(uint64_t C, int cpt, int log2max, int target) {
+    const int big = bs_choose_log2L(C, cpt, BS_LOG2L_MIN_SINGLE, log2max, target);
+    if (big > BS_LOG2L_MIN_SINGLE) return big;
+    int fill = bs_floor_log2(C / ((uint64_t)cpt * (uint64_t)BS_TARGET_TASKS_FILL));
+    if (fill > BS_LOG2L_MIN_SINGLE) fill = BS_LOG2L_MIN_SINGLE;
+    if (fill < BS_LOG2L_MIN_MANY) fill = BS_LOG2L_MIN_MANY;
+    return fill > log2max ? log2max : fill;
 }
 
 // Lanes that walk one chunk together in the FP32 fused-minor kernel (each

@@ -116,6 +116,31 @@ def test_planner_addend_counts_and_orientation(bslib):
     assert m["C"] == 2 and m["K"] == 3 and not m["transposed"]
 
 
+def test_single_call_chunking(bslib):
+    """Jobs planned one call at a time: chunks of 2^6 to 2^12 addends aimed
+    at 32768 warp tasks of 32 chunks; a job too small to give 2048 tasks at
+    2^6 gets chunks down to 2^3 until it does (latency-bound jobs spread
+    over more warps); jobs large enough keep 2^6 or longer."""
+    def plan(n):
+        return bslib.debug_plan([1] * n, [1] * n)
+    for n in (3, 8, 11, 14, 17, 20, 23, 26, 29, 32, 36):
+        p = plan(n)
+        C, l, tasks = p["C"], p["log2L"], p["tasks"]
+        assert C == 2 ** (n - 1) and 3 <= l <= 12
+        assert tasks == -(-C // (32 << l))
+        if l == 12:  # the re-seed interval caps the chunk
+            assert tasks >= 32768
+        elif l > 6:  # the large-job rule: about 32768 tasks
+            assert 32768 <= tasks < 2 * 32768
+        elif l == 6:
+            assert tasks >= 2048
+        else:        # shortened only as far as needed to reach 2048 tasks
+            assert l == 3 or 2048 <= tasks < 2 * 2048
+    assert [plan(n)["log2L"] for n in (20, 21, 22, 23, 26, 29, 33)] == [3, 4, 5, 6, 6, 8, 12]
+    c1 = bslib.debug_plan([3, 2, 2, 1, 1, 1, 1, 1], [1] * 12)
+    assert c1["log2L"] == 3 and c1["tasks"] == 3
+
+
 def test_planner_rejects_invalid(bslib):
     for M, N, kind in [([1, 1], [1], 0), ([-1, 2], [1], 0), ([25, 25], [50], 0), ([1], [1], 1)]:
         with pytest.raises(bslib.BsError) as e:

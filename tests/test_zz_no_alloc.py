@@ -46,7 +46,7 @@ def test_noalloc_matches_bs_perm_on_two_calls(ctx, bslib, mode):
     lib = ctypes.CDLL(bslib.library_path())
     u = S.haar_unitary(40, 11)
     big = (u[:22, :22], np.ones(22, np.int32), np.ones(22, np.int32))      # 2^21 addends, many tasks
-    a1, M1, N1, _, _ = S.config_single(seed=1)                              # 576 addends, one task
+    a1, M1, N1, _, _ = S.config_single(seed=1)                              # 576 addends, 3 tasks
     for a, M, N in (big, (a1, M1, N1)):
         ref = ctx.perm(a, M, N, mode=mode)
         got = noalloc_c_abi(lib, a, M, N, mode)
