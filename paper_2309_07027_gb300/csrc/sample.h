@@ -13,7 +13,7 @@
 // same way alone or inside any batch that uses the same rule.  Jobs planned
 // one call at a time use BS_TARGET_TASKS_SINGLE (several tasks per resident
 // warp, so one job fills the GPU without a ragged tail) and chunks of at
-// least 2^6, shorter only for jobs too small to fill the GPU
+// least 2^6, shorter only for jobs too small to give 256 tasks
 // (bs_choose_log2L_single).  The sampler and the server, which always run many jobs
 // together, use BS_TARGET_TASKS_MANY (longer chunks, fewer tasks) with a
 // floor of 2^3: their small jobs (early steps, heavy-collision chains sent to
@@ -26,9 +26,9 @@
 #define BS_TARGET_TASKS_MANY 64
 #define BS_LOG2L_MIN_SINGLE 6
 #define BS_LOG2L_MIN_MANY 3
-// Tasks that fill the GPU once (resident warps of the walk kernels: about
-// 1200-2400 on 152 SMs).
-#define BS_TARGET_TASKS_FILL 2048
+// Warp tasks below which a job planned alone is latency-bound (its walk
+// time is one lane's chunk); see bs_choose_log2L_single.
+#define BS_TARGET_TASKS_FILL 256
 BS_HD int bs_floor_log2(uint64_t x) {  // floor(log2(x)) for x >= 1, 0 for x = 0
     int l = 0;
     while ((2ull << l) <= x) ++l;
@@ -47,6 +47,9 @@ BS_HD int bs_choose_log2L(uint64_t C, int cpt, int log2min, int log2max, int tar
 // 2^3 floor of the sampler) until it does: such a job is latency-bound, and
 // its walk time is one lane's chunk, not the total work (a 576-addend FP64
 // job in one warp of 9 chunks of 64 runs at one scheduler's FP64 rate).
+// 256 tasks keeps the re-seeding of mid-size jobs as it was: with 2048 (one
+// resident wave) jobs of 2^19 to 2^21 addends also got shorter chunks and the
+// 4096-item batch ran 5 % slower, for no gain on small calls.
 BS_HD int bs_choose_log2L_single(uint64_t C, int cpt, int log2max, int target) {
     const int big = bs_choose_log2L(C, cpt, BS_LOG2L_MIN_SINGLE, log2max, target);
     if (big > BS_LOG2L_MIN_SINGLE) return big;

@@ -118,7 +118,7 @@ def test_planner_addend_counts_and_orientation(bslib):
 
 def test_single_call_chunking(bslib):
     """Jobs planned one call at a time: chunks of 2^6 to 2^12 addends aimed
-    at 32768 warp tasks of 32 chunks; a job too small to give 2048 tasks at
+    at 32768 warp tasks of 32 chunks; a job too small to give 256 tasks at
     2^6 gets chunks down to 2^3 until it does (latency-bound jobs spread
     over more warps); jobs large enough keep 2^6 or longer."""
     def plan(n):
@@ -133,10 +133,10 @@ def test_single_call_chunking(bslib):
         elif l > 6:  # the large-job rule: about 32768 tasks
             assert 32768 <= tasks < 2 * 32768
         elif l == 6:
-            assert tasks >= 2048
-        else:        # shortened only as far as needed to reach 2048 tasks
-            assert l == 3 or 2048 <= tasks < 2 * 2048
-    assert [plan(n)["log2L"] for n in (20, 21, 22, 23, 26, 29, 33)] == [3, 4, 5, 6, 6, 8, 12]
+            assert tasks >= 256
+        else:        # shortened only as far as needed to reach 256 tasks
+            assert l == 3 or 256 <= tasks < 2 * 256
+    assert [plan(n)["log2L"] for n in (17, 18, 19, 20, 23, 26, 29, 33)] == [3, 4, 5, 6, 6, 6, 8, 12]
     c1 = bslib.debug_plan([3, 2, 2, 1, 1, 1, 1, 1], [1] * 12)
     assert c1["log2L"] == 3 and c1["tasks"] == 3
 
