@@ -32,3 +32,24 @@ def test_reference_arm_prints_one_line():
 def test_reference_arm_other_ranks_are_silent():
     r = _run(1)
     assert r.returncode == 0 and r.stdout.strip() == ""
+
+
+def test_bench_addend_count_matches_the_planner():
+    """The addend count the benchmark reports (bench.addend_count) is the
+    planner's: one copy of a smallest-multiplicity row pinned, the others
+    digits of radix M + 1."""
+    import numpy as np
+    sys.path.insert(0, ROOT)
+    import bench
+    import paper_2309_07027_gb300 as bs
+    g = np.random.default_rng(77)
+    for _ in range(40):
+        R = int(g.integers(1, 8))
+        M = g.integers(0, 4, size=R).astype(np.int32)
+        if M.sum() == 0:
+            M[0] = 1
+        n = int(M.sum())
+        plan = bs.debug_plan(M, np.ones(n, np.int32))
+        assert not plan["transposed"]
+        assert bench.addend_count(M) == plan["C"], (M, plan)
+    assert bench.addend_count([3, 2, 2, 1, 1, 1, 1, 1]) == 576
