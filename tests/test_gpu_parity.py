@@ -420,6 +420,23 @@ def test_sampler_matches_oracle_sampler_fp64(ctx):
     assert np.all(got.sum(axis=1) == 6)
 
 
+@pytest.mark.parametrize("n,m", [(6, 12), (8, 16)])
+def test_lossy_sampler_matches_oracle_sampler_fp64(ctx, n, m):
+    """Lossy sampling (one loss mode per photon, transmissivity 0.5): the GPU
+    chains and the oracle's draw the same rows, seed for seed, only modes
+    below m counted, except a draw within 1e-9 of a CDF boundary."""
+    v, mdet = S.config_lossy(n=n, m=m, eta=0.5, seed=40 + n)
+    ns = 120
+    occ = np.ones(n, dtype=np.int32)
+    got = ctx.sample_ex(v, occ, ns, seed=4040 + n, m_detected=mdet, mode=0)
+    ref, margin, _ = oracle.cc_sample(v, occ, ns, seed=4040 + n, m_detected=mdet)
+    assert got.shape == ref.shape == (ns, m)
+    mismatch = [s_ for s_ in range(ns) if not np.array_equal(got[s_], ref[s_])]
+    assert all(margin[s_] < 1e-9 for s_ in mismatch), (mismatch, margin[mismatch])
+    assert len(mismatch) <= 1
+    assert np.all(got.sum(axis=1) <= n) and got.sum() < n * ns
+
+
 def test_sampler_graph_replay_equals_eager(ctx):
     """The captured step loop, replayed for new seeds, draws exactly what the
     directly launched kernels draw."""
