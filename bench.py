@@ -405,6 +405,7 @@ def run_mine(args):
             t0 = time.perf_counter()
             ctx.sample(u, occ, S_, seed_base + 100 + i, mode=mode)
             e2e_t += time.perf_counter() - t0
+        e2e_t = max_over_ranks(e2e_t, dist)  # the slowest rank, as for the device-timed value
         e2e = {"value": world * S_ * args.steps / e2e_t, "unit": UNIT, "h2d_bytes_per_step": int(u.nbytes),
                "d2h_bytes_per_step": int(S_ * M_MODES * 4)}
         ctx.set_stream(stream)
