@@ -95,11 +95,15 @@ struct bs_ctx {
     // bumped whenever the job/metadata buffers are rewritten or any buffer
     // is reallocated (a captured graph refers to them)
     uint64_t buf_gen = 1;
-    void* h_stage = nullptr;
-    size_t h_stage_n = 0;
+    // two pinned staging buffers, used in turn: a buffer is reused only after
+    // the copy out of it (stage_ev) has finished, so staging one upload never
+    // waits for the copy just enqueued from the other
+    void* h_stage[2] = {nullptr, nullptr};
+    size_t h_stage_n[2] = {0, 0};
+    int stage_cur = 0;
     void* h_back = nullptr;  // pinned read-back buffer of single calls
     size_t h_back_n = 0;
-    cudaEvent_t stage_ev = nullptr;
+    cudaEvent_t stage_ev[2] = {nullptr, nullptr};
     double deadline_s = 0.0;
     int log2max[2] = {12, 12};
     bool profiling = false;
@@ -145,21 +149,25 @@ void release(bs_ctx* c, DevBuf& b) {
     b.n = 0;
 }
 
-// Pinned staging buffer; waits for the previous upload from it first.
+// The next of the two pinned staging buffers, at least `bytes` long; waits
+// first for the last copy recorded out of it (stage_ev of that buffer).
+// Callers record c->stage_ev[c->stage_cur] after enqueueing their copy.
 void* stage(bs_ctx* c, size_t bytes) {
-    if (c->stage_ev) cudaEventSynchronize(c->stage_ev);
-    if (c->h_stage_n < bytes) {
-        if (c->h_stage) cudaFreeHost(c->h_stage);
-        size_t want = std::max(bytes, c->h_stage_n * 2);
-        if (cudaHostAlloc(&c->h_stage, want, cudaHostAllocDefault) != cudaSuccess) {
+    const int b = c->stage_cur ^ 1;
+    if (c->stage_ev[b]) cudaEventSynchronize(c->stage_ev[b]);
+    c->stage_cur = b;
+    if (c->h_stage_n[b] < bytes) {
+        if (c->h_stage[b]) cudaFreeHost(c->h_stage[b]);
+        size_t want = std::max(bytes, c->h_stage_n[b] * 2);
+        if (cudaHostAlloc(&c->h_stage[b], want, cudaHostAllocDefault) != cudaSuccess) {
             cudaGetLastError();
-            c->h_stage = nullptr;
-            c->h_stage_n = 0;
+            c->h_stage[b] = nullptr;
+            c->h_stage_n[b] = 0;
             return nullptr;
         }
-        c->h_stage_n = want;
+        c->h_stage_n[b] = want;
     }
-    return c->h_stage;
+    return c->h_stage[b];
 }
 
 using bs::IntPlan;
@@ -380,7 +388,7 @@ int plan_upload(bs_ctx* c, std::vector<JobIn>& ins, bs_mode mode, Prepared& P) {
     std::memcpy(h + jobs_b, meta.data(), meta_b);
     BS_CUDA(cudaMemcpyAsync(c->jobs.p, h, jobs_b, cudaMemcpyHostToDevice, c->stream));
     BS_CUDA(cudaMemcpyAsync(c->meta.p, h + jobs_b, meta_b, cudaMemcpyHostToDevice, c->stream));
-    BS_CUDA(cudaEventRecord(c->stage_ev, c->stream));
+    BS_CUDA(cudaEventRecord(c->stage_ev[c->stage_cur], c->stream));
     c->buf_gen++;
     P.njobs = rows.size();
     // FP64 jobs come first (sorted by precision), then FP32 jobs
@@ -541,7 +549,7 @@ int run_single(bs_ctx* c, const bs_c128* A, int rows, int cols, int ld, int kind
     if (!h) return fail(BS_ENOMEM, "pinned host staging allocation failed");
     copy_matrix(h, A, rows, cols, ld);
     BS_CUDA(cudaMemcpyAsync(c->src.p, h, mat_b, cudaMemcpyHostToDevice, c->stream));
-    BS_CUDA(cudaEventRecord(c->stage_ev, c->stream));
+    BS_CUDA(cudaEventRecord(c->stage_ev[c->stage_cur], c->stream));
     std::vector<JobIn> ins = {{&p, 0, cols, 0}};
     rc = run_jobs(c, ins, static_cast<const double2*>(c->src.p), mode, static_cast<double2*>(c->out.p),
                   static_cast<double2*>(c->out_lo.p));
@@ -671,7 +679,7 @@ int sample_dev(bs_ctx* c, const double2* dU, int m_rows, int m_cols, int ld, con
     if (!h) return fail(BS_ENOMEM, "pinned host staging allocation failed");
     std::memcpy(h, inputs.data(), n * sizeof(int));
     BS_CUDA(cudaMemcpyAsync(c->cc_inputs.p, h, n * sizeof(int), cudaMemcpyHostToDevice, c->stream));
-    BS_CUDA(cudaEventRecord(c->stage_ev, c->stream));
+    BS_CUDA(cudaEventRecord(c->stage_ev[c->stage_cur], c->stream));
     // counters, totals and status; the statistics slots are cleared only by
     // bs_ctx_reset_stats
     BS_CUDA(cudaMemsetAsync(c->ctl.p, 0, kCtlStats * 8, c->stream));
@@ -807,7 +815,8 @@ int bs_ctx_create(bs_ctx** out, int device, size_t mem_budget_bytes) {
     c->budget = mem_budget_bytes;
     e = cudaSetDevice(device);
     if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&c->own, cudaStreamNonBlocking);
-    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&c->stage_ev, cudaEventDisableTiming);
+    for (int b = 0; b < 2 && e == cudaSuccess; ++b)
+        e = cudaEventCreateWithFlags(&c->stage_ev[b], cudaEventDisableTiming);
     c->stream = c->own;
     if (e != cudaSuccess) {
         cudaGetLastError();
@@ -840,9 +849,11 @@ void bs_ctx_destroy(bs_ctx* c) {
     drop_graph_timing(c);
     if (c->batch_exec) cudaGraphExecDestroy(c->batch_exec);
     for (DevBuf* b : bufs) release(c, *b);
-    if (c->h_stage) cudaFreeHost(c->h_stage);
+    for (int b = 0; b < 2; ++b)
+        if (c->h_stage[b]) cudaFreeHost(c->h_stage[b]);
     if (c->h_back) cudaFreeHost(c->h_back);
-    if (c->stage_ev) cudaEventDestroy(c->stage_ev);
+    for (int b = 0; b < 2; ++b)
+        if (c->stage_ev[b]) cudaEventDestroy(c->stage_ev[b]);
     if (c->own) cudaStreamDestroy(c->own);
     delete c;
 }
@@ -1082,7 +1093,7 @@ int bs_perm_batch(bs_ctx* c, int count, const bs_c128* A_packed, const int64_t* 
     for (int b = 0; b < count; ++b)
         if (!plans[b].trivial) copy_matrix(h + off[b], A_packed + a_offset[b], rows[b], cols[b], cols[b]);
     BS_CUDA(cudaMemcpyAsync(c->src.p, h, total * sizeof(bs_c128), cudaMemcpyHostToDevice, c->stream));
-    BS_CUDA(cudaEventRecord(c->stage_ev, c->stream));
+    BS_CUDA(cudaEventRecord(c->stage_ev[c->stage_cur], c->stream));
     // the staged sources are contiguous: the key uses their offsets
     const std::vector<int64_t> key =
         batch_key(c, count, off.data(), rows, cols, mult_packed, row_mult_off, col_mult_off, mode);
@@ -1161,14 +1172,17 @@ int bs_sample_ex(bs_ctx* c, const bs_c128* U, int m_rows, int m_cols, int ld, co
     if (!h) return fail(BS_ENOMEM, "pinned host staging allocation failed");
     copy_matrix(h, U, m_rows, m_cols, ld);
     BS_CUDA(cudaMemcpyAsync(c->cc_U.p, h, ub, cudaMemcpyHostToDevice, c->stream));
-    BS_CUDA(cudaEventRecord(c->stage_ev, c->stream));
+    BS_CUDA(cudaEventRecord(c->stage_ev[c->stage_cur], c->stream));
     rc = sample_dev(c, static_cast<const double2*>(c->cc_U.p), m_rows, m_cols, m_cols, input_occupation, n_samples,
                     seed, mdet, mode, static_cast<int*>(c->cc_out.p));
     if (rc) return rc;
-    BS_CUDA(cudaEventSynchronize(c->stage_ev));
-    BS_CUDA(cudaMemcpyAsync(c->h_stage, c->cc_out.p, ob, cudaMemcpyDeviceToHost, c->stream));
+    // read back through a staging buffer (stage() waits until no copy out of
+    // it is pending)
+    void* hb = stage(c, ob);
+    if (!hb) return fail(BS_ENOMEM, "pinned host staging allocation failed");
+    BS_CUDA(cudaMemcpyAsync(hb, c->cc_out.p, ob, cudaMemcpyDeviceToHost, c->stream));
     if ((rc = sync_and_check(c))) return rc;
-    std::memcpy(out, c->h_stage, ob);
+    std::memcpy(out, hb, ob);
     return BS_OK;
 }
 
