@@ -90,6 +90,8 @@ struct bs_ctx {
     std::vector<int64_t> batch_key;
     const void* batch_src = nullptr;
     void* batch_out = nullptr;
+    void* batch_out_lo = nullptr;
+    std::vector<int64_t> single_last_key;  // key of the last single call (capture on a repeat)
     uint64_t batch_gen = 0;
     uint64_t batch_walks = 0, batch_kernels = 0, batch_adds[2] = {0, 0}, batch_flops[2] = {0, 0};
     // bumped whenever the job/metadata buffers are rewritten or any buffer
@@ -525,8 +527,104 @@ void copy_matrix(bs_c128* dst, const bs_c128* A, int rows, int cols, int ld) {
     for (int r = 0; r < rows; ++r) std::memcpy(dst + (size_t)r * cols, A + (size_t)r * ld, sizeof(bs_c128) * cols);
 }
 
+// Walks a validated batch whose sources sit at d_src (+ each item's offset)
+// and writes item b to d_out[b].  The device sequence of the last batch is
+// kept as a captured CUDA graph: a batch with the same key, the same device
+// pointers and untouched context buffers replays it without planning,
+// uploading or launching anew.  Eager when graphs are off, when profiling, on
+// the legacy default stream and while the caller captures the stream.
+int batch_walk(bs_ctx* c, std::vector<IntPlan>& plans, const std::vector<int64_t>& key,
+                      const int64_t* a_offset, const int* cols, const double2* d_src, double2* d_out, bs_mode mode,
+                      double2* d_out_lo, bool capture_on_repeat = false) {
+    int rc;
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    if (c->stream != nullptr) BS_CUDA(cudaStreamIsCapturing(c->stream, &cap));
+    bool graphs = c->use_graphs && !c->profiling && c->stream != nullptr && c->stream != cudaStreamPerThread &&
+                  cap == cudaStreamCaptureStatusNone;
+    if (capture_on_repeat) {
+        // single calls: a capture costs more than one eager run, so a key is
+        // captured only when it repeats the previous single call's
+        const bool repeat = c->single_last_key == key;
+        if (!repeat) c->single_last_key = key;
+        if (!repeat && !(c->batch_exec && c->batch_key == key)) graphs = false;
+    }
+    if (graphs && c->batch_exec && c->batch_gen == c->buf_gen && c->batch_src == d_src && c->batch_out == d_out &&
+        c->batch_out_lo == d_out_lo && c->batch_key == key) {
+        BS_CUDA(cudaGraphLaunch(c->batch_exec, c->stream));
+        c->stats.walk_launches += c->batch_walks;
+        c->stats.kernel_launches += c->batch_kernels;
+        for (int p = 0; p < 2; ++p) {
+            c->stats.addends[p] += c->batch_adds[p];
+            c->stats.addend_flops[p] += c->batch_flops[p];
+        }
+        return BS_OK;
+    }
+    std::vector<JobIn> ins;
+    for (size_t b = 0; b < plans.size(); ++b)
+        if (!plans[b].trivial) ins.push_back({&plans[b], a_offset[b], cols[b], (int)b});
+    Prepared P;
+    if ((rc = plan_upload(c, ins, mode, P))) return rc;
+    if (P.njobs == 0) return BS_OK;
+    if (!graphs) {
+        if ((rc = enqueue_device(c, P, d_src, d_out, d_out_lo))) return rc;
+    } else {
+        const uint64_t w0 = c->stats.walk_launches, k0 = c->stats.kernel_launches;
+        BS_CUDA(cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal));
+        rc = enqueue_device(c, P, d_src, d_out, d_out_lo);
+        cudaGraph_t g = nullptr;
+        cudaError_t e = cudaStreamEndCapture(c->stream, &g);
+        if (rc || e != cudaSuccess) {
+            if (g) cudaGraphDestroy(g);
+            cudaGetLastError();
+            return rc ? rc : fail(BS_ECUDA, "batch graph capture: %s", cudaGetErrorString(e));
+        }
+        cudaGraphExec_t exec = nullptr;
+        e = cudaGraphInstantiate(&exec, g, 0);
+        cudaGraphDestroy(g);
+        if (e != cudaSuccess) return fail(BS_ECUDA, "batch graph instantiate: %s", cudaGetErrorString(e));
+        if (c->batch_exec) cudaGraphExecDestroy(c->batch_exec);
+        c->batch_exec = exec;
+        c->batch_key = key;
+        c->batch_gen = c->buf_gen;
+        c->batch_src = d_src;
+        c->batch_out = d_out;
+        c->batch_out_lo = d_out_lo;
+        c->batch_walks = c->stats.walk_launches - w0;
+        c->batch_kernels = c->stats.kernel_launches - k0;
+        for (int p = 0; p < 2; ++p) {
+            c->batch_adds[p] = P.adds[p];
+            c->batch_flops[p] = P.flops[p];
+        }
+        BS_CUDA(cudaGraphLaunch(c->batch_exec, c->stream));
+    }
+    for (int p = 0; p < 2; ++p) {
+        c->stats.addends[p] += P.adds[p];
+        c->stats.addend_flops[p] += P.flops[p];
+    }
+    return BS_OK;
+}
+
+// Graph-cache key of one job planned alone: everything the device sequence
+// depends on besides the buffers (the plan's digits, sources and product
+// columns, the source shape, mode, chunk caps and deadline).  The leading -1
+// keeps it apart from every batch key (which starts with the item count).
+static std::vector<int64_t> plan_key(const bs_ctx* c, const IntPlan& p, int rows, int cols, bs_mode mode) {
+    int64_t dl = 0;
+    std::memcpy(&dl, &c->deadline_s, sizeof(dl));
+    std::vector<int64_t> k = {-1, (int64_t)p.kind, (int64_t)p.formula, (int64_t)p.n, (int64_t)p.K,
+                              (int64_t)p.nrows, (int64_t)p.nbin, (int64_t)p.C, (int64_t)p.trans,
+                              (int64_t)p.pinned_src, (int64_t)rows, (int64_t)cols, (int64_t)mode,
+                              (int64_t)c->log2max[0], (int64_t)c->log2max[1], dl};
+    for (int j = 0; j < p.nrows; ++j) k.insert(k.end(), {(int64_t)p.radix[j], (int64_t)p.digit_src[j]});
+    for (int j = 0; j < p.K; ++j) k.push_back(p.col_src[j]);
+    return k;
+}
+
 // One planned job on a rows x cols host matrix: upload, walk, reduce, read
-// back (hi, lo: one value per output column).
+// back (hi, lo: one value per output column).  When the plan repeats the
+// previous single call's, the device sequence is captured as a graph and
+// replayed while it keeps repeating (only the matrix upload and the read-back
+// run outside it).
 int run_single(bs_ctx* c, const bs_c128* A, int rows, int cols, int ld, int kind, bs_mode mode, const IntPlan& p,
                std::vector<double2>& hi, std::vector<double2>& lo) {
     int rc;
@@ -550,9 +648,10 @@ int run_single(bs_ctx* c, const bs_c128* A, int rows, int cols, int ld, int kind
     copy_matrix(h, A, rows, cols, ld);
     BS_CUDA(cudaMemcpyAsync(c->src.p, h, mat_b, cudaMemcpyHostToDevice, c->stream));
     BS_CUDA(cudaEventRecord(c->stage_ev[c->stage_cur], c->stream));
-    std::vector<JobIn> ins = {{&p, 0, cols, 0}};
-    rc = run_jobs(c, ins, static_cast<const double2*>(c->src.p), mode, static_cast<double2*>(c->out.p),
-                  static_cast<double2*>(c->out_lo.p));
+    std::vector<IntPlan> plans = {p};
+    const int64_t off0 = 0;
+    rc = batch_walk(c, plans, plan_key(c, p, rows, cols, mode), &off0, &cols, static_cast<const double2*>(c->src.p),
+                    static_cast<double2*>(c->out.p), mode, static_cast<double2*>(c->out_lo.p), true);
     if (rc) return rc;
     return read_back_and_check(c, hi.data(), lo.data(), nout);
 }
@@ -1001,74 +1100,6 @@ static std::vector<int64_t> batch_key(const bs_ctx* c, int count, const int64_t*
     return k;
 }
 
-// Walks a validated batch whose sources sit at d_src (+ each item's offset)
-// and writes item b to d_out[b].  The device sequence of the last batch is
-// kept as a captured CUDA graph: a batch with the same key, the same device
-// pointers and untouched context buffers replays it without planning,
-// uploading or launching anew.  Eager when graphs are off, when profiling, on
-// the legacy default stream and while the caller captures the stream.
-static int batch_walk(bs_ctx* c, std::vector<IntPlan>& plans, const std::vector<int64_t>& key,
-                      const int64_t* a_offset, const int* cols, const double2* d_src, double2* d_out, bs_mode mode) {
-    int rc;
-    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
-    if (c->stream != nullptr) BS_CUDA(cudaStreamIsCapturing(c->stream, &cap));
-    const bool graphs = c->use_graphs && !c->profiling && c->stream != nullptr && c->stream != cudaStreamPerThread &&
-                        cap == cudaStreamCaptureStatusNone;
-    if (graphs && c->batch_exec && c->batch_gen == c->buf_gen && c->batch_src == d_src && c->batch_out == d_out &&
-        c->batch_key == key) {
-        BS_CUDA(cudaGraphLaunch(c->batch_exec, c->stream));
-        c->stats.walk_launches += c->batch_walks;
-        c->stats.kernel_launches += c->batch_kernels;
-        for (int p = 0; p < 2; ++p) {
-            c->stats.addends[p] += c->batch_adds[p];
-            c->stats.addend_flops[p] += c->batch_flops[p];
-        }
-        return BS_OK;
-    }
-    std::vector<JobIn> ins;
-    for (size_t b = 0; b < plans.size(); ++b)
-        if (!plans[b].trivial) ins.push_back({&plans[b], a_offset[b], cols[b], (int)b});
-    Prepared P;
-    if ((rc = plan_upload(c, ins, mode, P))) return rc;
-    if (P.njobs == 0) return BS_OK;
-    if (!graphs) {
-        if ((rc = enqueue_device(c, P, d_src, d_out, nullptr))) return rc;
-    } else {
-        const uint64_t w0 = c->stats.walk_launches, k0 = c->stats.kernel_launches;
-        BS_CUDA(cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal));
-        rc = enqueue_device(c, P, d_src, d_out, nullptr);
-        cudaGraph_t g = nullptr;
-        cudaError_t e = cudaStreamEndCapture(c->stream, &g);
-        if (rc || e != cudaSuccess) {
-            if (g) cudaGraphDestroy(g);
-            cudaGetLastError();
-            return rc ? rc : fail(BS_ECUDA, "batch graph capture: %s", cudaGetErrorString(e));
-        }
-        cudaGraphExec_t exec = nullptr;
-        e = cudaGraphInstantiate(&exec, g, 0);
-        cudaGraphDestroy(g);
-        if (e != cudaSuccess) return fail(BS_ECUDA, "batch graph instantiate: %s", cudaGetErrorString(e));
-        if (c->batch_exec) cudaGraphExecDestroy(c->batch_exec);
-        c->batch_exec = exec;
-        c->batch_key = key;
-        c->batch_gen = c->buf_gen;
-        c->batch_src = d_src;
-        c->batch_out = d_out;
-        c->batch_walks = c->stats.walk_launches - w0;
-        c->batch_kernels = c->stats.kernel_launches - k0;
-        for (int p = 0; p < 2; ++p) {
-            c->batch_adds[p] = P.adds[p];
-            c->batch_flops[p] = P.flops[p];
-        }
-        BS_CUDA(cudaGraphLaunch(c->batch_exec, c->stream));
-    }
-    for (int p = 0; p < 2; ++p) {
-        c->stats.addends[p] += P.adds[p];
-        c->stats.addend_flops[p] += P.flops[p];
-    }
-    return BS_OK;
-}
-
 int bs_perm_batch(bs_ctx* c, int count, const bs_c128* A_packed, const int64_t* a_offset, const int* rows,
                   const int* cols, const int* mult_packed, const int64_t* row_mult_off, const int64_t* col_mult_off,
                   bs_mode mode, bs_c128* out) {
@@ -1098,7 +1129,7 @@ int bs_perm_batch(bs_ctx* c, int count, const bs_c128* A_packed, const int64_t* 
     const std::vector<int64_t> key =
         batch_key(c, count, off.data(), rows, cols, mult_packed, row_mult_off, col_mult_off, mode);
     rc = batch_walk(c, plans, key, off.data(), cols, static_cast<const double2*>(c->src.p),
-                    static_cast<double2*>(c->out.p), mode);
+                    static_cast<double2*>(c->out.p), mode, nullptr);
     if (rc) return rc;
     std::vector<double2> res(count);
     BS_CUDA(cudaMemcpyAsync(res.data(), c->out.p, count * sizeof(double2), cudaMemcpyDeviceToHost, c->stream));
@@ -1132,7 +1163,7 @@ int bs_perm_batch_dev(bs_ctx* c, int count, const bs_c128* A_packed_dev, const i
     const std::vector<int64_t> key =
         batch_key(c, count, a_offset, rows, cols, mult_packed, row_mult_off, col_mult_off, mode);
     rc = batch_walk(c, plans, key, a_offset, cols, reinterpret_cast<const double2*>(A_packed_dev),
-                    reinterpret_cast<double2*>(out_dev), mode);
+                    reinterpret_cast<double2*>(out_dev), mode, nullptr);
     if (rc) return rc;
     if (!trivial.empty()) {
         static const double2 one = {1.0, 0.0};

@@ -377,6 +377,46 @@ def test_batch_graph_replay(ctx, mode):
     assert np.array_equal(host, eager)
 
 
+@pytest.mark.parametrize("mode", [0, 1])
+def test_single_call_graph_replay(ctx, mode):
+    """Repeated single calls of one plan replay a captured graph (from the
+    second call on): permanents with their double-double tails and minors
+    equal the eager launches bit for bit, each call reads its own matrix, and
+    a call of another plan in between runs eagerly and leaves the results
+    unchanged."""
+    u = S.haar_unitary(40, 31)
+    mats = [u[:14, :14], u[14:28, :14], u[20:34, 2:16]]
+    M = np.array([2, 1, 1, 1, 1, 1, 1, 1, 1, 1, 1, 1, 1], np.int32)
+    N = np.ones(14, np.int32)
+    a_rows = [m[:13] for m in mats]
+    M2 = M.copy()
+    M2[0] -= 1
+    stream = None
+
+    def calls():
+        out = []
+        for a in a_rows:
+            out.append(ctx.perm(a, M, N, mode=mode, with_tail=True))
+        for a in a_rows:
+            out.append(tuple(ctx.laplace_minors(a, M2, N, mode=mode)))
+        return out
+
+    try:
+        ctx.set_graphs(False)
+        eager = calls()
+        ctx.set_graphs(True)
+        first = calls()   # eager on first sight, captured on the second call
+        k0 = ctx.stats()["kernel_launches"]
+        second = calls()  # replays
+        assert ctx.stats()["kernel_launches"] > k0
+        assert first == eager and second == eager
+        ctx.perm(np.ones((3, 3)), [1, 1, 1], [1, 1, 1], mode=mode)  # another plan in between
+        assert calls() == eager
+    finally:
+        ctx.set_graphs(True)
+        ctx.set_stream(stream)
+
+
 def test_autotuner_picks_a_valid_chunk_and_results_stay_exact(ctx, bslib):
     saved = (ctx.chunk_log2(0), ctx.chunk_log2(1))
     try:
