@@ -268,8 +268,8 @@ template <int KB>
 __device__ void walk_task_minors_fp32(const bs_job& jb, const void* __restrict__ data_v,
                                       const int* __restrict__ radix, bs_zdd* __restrict__ partials, uint32_t local,
                                       int lane, float4* __restrict__ sm_ff, int stride) {
-    constexpr uint32_t FOLD = 64;
-    constexpr int LOG2_FOLD = 6;
+    constexpr uint32_t FOLD = 128;
+    constexpr int LOG2_FOLD = 7;
     constexpr int G = BS_MINORS_FP32_GROUP_KB(KB);
     constexpr int NP = KB / (2 * G);
     constexpr int CPT = 32 / G;

@@ -183,7 +183,7 @@ def test_minors_with_repeats_and_empty(ctx, mode):
 
 # (row multiplicities, binary digits after pinning one M = 1 row): binary
 # digit counts 1..6 with chunks of 64 addends, so the FP32 minors walk ends
-# its branch-free blocks every 2^nbin steps (nbin < 6) or at every fold
+# its branch-free blocks every 2^nbin steps (nbin < 7) or at every fold
 # point, takes the mixed-radix step at each block end, and (C not a multiple
 # of 64) lets a lane run past the end of a short last chunk inside a block.
 # Each case stays in FP32 under the MIXED rule (predicted error at least
