@@ -367,10 +367,10 @@ def run_mine(args):
     achieved = fl / walk_s / 1e12 if walk_s > 0 else 0.0
     # DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) of the
     # k = 30 FP32 fused-minor launch, from an ncu capture of 32 chains of
-    # this workload (1.03 MB + 0.09 MB), scaled to the step's chains: job
+    # this workload (1.11 MB + 0.09 MB), scaled to the step's chains: job
     # data, metadata and task partials grow with the number of chains.  The
     # kernel is compute-bound; the figure shows that it re-reads nothing.
-    traffic = 1.121e6 * S_ / 32 if p == 1 else None
+    traffic = 1.197e6 * S_ / 32 if p == 1 else None
     # nominal peak from unit counts and clocks: FMA lanes per SM per clock
     # (128 FP32, 2 FP64 on this part) x SMs x maximum SM clock x 2 flops
     sms = torch.cuda.get_device_properties(local).multi_processor_count
