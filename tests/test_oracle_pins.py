@@ -461,6 +461,28 @@ def test_cc_sampler_chi_square_tiny():
     assert pval > 1e-3, (chi2, pval)
 
 
+def test_cc_sampler_lossy_closed_forms():
+    """Uniform loss (one loss mode per input photon, transmissivity eta):
+    the detected photon number is Binomial(n, eta) exactly, and the mean
+    occupation of detected mode i is eta * sum_j |U_ij|^2 over the occupied
+    inputs j -- both checked on the oracle's lossy chains."""
+    scipy_stats = pytest.importorskip("scipy.stats")
+    n, m, eta, ns = 4, 6, 0.5, 3000
+    v, mdet = S.config_lossy(n=n, m=m, eta=eta, seed=61)
+    counts, _, _ = oracle.cc_sample(v, np.ones(n, np.int32), ns, seed=62, m_detected=mdet)
+    assert counts.shape == (ns, m)
+    det = counts.sum(axis=1)
+    o = np.bincount(det, minlength=n + 1)[: n + 1]
+    e = ns * scipy_stats.binom.pmf(np.arange(n + 1), n, eta)
+    chi2 = float(np.sum((o - e) ** 2 / e))
+    assert scipy_stats.chi2.sf(chi2, n) > 1e-3, (o, e)
+    u = S.haar_unitary(m, 61)
+    ref = eta * (np.abs(u[:, :n]) ** 2).sum(axis=1)
+    mean = counts.mean(axis=0)
+    sd = counts.std(axis=0) / np.sqrt(ns)
+    assert np.all(np.abs(mean - ref) < 5 * sd + 1e-3), (mean, ref)
+
+
 def test_cc_sampler_marginals_n6_m12():
     n, m = 6, 12
     u = S.haar_unitary(m, 26)
