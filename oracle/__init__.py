@@ -40,7 +40,7 @@ def lib():
         L.orc_philox4x32_10.argtypes = [C.POINTER(C.c_uint32), C.POINTER(C.c_uint32), C.POINTER(C.c_uint32)]
         L.orc_philox4x32_10.restype = None
         L.orc_cc_sample.argtypes = [C.c_int, C.c_int, dp, C.c_int, ip, C.c_int, C.c_uint64, C.c_int,
-                                    C.c_int, ip, dp, dp]
+                                    C.c_int, ip, dp, dp, ip, dp]
         _lib = L
     return _lib
 
@@ -227,22 +227,32 @@ def philox4x32_10(ctr, key):
     return [int(o[i]) for i in range(4)]
 
 
-def cc_sample(u, occupation, n_samples, seed, m_detected=0, max_steps=0):
+def cc_sample(u, occupation, n_samples, seed, m_detected=0, max_steps=0, trace=False):
     """Clifford & Clifford sampler.  ``u`` is m x m' (rows = output modes),
     ``occupation`` has length m'.  Returns (counts[n_samples, m_det],
     margin[n_samples], addend_ops) where margin is the smallest relative
-    distance of a draw to a CDF boundary in each sample."""
+    distance of a draw to a CDF boundary in each sample.  With trace=True
+    two more arrays follow: rows[n_samples, steps], the drawn row of every
+    step in draw order, and step_margin[n_samples, steps], the margin of
+    each draw alone (steps = max_steps, or n when max_steps <= 0)."""
     u = _mat(u)
     m, mc = u.shape
     occ = np.ascontiguousarray(np.asarray(occupation, dtype=np.int32))
     assert occ.shape == (mc,)
     mdet = m if m_detected <= 0 else int(m_detected)
+    n = int(occ.sum())
+    steps = n if max_steps <= 0 or max_steps > n else int(max_steps)
     out = np.zeros((n_samples, mdet), dtype=np.int32)
     margin = np.zeros(max(n_samples, 1))
     ops = np.zeros(1)
+    rows = np.zeros((max(n_samples, 1), max(steps, 1)), dtype=np.int32)
+    smargin = np.zeros((max(n_samples, 1), max(steps, 1)))
     _chk(lib().orc_cc_sample(m, mc, _dp(u.view(np.float64)), mc, _ip(occ), int(n_samples),
                              C.c_uint64(int(seed) & ((1 << 64) - 1)), int(mdet), int(max_steps),
-                             _ip(out), _dp(margin), _dp(ops)), "cc_sample")
+                             _ip(out), _dp(margin), _dp(ops),
+                             _ip(rows) if trace else None, _dp(smargin) if trace else None), "cc_sample")
+    if trace:
+        return out, margin[:n_samples], float(ops[0]), rows[:n_samples, :steps], smargin[:n_samples, :steps]
     return out, margin[:n_samples], float(ops[0])
 
 

@@ -698,10 +698,13 @@ static void draw(uint64_t seed, uint64_t sample, uint32_t purpose, uint32_t inde
 /* the output (all m when m_det <= 0).                                    */
 /* out: n_samples x m_det occupation counts; margin (nullable): per       */
 /* sample, the smallest |u*total - cdf boundary| / total over its steps.  */
+/* rows_out (nullable): n_samples x max_steps drawn rows r_1, r_2, ...,   */
+/* in draw order; step_margin (nullable, same shape): that smallest       */
+/* distance for each step alone.                                        */
 /* ------------------------------------------------------------------ */
 int orc_cc_sample(int m, int mcols, const double* U, int ld, const int* occ, int n_samples,
                   uint64_t seed, int m_det, int max_steps, int* out, double* margin,
-                  double* addend_ops) {
+                  double* addend_ops, int* rows_out, double* step_margin) {
     if (m <= 0 || mcols <= 0 || n_samples < 0) return -1;
     if (m_det <= 0 || m_det > m) m_det = m;
     int n = 0;
@@ -760,16 +763,20 @@ int orc_cc_sample(int m, int mcols, const double* U, int ld, const int* occ, int
             double u = (double)((((uint64_t)wd[0] << 32) | wd[1]) >> 11) * 0x1.0p-53;
             double target = u * total;
             double cdf = 0.0;
+            double step_min = INFINITY;
             int pick = -1;
             for (int i = 0; i < m; ++i) {
                 cdf += w[i];
                 double d = fabs(cdf - target) / total;
-                if (d < min_margin) min_margin = d;
+                if (d < step_min) step_min = d;
                 if (pick < 0 && cdf > target) pick = i;
             }
+            if (step_min < min_margin) min_margin = step_min;
+            if (step_margin) step_margin[(size_t)s * max_steps + (k - 1)] = step_min;
             if (pick < 0) { for (int i = m - 1; i >= 0; --i) if (w[i] > 0) { pick = i; break; } }
             if (pick < 0) pick = 0;
             rows[k - 1] = pick;
+            if (rows_out) rows_out[(size_t)s * max_steps + (k - 1)] = pick;
         }
         int* o = out + (size_t)s * m_det;
         for (int i = 0; i < m_det; ++i) o[i] = 0;

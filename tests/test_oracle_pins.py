@@ -502,3 +502,27 @@ def test_cc_sampler_deterministic_in_seed():
     c, _, _ = oracle.cc_sample(u, occ, 20, seed=100)
     assert np.array_equal(a, b)
     assert not np.array_equal(a, c)
+
+
+def test_cc_sampler_trace_is_consistent_and_first_draw_law():
+    """The drawn-row trace: its histogram is the returned occupation, a
+    max_steps run is a prefix of the full run, the smallest step margin is the
+    sample's margin, and the first draw follows the closed form of C&C's first
+    step: after the uniform column permutation, P(r_1 = i) = (1/n) sum_j s_j
+    |U_ij|^2 (the first weight is |U_i,col_1|^2)."""
+    scipy_stats = pytest.importorskip("scipy.stats")
+    u, occ = S.config_cc(n=5, m=10, seed=3)
+    counts, margin, _, rows, sm = oracle.cc_sample(u, occ, 30, seed=5, trace=True)
+    assert rows.shape == (30, 5) and sm.shape == (30, 5)
+    for s in range(30):
+        assert np.array_equal(np.bincount(rows[s], minlength=10), counts[s])
+        assert sm[s].min() == margin[s]
+    _, _, _, rows3, _ = oracle.cc_sample(u, occ, 30, seed=5, max_steps=3, trace=True)
+    assert np.array_equal(rows3, rows[:, :3])
+    ns = 20000
+    _, _, _, first, _ = oracle.cc_sample(u, occ, ns, seed=6, max_steps=1, trace=True)
+    p = (np.abs(u) ** 2) @ occ / occ.sum()
+    o = np.bincount(first[:, 0], minlength=10)
+    e = ns * p
+    chi2 = float(np.sum((o - e) ** 2 / e))
+    assert scipy_stats.chi2.sf(chi2, 9) > 1e-3, (o, e)
