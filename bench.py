@@ -6,19 +6,24 @@ library's C ABI.
 One step = one batch of ``--samples`` (default 200) samples drawn with every
 hot-path stage on the GPU: per-chain planning, Gray decode / re-seed, the
 incremental column-sum walk, the per-addend products, the fused Laplace
-minors, compensated accumulation and the weighted draw.
+minors, compensated accumulation and the weighted draw.  The headline runs
+the FP64 form (``--mode fp64``: column sums, products and weights in double
+precision, double-double partial sums); the MIXED form is reported beside it.
 
   value     samples/s with U resident on the device (bs_sample_dev), CUDA
             events around every step, L2 flushed (256 MiB write) between steps
   e2e       samples/s through bs_sample with host U / host counts (copies
-            inside the timed region), same seeds as the timed steps, after
-            the same number of warm-up calls through that API
-  roofline  the fused-minors walk kernel: algorithmic flops (per-addend count
-            22K - 22, K columns) / summed kernel time (CUDA events on the
-            launching stream) vs 2 x the FP32 FMA rate measured on this GPU
-  cpu_baseline  the oracle (double-double C, one process per host core) on
-            a bounded prefix of one chain per core, scaled to samples/s by its
-            own operation count; the one-core figure beside it
+            inside the timed region), on the first timed steps' seeds, after
+            one warm-up call through that API
+  roofline  the fused-minors walk kernel of the run's precision: algorithmic
+            flops (per-addend count 22K - 22, K columns) / summed kernel time
+            (CUDA events on the launching stream, over --profile-steps steps
+            of the same seeds) vs 2 x the FMA rate of that pipe measured on
+            this GPU
+  cpu_baseline  the oracle (double-double C, minors computed separately, one
+            process per host core) on a bounded prefix of one chain per core,
+            scaled to samples/s by its own operation count; the one-core
+            figure beside it
 
 ``--impl reference`` runs the oracle as the reference arm (CPU only).
 Multi-GPU: samples are independent, so ranks draw disjoint sample sets
@@ -50,8 +55,11 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="mine", choices=["mine", "reference"])
     ap.add_argument("--samples", type=int, default=200)
-    ap.add_argument("--mode", default="mixed", choices=["mixed", "fp64"])
-    ap.add_argument("--fp64-samples", type=int, default=20, help="samples of the plain FP64 form (0: skip)")
+    ap.add_argument("--mode", default="fp64", choices=["mixed", "fp64"])
+    ap.add_argument("--side-steps", type=int, default=3,
+                    help="steps of the other precision's side measurement (0: skip)")
+    ap.add_argument("--profile-steps", type=int, default=2, help="steps of the per-walk profiled pass")
+    ap.add_argument("--e2e-steps", type=int, default=3, help="steps of the end-to-end pass")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
@@ -195,8 +203,11 @@ def oracle_baseline(budget_s):
         pool.close()
     return {"value": ops / wall / full, "unit": UNIT, "cores": procs, "kind": "oracle",
             "one_core": one,
+            "what": ("the double-double oracle, each of a step's k minors computed separately as its own "
+                     "(k-1) x (k-1) Gray BB/FG permanent (k times the work of the fused walk), not a tuned CPU "
+                     "code"),
             "sample": (f"steps 1..{steps} of one n=30 m=60 chain per core, {procs} cores in parallel (double-double "
-                       f"C oracle, minors by direct Gray BB/FG permanents): {ops:.3g} addend-column ops in "
+                       f"C oracle, minors computed separately): {ops:.3g} addend-column ops in "
                        f"{wall:.2f} s; scaled by the {full:.3g} ops of a full collision-free sample")}
 
 
@@ -274,6 +285,11 @@ def aggregate_rate(world, units_per_rank, seconds):
 
 
 # ---------------------------------------------------------------- GPU arm
+# DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) of one k = 30
+# fused-minor launch of this workload under ncu, and the chains it ran; by
+# precision [FP64, FP32].  None where the kernel changed since the capture.
+TRAFFIC_K30 = [{"bytes": 0.52e6, "chains": 8}, {"bytes": 1.197e6, "chains": 32}]
+
 def run_mine(args):
     import numpy as np
     import torch
@@ -294,7 +310,8 @@ def run_mine(args):
         if dist is not None:
             dist.barrier()
 
-    mode = bs.BS_MIXED if args.mode == "mixed" else bs.BS_FP64
+    modes = {"fp64": bs.BS_FP64, "mixed": bs.BS_MIXED}
+    mode = modes[args.mode]
     u, occ = S.config_cc(N_PHOTONS, M_MODES, SEED)
     ctx = bs.Context(local)
     # a dedicated stream: on the legacy default stream the sampler cannot
@@ -312,18 +329,19 @@ def run_mine(args):
     for w in range(args.warmup):
         ctx.sample_dev(u_dev, occ, S_, seed_base + w, out_dev, mode=mode)
         ctx.sync()
-    def timed_steps(profile):
-        """args.steps sampler steps (seeds fixed per step), each between CUDA
+
+    def timed_steps(steps, profile, md, out):
+        """`steps` sampler steps (seeds fixed per step), each between CUDA
         events on the stream, the L2 flushed before each; returns the step
         times (ms)."""
         ctx.set_profiling(profile)
         evs = []
-        for i in range(args.steps):
+        for i in range(steps):
             flush.zero_()
             e0 = torch.cuda.Event(enable_timing=True)
             e1 = torch.cuda.Event(enable_timing=True)
             e0.record(stream)
-            ctx.sample_dev(u_dev, occ, S_, seed_base + 100 + i, out_dev, mode=mode)
+            ctx.sample_dev(u_dev, occ, S_, seed_base + 100 + i, out, mode=md)
             e1.record(stream)
             evs.append((e0, e1))
             if profile:
@@ -340,91 +358,101 @@ def run_mine(args):
     barrier()
     torch.cuda.synchronize()
     wall0 = time.perf_counter()
-    step_ms = timed_steps(False)
+    step_ms = timed_steps(args.steps, False, mode, out_dev)
     barrier()
     wall = time.perf_counter() - wall0
     clk = stop_clocks(clocks)
     ctx.sync()
     launches = int(ctx.stats()["kernel_launches"])
-    counts = out_dev.cpu().numpy()
+    counts = out_dev.cpu().numpy()  # the last timed step (seed seed_base + 100 + steps - 1)
     assert np.all(counts.sum(axis=1) == N_PHOTONS), "sampler returned a wrong photon count"
     t_max = max_over_ranks(sum(step_ms) / 1000.0, dist)
     value = aggregate_rate(world, S_ * args.steps, t_max)
-    # the same steps again with CUDA events around every walk launch (on the
+    # the first steps again with CUDA events around every walk launch (on the
     # launching stream, inside the replayed graph): kernel times for the
     # roofline; the events add about 3 % to a step
     ctx.reset_stats()
-    prof_step_ms = timed_steps(True)
+    psteps = max(1, min(args.profile_steps, args.steps))
+    prof_step_ms = timed_steps(psteps, True, mode, out_dev)
     st = ctx.stats()
 
-    # roofline of the dominant walk kernel (fused minors in the run's
-    # precision; MIXED sends heavy-collision chains to the FP64 kernel, whose
+    # roofline of the dominant walk kernel: the fused minors of the run's
+    # precision (MIXED sends heavy-collision chains to the FP64 kernel, whose
     # time and work are reported beside)
     p = 1 if mode == bs.BS_MIXED else 0
     walk_s = st["walk_ms"][p] / 1000.0
     fl = st["addend_flops"][p]
     peak = 2.0 * (fp32_rate if p == 1 else fp64_rate) / 1e12
     achieved = fl / walk_s / 1e12 if walk_s > 0 else 0.0
-    # DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) of the
-    # k = 30 FP32 fused-minor launch, from an ncu capture of 32 chains of
-    # this workload (1.11 MB + 0.09 MB), scaled to the step's chains: job
-    # data, metadata and task partials grow with the number of chains.  The
-    # kernel is compute-bound; the figure shows that it re-reads nothing.
-    traffic = 1.197e6 * S_ / 32 if p == 1 else None
+    # DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) of the k = 30
+    # fused-minor launch, from an ncu capture of a few chains of this
+    # workload, scaled to the step's chains (job data, metadata and task
+    # partials grow with the number of chains).  The kernels are
+    # compute-bound; the figure shows that they re-read nothing.
+    traffic = TRAFFIC_K30[p]["bytes"] * S_ / TRAFFIC_K30[p]["chains"] if TRAFFIC_K30[p] else None
     # nominal peak from unit counts and clocks: FMA lanes per SM per clock
     # (128 FP32, 2 FP64 on this part) x SMs x maximum SM clock x 2 flops
     sms = torch.cuda.get_device_properties(local).multi_processor_count
     max_mhz = (clk or {}).get("sm_max_mhz") or 2070.0
-    peak_nominal = 2.0 * (128 if p == 1 else 2) * sms * max_mhz * 1e6 / 1e12
+    lanes = 128 if p == 1 else 2
+    peak_nominal = 2.0 * lanes * sms * max_mhz * 1e6 / 1e12
     roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
             "frac": achieved / peak if peak else None, "traffic": traffic,
-            "traffic_launch": "the k = 30 launch (ncu capture of 32 chains, scaled)" if p == 1 else None,
+            "traffic_launch": (f"the k = 30 launch (ncu capture of {TRAFFIC_K30[p]['chains']} chains, scaled)"
+                               if TRAFFIC_K30[p] else None),
             "kernel": "walk_fp32_minors_kernel" if p == 1 else "walk_fp64_minors_kernel",
-            "peak_source": "measured on this GPU by bs_measure_fma_rates (2 flops per lane-FMA)",
+            "peak_source": ("measured on this GPU by bs_measure_fma_rates (2 flops per lane-FMA), "
+                            + ("FP32 FMA pipe" if p == 1 else "FP64 pipe")),
             "peak_nominal": peak_nominal, "frac_of_nominal": achieved / peak_nominal,
-            "peak_nominal_source": f"{128 if p == 1 else 2} FMA lanes / SM / clock x {sms} SMs x {max_mhz:.0f} MHz x 2",
-            "walk_ms_per_step": st["walk_ms"][p] / args.steps, "walk_launches": int(st["timed_launches"][p]),
-            "measured_over": f"{args.steps} profiled steps of the same workload and seeds, right after the timed "
-                             f"ones ({statistics.mean(prof_step_ms):.1f} ms per profiled step)",
+            "peak_nominal_source": f"{lanes} FMA lanes / SM / clock x {sms} SMs x {max_mhz:.0f} MHz x 2",
+            "walk_ms_per_step": st["walk_ms"][p] / psteps, "walk_launches": int(st["timed_launches"][p]),
+            "walk_share_of_step": st["walk_ms"][p] / sum(prof_step_ms) if sum(prof_step_ms) else None,
+            "measured_over": f"{psteps} profiled steps on the first timed steps' seeds, right after the timed "
+                             f"pass ({statistics.mean(prof_step_ms):.1f} ms per profiled step)",
             "addends_per_s": st["addends"][p] / walk_s if walk_s > 0 else 0.0,
-            "other_precision": {"walk_ms_per_step": st["walk_ms"][1 - p] / args.steps,
+            "other_precision": {"walk_ms_per_step": st["walk_ms"][1 - p] / psteps,
                                 "addends": st["addends"][1 - p]}}
 
     # end to end through the host API (U from host memory, counts back), on
-    # the same seeds, hence the same samples and work, as the timed steps;
-    # the L2 flush before each step stays outside the timed interval
+    # the first timed steps' seeds, hence the same samples and work; the L2
+    # flush before each step stays outside the timed interval
     e2e = None
     if not args.no_e2e:
         ctx.set_stream(None)
-        for w in range(args.warmup):  # the host path captures its own graph on first use
-            ctx.sample(u, occ, S_, seed_base + 90 + w, mode=mode)
+        ctx.sample(u, occ, S_, seed_base + 90, mode=mode)  # the host path captures its own graph on first use
+        esteps = max(1, min(args.e2e_steps, args.steps))
         e2e_t = 0.0
-        for i in range(args.steps):
+        for i in range(esteps):
             flush.zero_()
             torch.cuda.synchronize()
             t0 = time.perf_counter()
             ctx.sample(u, occ, S_, seed_base + 100 + i, mode=mode)
             e2e_t += time.perf_counter() - t0
         e2e_t = max_over_ranks(e2e_t, dist)  # the slowest rank, as for the device-timed value
-        e2e = {"value": world * S_ * args.steps / e2e_t, "unit": UNIT, "h2d_bytes_per_step": int(u.nbytes),
-               "d2h_bytes_per_step": int(S_ * M_MODES * 4)}
+        e2e = {"value": world * S_ * esteps / e2e_t, "unit": UNIT, "h2d_bytes_per_step": int(u.nbytes),
+               "d2h_bytes_per_step": int(S_ * M_MODES * 4), "steps": esteps}
         ctx.set_stream(stream)
 
-    # the plain FP64 form on a smaller sample set, same API
-    fp64_form = None
-    if args.fp64_samples > 0 and mode == bs.BS_MIXED:
-        out64 = torch.zeros((args.fp64_samples, M_MODES), dtype=torch.int32, device="cuda")
-        ctx.sample_dev(u_dev, occ, 2, seed_base + 299, out64, mode=bs.BS_FP64)
+    # the other precision on the same workload: samples/s over a few steps
+    # and, on the last timed step's seed, how many of its samples equal the
+    # headline run's
+    side = None
+    if args.side_steps > 0:
+        other = bs.BS_MIXED if mode == bs.BS_FP64 else bs.BS_FP64
+        out2 = torch.zeros((S_, M_MODES), dtype=torch.int32, device="cuda")
+        ctx.sample_dev(u_dev, occ, S_, seed_base + 98, out2, mode=other)  # warm-up / capture
         ctx.sync()
-        e0 = torch.cuda.Event(enable_timing=True)
-        e1 = torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
-        ctx.sample_dev(u_dev, occ, args.fp64_samples, seed_base + 300, out64, mode=bs.BS_FP64)
-        e1.record(stream)
+        sms_ = timed_steps(min(args.side_steps, args.steps), False, other, out2)
+        ctx.sample_dev(u_dev, occ, S_, seed_base + 100 + args.steps - 1, out2, mode=other)
         ctx.sync()
-        ms = e0.elapsed_time(e1)
-        fp64_form = {"samples_per_s": args.fp64_samples / (ms / 1000.0), "samples": args.fp64_samples,
-                     "fp64_fma_per_s_measured": fp64_rate}
+        same = float(np.mean(np.all(out2.cpu().numpy() == counts, axis=1)))
+        side = {"mode": "mixed" if other == bs.BS_MIXED else "fp64",
+                "samples_per_s": S_ * len(sms_) / (sum(sms_) / 1000.0), "steps": len(sms_),
+                "dtype": "f32" if other == bs.BS_MIXED else "f64",
+                "samples_equal_to_headline_run": same,
+                "what": ("same workload and seeds; MIXED runs FP32 column sums and products where its precision rule "
+                         "predicts an error below 1e-6 prod ||a_j|| (oracle-checked at widths 13-48 in "
+                         "tests/test_gpu_widths.py), FP64 otherwise")}
 
     # the plain FP64 kernels on single k = 30 jobs, as fractions of the FP64
     # peak (the FP64 form is meant to keep the FP64 pipe >= 60 % busy for
@@ -467,17 +495,20 @@ def run_mine(args):
         "warmup": args.warmup, "ms_per_step": statistics.mean(step_ms), "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None,
         "dtype": "f32" if mode == bs.BS_MIXED else "f64",
-        "dtype_detail": ("f32 column sums and products, float-float runs folded into double-double partials"
-                         if mode == bs.BS_MIXED else "f64 column sums and products, double-double partials"),
+        "dtype_detail": ("f32 column sums and products where the MIXED rule allows (else f64), float-float runs "
+                         "folded into double-double partials" if mode == bs.BS_MIXED else
+                         "f64 column sums, products and weights; per-lane double runs folded into double-double, "
+                         "double-double task partials (Sum2 reduce)"),
         "data": "synthetic (seeded Haar-random 60-mode unitary)",
         "config": {"workload": "cc_sampling_n30_m60", "n": N_PHOTONS, "m": M_MODES, "samples_per_step": S_,
                    "mode": args.mode, "l2": "flushed between steps (256 MiB write)",
                    "parallelism": f"replicas x{world} (independent samples)"},
-        "latency_ms": {"p50": statistics.median(step_ms), "p99": sorted(step_ms)[max(0, int(0.99 * len(step_ms)) - 1)],
-                       "what": "per batch of samples (all chains of a batch finish together)"},
+        "latency_ms": {"p50": statistics.median(step_ms), "max": max(step_ms), "steps": len(step_ms),
+                       "what": ("per batch of samples (all chains of a batch finish together), over the timed "
+                                "steps; per-request p50 / p99 come from the serving workload")},
         "paper_model": paper_model(value / world),
         "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
-        "clocks": clk, "fp64_form": fp64_form, "fp64_kernels_k30": fp64_k30, "wall_s": wall,
+        "clocks": clk, "other_precision_form": side, "fp64_kernels_k30": fp64_k30, "wall_s": wall,
         "fma_rates_measured": {"fp64_per_s": fp64_rate, "fp32_per_s": fp32_rate},
     }
     print(json.dumps(line), flush=True)

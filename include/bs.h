@@ -96,6 +96,14 @@ int bs_ctx_set_deadline(bs_ctx* ctx, double seconds);
 int bs_ctx_set_chunk_log2(bs_ctx* ctx, bs_mode mode, int log2_chunk_max);
 int bs_ctx_get_chunk_log2(const bs_ctx* ctx, bs_mode mode);
 
+/* Accuracy target of BS_MIXED: a job runs in the FP32 kernels when the
+ * precision rule predicts an FP32 error of at most tol * prod_j ||a_j||^{N_j}
+ * (column norms over the rows repeated by their multiplicities), else in the
+ * FP64 kernels.  Default 1e-6.  Larger values keep more jobs in FP32; a value
+ * >= 1e300 sends every MIXED job to FP32 (to measure the FP32 error itself).
+ * Errors: BS_EINVAL (tol <= 0 or NaN). */
+int bs_ctx_set_mixed_tolerance(bs_ctx* ctx, double tol);
+
 /* Autotuner: times a synthetic problem of the given kind (0 permanent,
  * 1 minors), mode and K product columns (4..48) with chunk-length caps
  * 2^8, 2^10, 2^12, 2^14 (the chunk length is the re-seed interval of the
@@ -181,16 +189,19 @@ int bs_perm_formula(bs_ctx* ctx, const bs_c128* A, int n, int ld, bs_formula for
                     bs_c128* out_lo);
 
 /* Allocation-free permanent, for callers that may not allocate device
- * memory when they need a result: code running while a CUDA graph is being
- * captured on its stream, hosts whose memory manager forbids allocations
- * outside its own budget, real-time loops that must not enter the CUDA
- * allocator.  Computes the same permanent as bs_perm (same kernels; FP64 or
- * MIXED) without any device or host heap allocation: all device scratch is
- * one file-scope __device__ array of 8 MiB that every GPU loading the library
- * holds until the process exits.  The paper has no counterpart of this call.
+ * memory when they need a result: hosts whose memory manager owns a fixed
+ * device budget and forbids allocations outside it, and real-time loops that
+ * must not enter the CUDA allocator (cudaMalloc / cudaFree may synchronise the
+ * device and have no latency bound).  Computes the same permanent as bs_perm
+ * (same kernels; FP64 or MIXED) without any device or host heap allocation:
+ * all device scratch is one file-scope __device__ array of 8 MiB that every
+ * GPU loading the library holds until the process exits.  The paper has no
+ * counterpart of this call.
  *   A, row_mult, col_mult, out, out_lo: host memory as in bs_perm (no
- *   context); stream: a cudaStream_t as void* (0 = legacy default stream),
- *   synchronised before the call returns.
+ *   context); stream: a cudaStream_t as void* (0 = legacy default stream);
+ *   the inputs are staged from the caller's stack and the call synchronises
+ *   the stream before it returns.  There is no deadline: the walk runs to
+ *   the end of the job.
  * Limit: the job's warp tasks must fit the fixed scratch (about 2.6e5 tasks,
  * e.g. every permanent with up to 2^34 addends); larger jobs return
  * BS_EINVAL with a message naming the limit.  The first call on a device looks
@@ -228,6 +239,15 @@ int bs_sample(bs_ctx* ctx, const bs_c128* U, int m, const int* input_occupation,
  * lossy simulation by extra modes).  m_detected <= 0 means m_rows. */
 int bs_sample_ex(bs_ctx* ctx, const bs_c128* U, int m_rows, int m_cols, int ld, const int* input_occupation,
                  int n_samples, uint64_t seed, int m_detected, bs_mode mode, int* out);
+
+/* bs_sample_ex that also returns each chain's drawn rows: rows_out
+ * (n_samples x n, host, n = sum of input_occupation) receives r_1, ..., r_n
+ * of every sample in draw order (step k of Clifford & Clifford's algorithm
+ * draws r_k; the occupation counts in out are their histogram over rows <
+ * m_detected).  The draws are the same as bs_sample_ex's for the same
+ * arguments.  Errors as bs_sample_ex, and BS_EINVAL when rows_out is NULL. */
+int bs_sample_trace(bs_ctx* ctx, const bs_c128* U, int m_rows, int m_cols, int ld, const int* input_occupation,
+                    int n_samples, uint64_t seed, int m_detected, bs_mode mode, int* out, int* rows_out);
 
 /* Device-pointer form of bs_sample_ex: U_dev and out_dev on the device,
  * input_occupation on the host.  Enqueued; valid after bs_ctx_sync(). */
@@ -328,6 +348,15 @@ int bs_debug_gray_walk(int ndigits, int nbin, const int* radix, uint64_t start, 
  * and info[7] = warp tasks when the job runs alone in FP64 mode.  Returns
  * BS_EINVAL on invalid multiplicities. */
 int bs_debug_plan(int rows, int cols, const int* row_mult, const int* col_mult, int kind, int64_t* info);
+
+/* Host-only view of the BS_MIXED precision rule for a permanent (kind 0) or
+ * minors (kind 1) problem planned alone: *log2_err receives the predicted
+ * log2 of the FP32 walk's error relative to prod_j ||a_j||^{N_j}, *log2L
+ * (nullable) the FP32 chunk length it assumed.  The job runs in FP32 when
+ * *log2_err <= log2 of the MIXED tolerance (bs_ctx_set_mixed_tolerance,
+ * default 1e-6).  Returns BS_EINVAL on invalid multiplicities. */
+int bs_debug_mixed_error(int rows, int cols, const int* row_mult, const int* col_mult, int kind, double* log2_err,
+                         int* log2L);
 
 #ifdef __cplusplus
 }

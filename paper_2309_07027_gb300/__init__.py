@@ -84,6 +84,7 @@ def load():
         "bs_ctx_set_deadline": ([vp, C.c_double], C.c_int),
         "bs_ctx_set_chunk_log2": ([vp, C.c_int, C.c_int], C.c_int),
         "bs_ctx_get_chunk_log2": ([vp, C.c_int], C.c_int),
+        "bs_ctx_set_mixed_tolerance": ([vp, C.c_double], C.c_int),
         "bs_tune": ([vp, C.c_int, C.c_int, C.c_int, ip, dp], C.c_int),
         "bs_perm": ([vp, vp, C.c_int, C.c_int, C.c_int, ip, ip, C.c_int, vp, vp], C.c_int),
         "bs_perm_formula": ([vp, vp, C.c_int, C.c_int, C.c_int, vp, vp], C.c_int),
@@ -95,6 +96,8 @@ def load():
                          C.c_int),
         "bs_sample_dev": ([vp, vp, C.c_int, C.c_int, C.c_int, ip, C.c_int, C.c_uint64, C.c_int, C.c_int, vp],
                           C.c_int),
+        "bs_sample_trace": ([vp, vp, C.c_int, C.c_int, C.c_int, ip, C.c_int, C.c_uint64, C.c_int, C.c_int, ip,
+                             ip], C.c_int),
         "bs_ctx_set_profiling": ([vp, C.c_int], C.c_int),
         "bs_ctx_set_graphs": ([vp, C.c_int], C.c_int),
         "bs_ctx_get_stats": ([vp, C.POINTER(_Stats)], C.c_int),
@@ -104,6 +107,7 @@ def load():
         "bs_debug_gray_walk": ([C.c_int, C.c_int, ip, C.c_uint64, C.c_int, ip, ip, C.POINTER(C.c_uint64)],
                                C.c_int),
         "bs_debug_plan": ([C.c_int, C.c_int, ip, ip, C.c_int, i64p], C.c_int),
+        "bs_debug_mixed_error": ([C.c_int, C.c_int, ip, ip, C.c_int, dp, ip], C.c_int),
         "bs_perm_noalloc": ([vp, C.c_int, C.c_int, C.c_int, ip, ip, C.c_int, vp, vp, vp], C.c_int),
         "bs_server_create": ([C.POINTER(C.c_void_p), C.c_int, C.c_size_t, C.c_int, C.c_int, C.c_int], C.c_int),
         "bs_server_destroy": ([vp], None),
@@ -200,6 +204,10 @@ class Context:
 
     def chunk_log2(self, mode: int) -> int:
         return int(self._L.bs_ctx_get_chunk_log2(self._p, int(mode)))
+
+    def set_mixed_tolerance(self, tol: float = 1e-6):
+        """MIXED accuracy target (bs_ctx_set_mixed_tolerance); >= 1e300 forces FP32."""
+        _check(self._L.bs_ctx_set_mixed_tolerance(self._p, float(tol)), self._p)
 
     def set_graphs(self, on: bool):
         """Replay the sampler's step loop from a captured CUDA graph (default)."""
@@ -345,6 +353,21 @@ class Context:
                self._p)
         return out
 
+    def sample_trace(self, u, occupation, n_samples: int, seed: int, m_detected: int = 0, mode: int = BS_FP64):
+        """bs_sample_trace: (counts[n_samples, m_detected], rows[n_samples, n]),
+        rows holding the drawn row of every step in draw order."""
+        u = _c128(u)
+        mr, mc = u.shape
+        occ = _i32(occupation, mc)
+        n = int(occ.sum())
+        mdet = mr if m_detected <= 0 or m_detected > mr else int(m_detected)
+        out = np.zeros((max(n_samples, 0), mdet), dtype=np.int32)
+        rows = np.zeros((max(n_samples, 0), n), dtype=np.int32)
+        _check(self._L.bs_sample_trace(self._p, u.ctypes.data, mr, mc, mc, _ip(occ), int(n_samples),
+                                       C.c_uint64(int(seed) & ((1 << 64) - 1)), int(mdet), int(mode), _ip(out),
+                                       _ip(rows)), self._p)
+        return out, rows
+
     def sample_dev(self, u_dev, occupation, n_samples: int, seed: int, out_dev, m_detected: int = 0,
                    mode: int = BS_FP64):
         """Device form: ``u_dev`` is a CUDA complex128 (m_rows x m_cols) tensor,
@@ -424,20 +447,23 @@ class Server:
 
 
 # ------------------------------------------------------------------ allocation-free call
-def perm_noalloc(a, row_mult=None, col_mult=None, mode: int = BS_FP64, stream=0):
-    """bs_perm_noalloc: the permanent without any device allocation (for
-    callers that may not allocate, e.g. during a CUDA graph capture on their
-    stream).  ``stream``: a torch.cuda.Stream, a raw handle, or 0."""
+def perm_noalloc(a, row_mult=None, col_mult=None, mode: int = BS_FP64, stream=0, with_tail: bool = False):
+    """bs_perm_noalloc: the permanent without any device allocation, for
+    callers whose memory manager forbids allocations outside its own budget or
+    that must not enter the CUDA allocator.  ``stream``: a torch.cuda.Stream,
+    a raw handle, or 0; synchronised before the call returns.  Returns the
+    value, or (value, tail) with with_tail=True."""
     L = load()
     a = _c128(a)
     R, K = a.shape
     M = _i32(np.ones(R) if row_mult is None else row_mult, R)
     N = _i32(np.ones(K) if col_mult is None else col_mult, K)
     out = np.zeros(1, dtype=np.complex128)
+    lo = np.zeros(1, dtype=np.complex128)
     handle = int(getattr(stream, "cuda_stream", stream) or 0)
     _check(L.bs_perm_noalloc(a.ctypes.data, R, K, K, _ip(M), _ip(N), int(mode), C.c_void_p(handle),
-                             out.ctypes.data, None))
-    return complex(out[0])
+                             out.ctypes.data, lo.ctypes.data))
+    return (complex(out[0]), complex(lo[0])) if with_tail else complex(out[0])
 
 
 # ------------------------------------------------------------------ host-only helpers
@@ -453,6 +479,19 @@ def debug_gray_walk(radix, nbin, start, steps):
     _check(L.bs_debug_gray_walk(nd, int(nbin), _ip(r), C.c_uint64(int(start)), int(steps), _ip(deltas),
                                 _ip(moved), w.ctypes.data_as(C.POINTER(C.c_uint64))))
     return deltas[:, :nd], moved[:steps], w[:steps]
+
+
+def debug_mixed_error(row_mult, col_mult, kind=0):
+    """MIXED precision rule for the problem planned alone: (predicted log2 of
+    the FP32 error relative to prod ||a_j||, FP32 chunk log2, runs in FP32 at
+    the default tolerance 1e-6)."""
+    L = load()
+    M = _i32(row_mult)
+    N = _i32(col_mult)
+    e = C.c_double(0.0)
+    l = C.c_int(0)
+    _check(L.bs_debug_mixed_error(len(M), len(N), _ip(M), _ip(N), int(kind), C.byref(e), C.byref(l)))
+    return float(e.value), int(l.value), float(e.value) <= float(np.float32(-19.93))
 
 
 def debug_plan(row_mult, col_mult, kind=0):

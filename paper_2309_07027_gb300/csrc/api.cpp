@@ -108,6 +108,7 @@ struct bs_ctx {
     cudaEvent_t stage_ev[2] = {nullptr, nullptr};
     double deadline_s = 0.0;
     int log2max[2] = {12, 12};
+    float mixed_log2_tol = BS_MIXED_LOG2_TOL_DEFAULT;  // MIXED precision rule threshold
     bool profiling = false;
     std::vector<Timed> timed;
     std::vector<double> walk_log;  // per-launch walk durations not yet read
@@ -295,11 +296,19 @@ int plan_upload(bs_ctx* c, std::vector<JobIn>& ins, bs_mode mode, Prepared& P) {
         uint32_t ntasks;
     };
     std::vector<Row> rows;
+    std::vector<double> q_work(BS_MIXED_QMAX + 1);
     for (auto& in : ins) {
         if (in.p->trivial) continue;
         Row r;
         r.in = in;
-        r.fp32 = (mode == BS_MIXED && bs_mixed_uses_fp32(in.p->radix, in.p->nrows, in.p->K, in.p->n)) ? 1 : 0;
+        r.fp32 = 0;
+        if (mode == BS_MIXED) {
+            // the rule needs the chunk length the FP32 kernel would use
+            const int cpt32 = bs_chunks_per_task(in.p->kind, 1, in.p->K);
+            const int l32 = bs_choose_log2L_single(in.p->C, cpt32, c->log2max[1], BS_TARGET_TASKS_SINGLE_FP32);
+            r.fp32 = bs_mixed_uses_fp32(in.p->radix, in.p->nrows, in.p->pinned_m, in.p->K, in.p->n, l32,
+                                        c->mixed_log2_tol, q_work.data());
+        }
         r.kind = in.p->kind;
         r.bucket = (in.p->K + 3) >> 2;
         r.cpt = bs_chunks_per_task(r.kind, r.fp32, in.p->K);
@@ -604,6 +613,13 @@ int batch_walk(bs_ctx* c, std::vector<IntPlan>& plans, const std::vector<int64_t
     return BS_OK;
 }
 
+// The MIXED threshold as a key entry (its bits).
+static int64_t tol_key(const bs_ctx* c) {
+    int32_t b = 0;
+    std::memcpy(&b, &c->mixed_log2_tol, sizeof(b));
+    return b;
+}
+
 // Graph-cache key of one job planned alone: everything the device sequence
 // depends on besides the buffers (the plan's digits, sources and product
 // columns, the source shape, mode, chunk caps and deadline).  The leading -1
@@ -614,7 +630,7 @@ static std::vector<int64_t> plan_key(const bs_ctx* c, const IntPlan& p, int rows
     std::vector<int64_t> k = {-1, (int64_t)p.kind, (int64_t)p.formula, (int64_t)p.n, (int64_t)p.K,
                               (int64_t)p.nrows, (int64_t)p.nbin, (int64_t)p.C, (int64_t)p.trans,
                               (int64_t)p.pinned_src, (int64_t)rows, (int64_t)cols, (int64_t)mode,
-                              (int64_t)c->log2max[0], (int64_t)c->log2max[1], dl};
+                              (int64_t)c->log2max[0], (int64_t)c->log2max[1], dl, tol_key(c)};
     for (int j = 0; j < p.nrows; ++j) k.insert(k.end(), {(int64_t)p.radix[j], (int64_t)p.digit_src[j]});
     for (int j = 0; j < p.K; ++j) k.push_back(p.col_src[j]);
     return k;
@@ -723,7 +739,7 @@ int enqueue_sampler_batch(bs_ctx* c, const bs::CcArgs& a, const bs::CcArgs* da, 
 }
 
 int sample_dev(bs_ctx* c, const double2* dU, int m_rows, int m_cols, int ld, const int* occ, int n_samples,
-               uint64_t seed, int m_det, bs_mode mode, int* dout) {
+               uint64_t seed, int m_det, bs_mode mode, int* dout, int* dtrace = nullptr) {
     if (m_rows <= 0 || m_cols <= 0) return fail(BS_EINVAL, "bad interferometer size %d x %d", m_rows, m_cols);
     if (ld < m_cols) return fail(BS_EINVAL, "leading dimension %d < columns %d", ld, m_cols);
     if (m_rows > 8192) return fail(BS_EINVAL, "at most 8192 output modes are supported");
@@ -811,12 +827,14 @@ int sample_dev(bs_ctx* c, const double2* dU, int m_rows, int m_cols, int ld, con
         a.lists = static_cast<int*>(c->cc_lists.p);
         a.list_len = reinterpret_cast<int*>(ctl + kCtlListLen);
         a.out = dout + (size_t)base * m_det;
+        a.trace = dtrace ? dtrace + (size_t)base * n : nullptr;
         a.meta_stride = meta_stride;
         a.data_stride = data_stride;
         a.tasks_stride = (int64_t)tasks_stride;
         a.mixed = mixed ? 1 : 0;
         a.log2max64 = c->log2max[0];
         a.log2max32 = c->log2max[1];
+        a.mixed_log2_tol = c->mixed_log2_tol;
         // the kernels read the arguments from device memory (pageable copy:
         // staged before cudaMemcpyAsync returns, so `a` may go out of scope)
         BS_CUDA(cudaMemcpyAsync(da, &a, sizeof(a), cudaMemcpyHostToDevice, c->stream));
@@ -844,6 +862,8 @@ int sample_dev(bs_ctx* c, const double2* dU, int m_rows, int m_cols, int ld, con
                                      (uint64_t)(uintptr_t)c->cc_lists.p, (uint64_t)(uintptr_t)c->ctl.p,
                                      (uint64_t)(uintptr_t)da, tasks_stride, dl, (uint64_t)(uintptr_t)c->stream,
                                      (uint64_t)c->profiling};
+        // (the MIXED threshold is read by the device planner from *da, so a
+        // replay follows a changed threshold without a new capture)
         harvest_graph_timing(c);
         if (!c->cc_exec || key != c->cc_key) {
             if (c->cc_exec) {
@@ -995,6 +1015,14 @@ int bs_ctx_set_chunk_log2(bs_ctx* c, bs_mode mode, int log2_chunk_max) {
     return BS_OK;
 }
 
+int bs_ctx_set_mixed_tolerance(bs_ctx* c, double tol) {
+    if (!ok_ctx(c)) return BS_EINVAL;
+    if (!(tol > 0.0)) return fail(BS_EINVAL, "MIXED tolerance must be positive");
+    std::lock_guard<std::mutex> lk(c->mu);
+    c->mixed_log2_tol = tol >= 1e300 ? 1e30f : (float)std::log2(tol);
+    return BS_OK;
+}
+
 int bs_ctx_get_chunk_log2(const bs_ctx* c, bs_mode mode) {
     if (!c) return BS_EINVAL;
     return c->log2max[mode == BS_MIXED ? 1 : 0];
@@ -1091,7 +1119,7 @@ static std::vector<int64_t> batch_key(const bs_ctx* c, int count, const int64_t*
     std::vector<int64_t> k;
     int64_t dl = 0;
     std::memcpy(&dl, &c->deadline_s, sizeof(dl));
-    k.insert(k.end(), {(int64_t)count, (int64_t)mode, (int64_t)c->log2max[0], (int64_t)c->log2max[1], dl});
+    k.insert(k.end(), {(int64_t)count, (int64_t)mode, (int64_t)c->log2max[0], (int64_t)c->log2max[1], dl, tol_key(c)});
     for (int b = 0; b < count; ++b) {
         k.insert(k.end(), {a_offset[b], (int64_t)rows[b], (int64_t)cols[b]});
         for (int r = 0; r < rows[b]; ++r) k.push_back(mult_packed[row_mult_off[b] + r]);
@@ -1184,37 +1212,57 @@ int bs_sample_dev(bs_ctx* c, const bs_c128* U_dev, int m_rows, int m_cols, int l
                       seed, m_detected, mode, out_dev);
 }
 
-int bs_sample_ex(bs_ctx* c, const bs_c128* U, int m_rows, int m_cols, int ld, const int* input_occupation,
-                 int n_samples, uint64_t seed, int m_detected, bs_mode mode, int* out) {
+// Host-memory sampling: U up, counts (and, when rows_out is given, the drawn
+// rows of every step) back.
+static int sample_host(bs_ctx* c, const bs_c128* U, int m_rows, int m_cols, int ld, const int* input_occupation,
+                       int n_samples, uint64_t seed, int m_detected, bs_mode mode, int* out, int* rows_out) {
     if (!ok_ctx(c)) return BS_EINVAL;
     if (mode != BS_FP64 && mode != BS_MIXED) return fail(BS_EINVAL, "unknown mode %d", (int)mode);
     if (!U || (!out && n_samples > 0)) return fail(BS_EINVAL, "NULL pointer");
     if (m_rows <= 0 || m_cols <= 0 || ld < m_cols) return fail(BS_EINVAL, "bad interferometer size");
     if (n_samples <= 0) return n_samples < 0 ? fail(BS_EINVAL, "negative sample count") : BS_OK;
+    if (!input_occupation) return fail(BS_EINVAL, "input occupation is NULL");
+    int n = 0;
+    for (int i = 0; i < m_cols; ++i) n += input_occupation[i] > 0 ? input_occupation[i] : 0;
     const int mdet = (m_detected <= 0 || m_detected > m_rows) ? m_rows : m_detected;
     std::lock_guard<std::mutex> lk(c->mu);
     BS_CUDA(cudaSetDevice(c->device));
     const size_t ub = (size_t)m_rows * m_cols * sizeof(bs_c128);
     const size_t ob = (size_t)n_samples * mdet * sizeof(int);
+    const size_t tb = rows_out ? (size_t)n_samples * n * sizeof(int) : 0;
     int rc;
     if ((rc = ensure(c, c->cc_U, ub))) return rc;
-    if ((rc = ensure(c, c->cc_out, ob))) return rc;
-    bs_c128* h = static_cast<bs_c128*>(stage(c, std::max(ub, ob)));
+    if ((rc = ensure(c, c->cc_out, ob + tb))) return rc;
+    bs_c128* h = static_cast<bs_c128*>(stage(c, std::max(ub, ob + tb)));
     if (!h) return fail(BS_ENOMEM, "pinned host staging allocation failed");
     copy_matrix(h, U, m_rows, m_cols, ld);
     BS_CUDA(cudaMemcpyAsync(c->cc_U.p, h, ub, cudaMemcpyHostToDevice, c->stream));
     BS_CUDA(cudaEventRecord(c->stage_ev[c->stage_cur], c->stream));
+    int* d_out = static_cast<int*>(c->cc_out.p);
+    int* d_trace = rows_out ? d_out + (size_t)n_samples * mdet : nullptr;
     rc = sample_dev(c, static_cast<const double2*>(c->cc_U.p), m_rows, m_cols, m_cols, input_occupation, n_samples,
-                    seed, mdet, mode, static_cast<int*>(c->cc_out.p));
+                    seed, mdet, mode, d_out, d_trace);
     if (rc) return rc;
     // read back through a staging buffer (stage() waits until no copy out of
     // it is pending)
-    void* hb = stage(c, ob);
+    void* hb = stage(c, ob + tb);
     if (!hb) return fail(BS_ENOMEM, "pinned host staging allocation failed");
-    BS_CUDA(cudaMemcpyAsync(hb, c->cc_out.p, ob, cudaMemcpyDeviceToHost, c->stream));
+    BS_CUDA(cudaMemcpyAsync(hb, c->cc_out.p, ob + tb, cudaMemcpyDeviceToHost, c->stream));
     if ((rc = sync_and_check(c))) return rc;
     std::memcpy(out, hb, ob);
+    if (rows_out) std::memcpy(rows_out, static_cast<char*>(hb) + ob, tb);
     return BS_OK;
+}
+
+int bs_sample_ex(bs_ctx* c, const bs_c128* U, int m_rows, int m_cols, int ld, const int* input_occupation,
+                 int n_samples, uint64_t seed, int m_detected, bs_mode mode, int* out) {
+    return sample_host(c, U, m_rows, m_cols, ld, input_occupation, n_samples, seed, m_detected, mode, out, nullptr);
+}
+
+int bs_sample_trace(bs_ctx* c, const bs_c128* U, int m_rows, int m_cols, int ld, const int* input_occupation,
+                    int n_samples, uint64_t seed, int m_detected, bs_mode mode, int* out, int* rows_out) {
+    if (!rows_out && n_samples > 0) return fail(BS_EINVAL, "rows_out is NULL");
+    return sample_host(c, U, m_rows, m_cols, ld, input_occupation, n_samples, seed, m_detected, mode, out, rows_out);
 }
 
 int bs_sample(bs_ctx* c, const bs_c128* U, int m, const int* input_occupation, int n_samples, uint64_t seed,
@@ -1400,6 +1448,24 @@ int bs_debug_gray_walk(int ndigits, int nbin, const int* radix, uint64_t start, 
             for (int j = 0; j < ndigits; ++j) deltas[(size_t)s * ndigits + j] = bs_gray_delta(g, j);
         if (weights) weights[s] = g.w;
     }
+    return BS_OK;
+}
+
+int bs_debug_mixed_error(int rows, int cols, const int* row_mult, const int* col_mult, int kind, double* log2_err,
+                         int* log2L) {
+    if (!log2_err) return fail(BS_EINVAL, "log2_err is NULL");
+    IntPlan p;
+    int rc = plan_job(rows, cols, row_mult, col_mult, kind == 1 ? BS_KIND_MINORS : BS_KIND_PERM, p);
+    if (rc) return rc;
+    if (p.trivial) {
+        *log2_err = -1000.0;
+        if (log2L) *log2L = 0;
+        return BS_OK;
+    }
+    const int l32 = bs_choose_log2L_single(p.C, bs_chunks_per_task(p.kind, 1, p.K), 12, BS_TARGET_TASKS_SINGLE_FP32);
+    std::vector<double> q_work(BS_MIXED_QMAX + 1);
+    *log2_err = bs_mixed_log2_error(p.radix, p.nrows, p.pinned_m, p.K, p.n, l32, q_work.data());
+    if (log2L) *log2L = l32;
     return BS_OK;
 }
 

@@ -1,13 +1,14 @@
 // Allocation-free permanent: bs_perm_noalloc.
 //
 // Who needs it: callers that must not allocate device memory at the moment
-// they ask for a permanent -- code running while a CUDA graph is being
-// captured on its stream (a cudaMalloc there would invalidate the capture or
-// synchronise the device), hosts whose memory manager owns a fixed device
-// budget and forbids allocations outside it, and real-time loops that may
-// not enter the CUDA allocator.  bs_perm (a context with grow-only buffers)
-// allocates on first use and whenever a larger problem arrives; this entry
-// point never does.
+// they ask for a permanent -- hosts whose memory manager owns a fixed device
+// budget and forbids allocations outside it (a cudaMalloc there can fail or
+// take memory the manager has promised elsewhere), and real-time loops that
+// may not enter the CUDA allocator (cudaMalloc and cudaFree can synchronise
+// the device and have no latency bound).  bs_perm (a context with grow-only
+// buffers) allocates on first use and whenever a larger problem arrives;
+// this entry point never does.  It has no deadline: the walk runs to the
+// end of the job.
 //
 // How: every byte of device scratch (job descriptor, metadata, the compacted
 // matrix, the packed column data, the per-task partial sums, the result and
@@ -118,7 +119,13 @@ extern "C" int bs_perm_noalloc(const bs_c128* A, int rows, int cols, int ld, con
     }
     if (!A) return bs::fail(BS_EINVAL, "matrix pointer is NULL");
     if (ld < cols) return bs::fail(BS_EINVAL, "leading dimension %d < columns %d", ld, cols);
-    const int fp32 = (mode == BS_MIXED && bs_mixed_uses_fp32(p.radix, p.nrows, p.K, p.n)) ? 1 : 0;
+    int fp32 = 0;
+    if (mode == BS_MIXED) {
+        double q_work[BS_MIXED_QMAX + 1];  // the rule's scratch, on the stack
+        const int l32 = bs_choose_log2L_single(p.C, bs_chunks_per_task(BS_KIND_PERM, 1, p.K), 12,
+                                               BS_TARGET_TASKS_SINGLE_FP32);
+        fp32 = bs_mixed_uses_fp32(p.radix, p.nrows, p.pinned_m, p.K, p.n, l32, BS_MIXED_LOG2_TOL_DEFAULT, q_work);
+    }
     const int cpt = bs_chunks_per_task(BS_KIND_PERM, fp32, p.K);
     const int log2L = bs_choose_log2L_single(p.C, cpt, 12,
                                              fp32 ? BS_TARGET_TASKS_SINGLE_FP32 : BS_TARGET_TASKS_SINGLE);
@@ -188,7 +195,6 @@ extern "C" int bs_perm_noalloc(const bs_c128* A, int rows, int cols, int ld, con
     NA_CUDA(cudaMemcpyAsync(res, scr + kOut, sizeof(res), cudaMemcpyDeviceToHost, s));
     NA_CUDA(cudaMemcpyAsync(&status, scr + kCtl + 8, sizeof(int), cudaMemcpyDeviceToHost, s));
     NA_CUDA(cudaStreamSynchronize(s));
-    if (status == BS_STATUS_TIMEOUT) return bs::fail(BS_ETIMEOUT, "a walk kernel passed its deadline");
     if (status != BS_STATUS_OK) return bs::fail(BS_ECUDA, "walk kernel status %d", status);
     out->re = res[0].x;
     out->im = res[0].y;

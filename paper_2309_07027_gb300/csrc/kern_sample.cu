@@ -90,6 +90,7 @@ __global__ void cc_plan_kernel(const CcArgs* __restrict__ pa, int k) {
     __shared__ int urow[BS_MAX_PHOTONS], ucnt[BS_MAX_PHOTONS];
     __shared__ int drad[BS_MAX_PHOTONS], dsrc[BS_MAX_PHOTONS];
     __shared__ bs_job sjb;
+    __shared__ double q_work[BS_MIXED_QMAX + 1];  // the MIXED rule's scratch (thread 0)
     const int s = blockIdx.x;
     const int* rows = a.rows + (size_t)s * a.n;
     const int* cols = a.cols + (size_t)s * a.n;
@@ -154,7 +155,15 @@ __global__ void cc_plan_kernel(const CcArgs* __restrict__ pa, int k) {
         }
         jb.nrows = nrows;
         jb.nbin = nbin;
-        const int fp32 = a.mixed ? bs_mixed_uses_fp32(drad, nrows, k, k - 1) : 0;
+        uint64_t C = 1;
+        for (int j = 0; j < nrows; ++j) C *= (uint64_t)drad[j];
+        int fp32 = 0;
+        if (a.mixed) {
+            // decided with the chunk length the FP32 kernel would use
+            const int l32 = bs_choose_log2L(C, bs_chunks_per_task(BS_KIND_MINORS, 1, k), BS_LOG2L_MIN_MANY,
+                                            a.log2max32, BS_TARGET_TASKS_MANY);
+            fp32 = bs_mixed_uses_fp32(drad, nrows, ucnt[p], k, k - 1, l32, a.mixed_log2_tol, q_work);
+        }
         jb.fp32 = fp32;
         jb.normalize = fp32;
         // the chain's data slot holds data_stride complex doubles; an FP32
@@ -168,8 +177,6 @@ __global__ void cc_plan_kernel(const CcArgs* __restrict__ pa, int k) {
         }
         for (int c = 0; c < k; ++c) meta[2 * nrows + c] = cols[c];
         meta[2 * nrows + 2 * k] = urow[p];
-        uint64_t C = 1;
-        for (int j = 0; j < nrows; ++j) C *= (uint64_t)meta[j];
         jb.C = C;
         jb.log2L = bs_choose_log2L(C, cpt, BS_LOG2L_MIN_MANY, log2max, BS_TARGET_TASKS_MANY);
         jb.ntasks = (uint32_t)((C + ((uint64_t)cpt << jb.log2L) - 1) / ((uint64_t)cpt << jb.log2L));
@@ -288,6 +295,8 @@ __global__ void cc_draw_kernel(const CcArgs* __restrict__ pa, int k) {
     }
 }
 
+// Occupation counts of every chain; with a trace buffer, also the drawn
+// rows r_1..r_n in draw order.
 __global__ void cc_counts_kernel(const CcArgs* __restrict__ pa) {
     const CcArgs& a = *pa;
     const int s = blockIdx.x;
@@ -297,6 +306,8 @@ __global__ void cc_counts_kernel(const CcArgs* __restrict__ pa) {
         for (int t = 0; t < a.n; ++t) c += rows[t] == i;
         a.out[(size_t)s * a.m_det + i] = c;
     }
+    if (a.trace)
+        for (int t = threadIdx.x; t < a.n; t += blockDim.x) a.trace[(size_t)s * a.n + t] = rows[t];
 }
 
 // `a` is the host copy (launch shapes); `da` the same struct in device

@@ -120,6 +120,7 @@ int plan_job(int rows, int cols, const int* M, const int* N, int kind, IntPlan& 
     for (int i = 1; i < nR; ++i)
         if (Rm[i] < Rm[pin]) pin = i;
     p.pinned_src = Rs[pin];
+    p.pinned_m = Rm[pin];
     // digits: binary first (order of appearance, then a split pinned row of
     // multiplicity 2), then repeated rows by increasing multiplicity
     int dm[BS_MAX_DIGITS], ds[BS_MAX_DIGITS], nd = 0;

@@ -23,6 +23,7 @@ struct IntPlan {
     uint64_t C = 1;
     bool trans = false;
     int pinned_src = 0;
+    int pinned_m = 1;      // multiplicity of the pinned row
     int radix[BS_MAX_DIGITS];
     int digit_src[BS_MAX_DIGITS];
     int col_src[BS_MAX_COLS];

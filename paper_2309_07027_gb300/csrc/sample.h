@@ -85,28 +85,88 @@ BS_HD int64_t bs_flops_per_addend(int K, int kind) {
     return 2 * (int64_t)K + 12 * (kk - 2) + 2 + 8 * (int64_t)K;
 }
 
-// MIXED-mode precision rule.  FP32 rounding gives each addend a relative
-// error of about K 2^-24, amplified by up to sqrt(M) where a column sum of a
-// repeated row cancels; the addends' root-sum-square is about
-// 2^(1-n) sqrt(prod_j C(2 M_j, M_j)) times prod_col ||a_col|| (Vandermonde:
-// sum_D C(M, D)^2 = C(2M, M)), so the predicted error relative to the MIXED
-// tolerance scale prod_col ||a_col|| is
-//   log2 K + log2(2n)/2 + log2(max M)/2 - 24 + (1 - n)
-//     + sum_j log2 C(2 M_j, M_j) / 2 + 2        (safety factor 4).
-// The job runs in FP32 when that is <= log2(1e-6), else in FP64 ("FP64 ...
-// at large k, where cancellation demands it").  Depends only on the
-// multiplicities, K and n, so every planner decides alike.
-BS_HD int bs_mixed_uses_fp32(const int* radix, int nrows, int K, int n) {
-    float lg = log2f((float)(K > 1 ? K : 1)) + 0.5f * log2f(2.0f * (float)(n > 1 ? n : 1)) - 24.0f +
-               (1.0f - (float)n) + 2.0f;
-    int mmax = 1;
+// MIXED-mode precision rule: the predicted log2 of the FP32 walk's error
+// relative to the MIXED tolerance scale prod_j ||a_j||^{N_j} (column norms
+// over the rows repeated by their multiplicities).
+//
+// Model.  With the entries of a column of comparable magnitude
+// (|a_kj|^2 ~ ||a_j||^2 / n), the column sum of the addend with Delta vector D
+// has |c_j(D)|^2 ~ ||a_j||^2 Q(D) / n, Q(D) = sum over rows of (M_k - 2 D_k)^2,
+// so the root-sum-square of the weighted addends is
+//   RSS / prod_j ||a_j|| = 2^(1-n) sqrt( sum_D prod_k C(M_k, D_k)^2 (Q(D)/n)^K )
+// (the pinned row: coefficient M_p - 2D for D in [0, M_p), weight
+// C(M_p - 1, D)).  A heavily repeated row enters through its extreme D,
+// whose coefficients +-M make those addends large though their weights are
+// small.  Each addend carries a relative rounding error of about
+// sqrt(K) 2^-24, and the incremental column sums drift like sqrt(steps)
+// within a chunk of 2^log2L addends, so
+//   log2 err ~ log2(RSS / prod ||a_j||) + log2(K)/2
+//              + max(0, log2L - 8)/2 + c,
+// c = -22.02 being the largest residual of that form over 724 measured FP32
+// jobs (K = 10..40, multiplicities 1..8, chunks 2^3..2^12, errors against
+// the FP64 kernels on Haar-random inputs), plus one bit of margin.  The sum
+// over D is a dynamic program over Q: binary rows add 1 to Q with weight 2
+// (two values of D); every other row adds (top - 2D)^2 with weight C(.,D)^2.
+// The model assumes unstructured inputs; matrices with many exact zeros
+// (block structure) cancel far more than it predicts and belong in FP64.
+#define BS_MIXED_LOG2_TOL_DEFAULT (-19.93f)  // log2(1e-6)
+#define BS_MIXED_QMAX (BS_MAX_PHOTONS * BS_MAX_PHOTONS)  // Q <= sum M_k^2 <= n^2
+#define BS_MIXED_RESIDUAL (-21.02)
+
+// q_work: BS_MIXED_QMAX + 1 doubles of scratch.  radix / nrows: the job's
+// digits; pinned_m: multiplicity of the pinned row (its other pinned_m - 1
+// copies are the digit of radix pinned_m when pinned_m > 1); log2L: the
+// chunk length the FP32 kernel would use for the job.
+BS_HD float bs_mixed_log2_error(const int* radix, int nrows, int pinned_m, int K, int n, int log2L,
+                                double* q_work) {
+    if (n <= 0) return -1000.0f;
+    double* f = q_work;
+    f[0] = 1.0;
+    int qmax = 0, nb = 0;
+    int off = pinned_m <= 1 ? 1 : 0;  // a lone pinned copy: coefficient 1
+    bool pin_seen = pinned_m <= 1;
     for (int j = 0; j < nrows; ++j) {
         const int M = radix[j] - 1;
-        if (M > mmax) mmax = M;
-        for (int t = 1; t <= M; ++t) lg += 0.5f * log2f((float)(M + t) / (float)t);
+        const bool pin = !pin_seen && radix[j] == pinned_m;
+        if (pin) pin_seen = true;
+        if (!pin && M == 1) {
+            ++nb;
+            continue;
+        }
+        const int top = pin ? pinned_m : M;  // largest |coefficient|
+        const int dmax = pin ? pinned_m - 1 : M;
+        const int add = top * top;
+        if (qmax + add > BS_MIXED_QMAX) return 1000.0f;  // outside the model: FP64
+        for (int q = qmax + add; q >= 0; --q) {
+            double acc = 0.0;
+            for (int d = 0; d <= dmax; ++d) {
+                const int sq = (top - 2 * d) * (top - 2 * d);
+                const int src = q - sq;
+                if (src < 0 || src > qmax) continue;
+                const double w = (double)bs_binom(dmax, d);
+                acc += f[src] * w * w;
+            }
+            f[q] = acc;
+        }
+        qmax += add;
     }
-    lg += 0.5f * log2f((float)mmax);
-    return lg <= -19.93f;
+    double total = 0.0;
+    const double inv_n = 1.0 / (double)n;
+    for (int q = 0; q <= qmax; ++q)
+        if (f[q] != 0.0) total += f[q] * pow((double)(q + off + nb) * inv_n, (double)K);
+    if (!(total > 0.0)) return -1000.0f;
+    const double lrss = (1.0 - (double)n) + 0.5 * (log2(total) + (double)nb);
+    const double drift = log2L > 8 ? 0.5 * (double)(log2L - 8) : 0.0;
+    return (float)(lrss + 0.5 * log2((double)(K > 1 ? K : 1)) + drift + BS_MIXED_RESIDUAL);
+}
+
+// The job runs in FP32 when the predicted error is <= log2_tol (default
+// log2(1e-6)), else in FP64 ("FP64 ... at large k, where cancellation
+// demands it").  Depends only on the multiplicities, K, n and the FP32
+// chunk length, so every planner with the same chunk rule decides alike.
+BS_HD int bs_mixed_uses_fp32(const int* radix, int nrows, int pinned_m, int K, int n, int log2L, float log2_tol,
+                             double* q_work) {
+    return bs_mixed_log2_error(radix, nrows, pinned_m, K, n, log2L, q_work) <= log2_tol;
 }
 
 namespace bs {
@@ -132,8 +192,10 @@ struct CcArgs {
     int* lists;                   // device job lists: [FP64: S][FP32: S]
     int* list_len;                // device list lengths [FP64, FP32]
     int* out;                     // device, S x m_det
+    int* trace;                   // device, S x n drawn rows in draw order (nullable)
     int64_t meta_stride, data_stride, tasks_stride;
     int mixed;                    // 1: MIXED mode (per-chain FP32 / FP64 rule)
+    float mixed_log2_tol;         // the rule's threshold, log2 of the MIXED tolerance
     int log2max64, log2max32;
 };
 

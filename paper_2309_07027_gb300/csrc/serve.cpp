@@ -561,7 +561,14 @@ int64_t bs_server_submit(bs_server* s, int kind, const bs_c128* A, int rows, int
     }
     r->mat.resize((size_t)rows * cols);
     for (int i = 0; i < rows; ++i) std::memcpy(&r->mat[(size_t)i * cols], A + (size_t)i * ld, sizeof(bs_c128) * cols);
-    r->fp32 = (s->mode == BS_MIXED && bs_mixed_uses_fp32(r->plan.radix, r->plan.nrows, r->plan.K, r->plan.n)) ? 1 : 0;
+    r->fp32 = 0;
+    if (s->mode == BS_MIXED) {
+        double q_work[BS_MIXED_QMAX + 1];
+        const int l32 = bs_choose_log2L(r->plan.C, bs_chunks_per_task(r->kind, 1, r->plan.K), BS_LOG2L_MIN_MANY, 12,
+                                        BS_TARGET_TASKS_MANY);
+        r->fp32 = bs_mixed_uses_fp32(r->plan.radix, r->plan.nrows, r->plan.pinned_m, r->plan.K, r->plan.n, l32,
+                                     BS_MIXED_LOG2_TOL_DEFAULT, q_work);
+    }
     r->cpt = bs_chunks_per_task(r->kind, r->fp32, r->plan.K);
     r->log2L = bs_choose_log2L(r->plan.C, r->cpt, BS_LOG2L_MIN_MANY, 12, BS_TARGET_TASKS_MANY);
     const uint64_t per = (uint64_t)r->cpt << r->log2L;

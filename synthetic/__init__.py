@@ -21,7 +21,7 @@ import numpy as np
 __all__ = [
     "rng", "haar_unitary", "random_complex", "gaussian_integer_matrix",
     "config_single", "config_batch", "config_cc", "config_serving", "config_lossy",
-    "collapse_modes", "lossy_isometry",
+    "collapse_modes", "lossy_isometry", "block_diagonal",
 ]
 
 
@@ -143,3 +143,37 @@ def config_lossy(n: int = 40, m: int = 60, eta: float = 0.5, seed: int = 5):
     u = haar_unitary(m, seed)
     v = lossy_isometry(u, np.arange(n), eta)
     return v, m
+
+
+def block_diagonal(K: int, n: int, seed: int, width: int = 12, mult: int = 3):
+    """Block-diagonal problem with K distinct columns (multiplicity 1) and n
+    photons (n = K for a permanent, K - 1 for Laplace minors).
+
+    The columns are split into ceil(K / width) nearly equal consecutive
+    groups; group g gets its own distinct rows, as many of multiplicity
+    ``mult`` as fit and the rest of multiplicity 1, whose multiplicities sum
+    to the group's column count -- except the last group, which gets one
+    photon less when n = K - 1.  The entries of each block are a block of one
+    Haar 64 x 64 unitary (disjoint rows and columns); every entry outside the
+    blocks is zero.  Returns (A[R, K], row_mult[R], col_mult[K], groups) with
+    groups = [(row indices, column indices), ...] into A."""
+    assert n in (K, K - 1) and K >= 1
+    u = haar_unitary(64, seed)
+    g = rng(seed + 17)
+    ngroups = -(-K // width)
+    bounds = [K * i // ngroups for i in range(ngroups + 1)]
+    rows_m, groups = [], []
+    for gi in range(ngroups):
+        kc = bounds[gi + 1] - bounds[gi]
+        photons = kc - (1 if (n == K - 1 and gi == ngroups - 1) else 0)
+        ms = [mult] * (photons // mult) + [1] * (photons % mult)
+        first = len(rows_m)
+        rows_m.extend(ms)
+        groups.append((list(range(first, len(rows_m))), list(range(bounds[gi], bounds[gi + 1]))))
+    R = len(rows_m)
+    src_rows = g.permutation(64)[:R]
+    src_cols = g.permutation(64)[:K]
+    a = np.zeros((R, K), dtype=np.complex128)
+    for rows, cols in groups:
+        a[np.ix_(rows, cols)] = u[np.ix_(src_rows[rows], src_cols[cols])]
+    return a, np.array(rows_m, dtype=np.int32), np.ones(K, dtype=np.int32), groups

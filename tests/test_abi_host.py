@@ -155,3 +155,49 @@ def test_no_gpu_fails_loudly(bslib):
     with pytest.raises(bslib.BsError) as e:
         bslib.Context(0)
     assert "BS_ENODEV" in str(e.value)
+
+
+def test_mixed_rule_sum_over_delta_matches_brute_force(bslib):
+    """The MIXED precision rule's sum over Delta vectors (a dynamic program
+    over Q = sum_k (M_k - 2 Delta_k)^2) against direct enumeration of every
+    Delta vector: one copy of a smallest-multiplicity row pinned (coefficient
+    M_p - 2D, weight C(M_p - 1, D)), every other row coefficient M_k - 2D with
+    weight C(M_k, D).  The prediction is that sum's log2 RSS plus the
+    rounding and drift terms, log2(K)/2 + max(0, log2L - 8)/2 - 21.02."""
+    import itertools
+    from math import comb, log2
+    g = np.random.default_rng(5)
+    for trial in range(40):
+        R = int(g.integers(1, 6))
+        M = g.integers(1, 5, size=R).astype(np.int32)
+        n = int(M.sum())
+        kind = int(g.integers(0, 2))
+        K = n + kind
+        order = sorted(range(R), key=lambda k: M[k])
+        p = order[0]
+        ranges = [range(M[k]) if k == p else range(M[k] + 1) for k in range(R)]
+        total = 0.0
+        for D in itertools.product(*ranges):
+            w, q = 1.0, 0
+            for k in range(R):
+                if k == p:
+                    w *= comb(int(M[k]) - 1, D[k]) ** 2
+                    q += (int(M[k]) - 2 * D[k]) ** 2
+                else:
+                    w *= comb(int(M[k]), D[k]) ** 2
+                    q += (int(M[k]) - 2 * D[k]) ** 2
+            total += w * (q / n) ** K
+        lrss = (1 - n) + 0.5 * log2(total)
+        got, l32, _ = bslib.debug_mixed_error(M, np.ones(K, np.int32), kind)
+        want = lrss + 0.5 * log2(K) + 0.5 * max(0, l32 - 8) - 21.02
+        assert abs(got - want) < 1e-4, (M.tolist(), kind, got, want)
+
+
+def test_mixed_rule_closed_form_for_distinct_rows(bslib):
+    """Distinct rows (every M = 1): every coefficient is +-1, Q = n for all
+    2^(n-1) addends, so RSS / prod ||a_j|| = 2^((1-n)/2) exactly."""
+    from math import log2
+    for n in (3, 10, 24, 30):
+        got, l32, _ = bslib.debug_mixed_error(np.ones(n, np.int32), np.ones(n, np.int32), 0)
+        want = (1 - n) / 2 + 0.5 * log2(n) + 0.5 * max(0, l32 - 8) - 21.02
+        assert abs(got - want) < 1e-4, (n, got, want)

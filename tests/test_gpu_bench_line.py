@@ -17,7 +17,7 @@ ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 
 def test_bench_line_has_the_contract_keys():
     cmd = [sys.executable, os.path.join(ROOT, "bench.py"), "--samples", "16", "--steps", "3", "--warmup", "3",
-           "--no-cpu-baseline", "--fp64-samples", "0"]
+           "--no-cpu-baseline", "--side-steps", "1"]
     r = subprocess.run(cmd, cwd=ROOT, capture_output=True, text=True, timeout=600)
     assert r.returncode == 0, r.stderr[-3000:]
     lines = [l for l in r.stdout.splitlines() if l.strip()]
@@ -28,7 +28,11 @@ def test_bench_line_has_the_contract_keys():
                 "gpu_launches", "clocks"):
         assert key in d, key
     assert d["unit"] == "samples/s" and d["n_gpus"] == 1 and d["steps"] == 3 and d["warmup"] == 3
-    assert d["dtype"] == "f32" and d["higher_is_better"] is True and d["scaling"] == "weak"
+    assert d["dtype"] == "f64" and d["higher_is_better"] is True and d["scaling"] == "weak"
+    assert d["config"]["mode"] == "fp64" and d["roofline"]["kernel"] == "walk_fp64_minors_kernel"
+    side = d["other_precision_form"]
+    assert side["mode"] == "mixed" and side["samples_per_s"] > 0 and 0 <= side["samples_equal_to_headline_run"] <= 1
+    assert d["latency_ms"]["max"] >= d["latency_ms"]["p50"] > 0
     assert d["config"]["workload"] == "cc_sampling_n30_m60" and d["config"]["samples_per_step"] == 16
     assert abs(d["value"] - 16 / (d["ms_per_step"] / 1000.0)) <= 1e-6 * d["value"]
     roof = d["roofline"]
