@@ -57,8 +57,17 @@ typedef struct {
  *   BS_MIXED: column sums and products in single precision (column sums
  *             re-seeded from the matrix every chunk, columns scaled by powers
  *             of two), addends summed in float-float runs, partial sums in
- *             double-double (Sec. 3.2 discusses the accuracy trade-off). */
-typedef enum { BS_FP64 = 0, BS_MIXED = 1 } bs_mode;
+ *             double-double (Sec. 3.2 discusses the accuracy trade-off), for
+ *             every job whose predicted FP32 error meets the MIXED tolerance
+ *             (bs_ctx_set_mixed_tolerance); other jobs run in FP64.
+ *   BS_DF64:  double-float: every quantity an unevaluated pair of floats
+ *             (about 48 significant bits) on the single-precision pipe --
+ *             column sums exact in fixed point (no drift), products by
+ *             FMA-based exact multiplication, compensated sums, partial sums
+ *             in double-double; results within the FP64 tolerance at several
+ *             times the FP64 kernels' speed on this part, whose FP64 rate is
+ *             1/64 of its FP32 rate. */
+typedef enum { BS_FP64 = 0, BS_MIXED = 1, BS_DF64 = 2 } bs_mode;
 
 typedef struct bs_ctx bs_ctx;
 
@@ -303,10 +312,10 @@ int bs_server_get_stats(bs_server* server, bs_server_stats* out);
 typedef struct {
     uint64_t walk_launches;     /* walk kernels launched */
     uint64_t kernel_launches;   /* all kernels this context launched */
-    uint64_t addends[2];        /* Gray-walk addends evaluated: [FP64 kernels, FP32 kernels] */
-    uint64_t addend_flops[2];   /* algorithmic flops of those addends */
-    double walk_ms[2];          /* summed walk-kernel time (profiling on) */
-    uint64_t timed_launches[2]; /* walk launches included in walk_ms */
+    uint64_t addends[3];        /* Gray-walk addends evaluated: [FP64, FP32, double-float kernels] */
+    uint64_t addend_flops[3];   /* algorithmic flops of those addends */
+    double walk_ms[3];          /* summed walk-kernel time (profiling on) */
+    uint64_t timed_launches[3]; /* walk launches included in walk_ms */
 } bs_stats;
 
 /* Sampling and batches replay their kernel sequence from a captured CUDA

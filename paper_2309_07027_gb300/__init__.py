@@ -21,11 +21,14 @@ import os
 
 import numpy as np
 
-__all__ = ["BS_FP64", "BS_MIXED", "BsError", "Context", "Server", "library_path", "load", "debug_gray_walk",
+__all__ = ["BS_FP64", "BS_MIXED", "BS_DF64", "BsError", "Context", "Server", "library_path", "load", "debug_gray_walk",
            "debug_plan", "perm_noalloc", "MAX_N"]
 
 BS_FP64 = 0
 BS_MIXED = 1
+BS_DF64 = 2  # double-float: FP64-class results on the FP32 pipe
+# statistics slots by kernel family: FP64, FP32, double-float
+PRECISIONS = ("fp64", "fp32", "df")
 # formulas of bs_perm_formula (bs_formula)
 FORMULAS = {"bbfg": 0, "ryser": 1, "nw": 2}
 MAX_N = 48
@@ -49,8 +52,8 @@ class BsError(RuntimeError):
 
 class _Stats(C.Structure):
     # index 0: FP64 walk kernels, index 1: FP32 walk kernels
-    _fields_ = [("walk_launches", C.c_uint64), ("kernel_launches", C.c_uint64), ("addends", C.c_uint64 * 2),
-                ("addend_flops", C.c_uint64 * 2), ("walk_ms", C.c_double * 2), ("timed_launches", C.c_uint64 * 2)]
+    _fields_ = [("walk_launches", C.c_uint64), ("kernel_launches", C.c_uint64), ("addends", C.c_uint64 * 3),
+                ("addend_flops", C.c_uint64 * 3), ("walk_ms", C.c_double * 3), ("timed_launches", C.c_uint64 * 3)]
 
 
 class _ServerStats(C.Structure):

@@ -15,7 +15,7 @@ INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(PKG, "_build")
 LIB = os.path.join(PKG, "libbs.so")
 
-SOURCES = ["kern_walk_fp64.cu", "kern_walk_fp32.cu", "kern_pack.cu", "kern_sample.cu", "kern_peaks.cu",
+SOURCES = ["kern_walk_fp64.cu", "kern_walk_fp32.cu", "kern_walk_df.cu", "kern_pack.cu", "kern_sample.cu", "kern_peaks.cu",
            "kern_noalloc.cu", "api.cpp", "plan.cpp", "serve.cpp"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-fvisibility=hidden",

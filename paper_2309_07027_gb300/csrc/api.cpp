@@ -52,16 +52,16 @@ struct DevBuf {
 
 // control block layout (unsigned long long slots)
 constexpr int kMaxGroups = 64;
-constexpr int kCtlStatus = kMaxGroups;       // int status word (in a 64-bit slot)
-constexpr int kCtlTotal = kMaxGroups + 1;    // sampler task totals [FP64, FP32]
-constexpr int kCtlCounter = kMaxGroups + 3;  // sampler work counters [FP64, FP32]
-constexpr int kCtlStats = kMaxGroups + 5;    // [addends64, flops64, addends32, flops32]
-constexpr int kCtlListLen = kMaxGroups + 9;  // two ints: sampler list lengths
-constexpr int kCtlSlots = kMaxGroups + 16;
+constexpr int kCtlStatus = kMaxGroups;                          // int status word (in a 64-bit slot)
+constexpr int kCtlTotal = kMaxGroups + 1;                       // sampler task totals, one per precision
+constexpr int kCtlCounter = kCtlTotal + BS_NPREC;                // sampler work counters, one per precision
+constexpr int kCtlStats = kCtlCounter + BS_NPREC;                // [addends, flops] per precision
+constexpr int kCtlListLen = kCtlStats + 2 * BS_NPREC;            // ints: sampler list lengths
+constexpr int kCtlSlots = kCtlListLen + 8;
 
 struct Timed {
     cudaEvent_t e0, e1;
-    int fp32;
+    int prec;  // BS_PREC_* of the timed walk
 };
 
 }  // namespace
@@ -93,7 +93,7 @@ struct bs_ctx {
     void* batch_out_lo = nullptr;
     std::vector<int64_t> single_last_key;  // key of the last single call (capture on a repeat)
     uint64_t batch_gen = 0;
-    uint64_t batch_walks = 0, batch_kernels = 0, batch_adds[2] = {0, 0}, batch_flops[2] = {0, 0};
+    uint64_t batch_walks = 0, batch_kernels = 0, batch_adds[BS_NPREC] = {}, batch_flops[BS_NPREC] = {};
     // bumped whenever the job/metadata buffers are rewritten or any buffer
     // is reallocated (a captured graph refers to them)
     uint64_t buf_gen = 1;
@@ -107,7 +107,7 @@ struct bs_ctx {
     size_t h_back_n = 0;
     cudaEvent_t stage_ev[2] = {nullptr, nullptr};
     double deadline_s = 0.0;
-    int log2max[2] = {12, 12};
+    int log2max[BS_NPREC] = {12, 12, 12};  // chunk-length caps, indexed by precision (= bs_mode)
     float mixed_log2_tol = BS_MIXED_LOG2_TOL_DEFAULT;  // MIXED precision rule threshold
     bool profiling = false;
     std::vector<Timed> timed;
@@ -193,8 +193,8 @@ void harvest_graph_timing(bs_ctx* c) {
     for (auto& t : c->cc_graph_timed) {
         float ms = 0.f;
         if (cudaEventElapsedTime(&ms, t.e0, t.e1) == cudaSuccess) {
-            c->stats.walk_ms[t.fp32] += ms;
-            c->stats.timed_launches[t.fp32]++;
+            c->stats.walk_ms[t.prec] += ms;
+            c->stats.timed_launches[t.prec]++;
             c->walk_log.push_back(ms);
         } else {
             cudaGetLastError();  // leave no stale error for the next launch check
@@ -239,7 +239,7 @@ int record_walk_start(bs_ctx* c, cudaEvent_t* e0) {
 }
 
 // Takes ownership of e0 (recorded by record_walk_start).
-int record_walk_end(bs_ctx* c, cudaEvent_t e0, bool fp32) {
+int record_walk_end(bs_ctx* c, cudaEvent_t e0, int prec) {
     if (!c->profiling || !e0) return BS_OK;
     cudaEvent_t e1;
     cudaError_t e = cudaEventCreate(&e1);
@@ -251,16 +251,18 @@ int record_walk_end(bs_ctx* c, cudaEvent_t e0, bool fp32) {
         cudaEventDestroy(e0);
         BS_CUDA(e);
     }
-    c->timed.push_back({e0, e1, fp32 ? 1 : 0});
+    c->timed.push_back({e0, e1, prec});
     return BS_OK;
 }
 
-int launch_walk(bs_ctx* c, const bs::WalkArgs& a, bool fp32, int kind) {
+int launch_walk(bs_ctx* c, const bs::WalkArgs& a, int prec, int kind) {
     cudaEvent_t e0;
     int rc = record_walk_start(c, &e0);
     if (rc) return rc;
     cudaError_t e;
-    if (fp32)
+    if (prec == BS_PREC_DF)
+        e = kind == BS_KIND_PERM ? bs::launch_walk_df_perm(a, c->stream) : bs::launch_walk_df_minors(a, c->stream);
+    else if (prec == BS_PREC_FP32)
         e = kind == BS_KIND_PERM ? bs::launch_walk_fp32_perm(a, c->stream) : bs::launch_walk_fp32_minors(a, c->stream);
     else
         e = kind == BS_KIND_PERM ? bs::launch_walk_fp64_perm(a, c->stream) : bs::launch_walk_fp64_minors(a, c->stream);
@@ -270,20 +272,38 @@ int launch_walk(bs_ctx* c, const bs::WalkArgs& a, bool fp32, int kind) {
     }
     c->stats.walk_launches++;
     c->stats.kernel_launches++;
-    return record_walk_end(c, e0, fp32);
+    return record_walk_end(c, e0, prec);
 }
+
+// The MIXED mode's kernels for jobs that fail the FP32 rule.
+constexpr int kMixedFallback = BS_MIXED_FALLBACK_PREC;
+
+// Precision of a job planned under `mode` (rule_fp32: the MIXED rule's
+// verdict).
+int job_prec(bs_mode mode, int rule_fp32) {
+    if (mode == BS_DF64) return BS_PREC_DF;
+    if (mode == BS_MIXED) return rule_fp32 ? BS_PREC_FP32 : kMixedFallback;
+    return BS_PREC_FP64;
+}
+
+// Data arena of a precision: FP32 jobs in complex floats (data32), FP64 and
+// DF jobs in 16-byte units (data64).
+inline int arena_of(int prec) { return prec == BS_PREC_FP32 ? 1 : 0; }
+
+bool valid_mode(bs_mode mode) { return mode == BS_FP64 || mode == BS_MIXED || mode == BS_DF64; }
 
 // A planned and uploaded set of jobs: what the device sequence needs.
 struct Prepared {
     struct Group {
         size_t first, last;
-        int fp32, kind, kmax;
+        int prec, kind, kmax;
         unsigned long long tasks;
     };
     std::vector<Group> groups;
-    size_t njobs = 0, n64 = 0;
+    size_t njobs = 0;
+    size_t pbeg[BS_NPREC + 1] = {};  // jobs [pbeg[p], pbeg[p + 1]) have precision p
     int max_cols = 1;
-    uint64_t adds[2] = {0, 0}, flops[2] = {0, 0};
+    uint64_t adds[BS_NPREC] = {}, flops[BS_NPREC] = {};
 };
 
 // Host half of a walk: plan every job (precision, chunking, groups of equal
@@ -292,7 +312,7 @@ struct Prepared {
 int plan_upload(bs_ctx* c, std::vector<JobIn>& ins, bs_mode mode, Prepared& P) {
     struct Row {
         JobIn in;
-        int fp32, kind, bucket, log2L, cpt, ncols;
+        int prec, kind, bucket, log2L, cpt, ncols;
         uint32_t ntasks;
     };
     std::vector<Row> rows;
@@ -301,19 +321,20 @@ int plan_upload(bs_ctx* c, std::vector<JobIn>& ins, bs_mode mode, Prepared& P) {
         if (in.p->trivial) continue;
         Row r;
         r.in = in;
-        r.fp32 = 0;
+        int rule = 0;
         if (mode == BS_MIXED) {
             // the rule needs the chunk length the FP32 kernel would use
-            const int cpt32 = bs_chunks_per_task(in.p->kind, 1, in.p->K);
-            const int l32 = bs_choose_log2L_single(in.p->C, cpt32, c->log2max[1], BS_TARGET_TASKS_SINGLE_FP32);
-            r.fp32 = bs_mixed_uses_fp32(in.p->radix, in.p->nrows, in.p->pinned_m, in.p->K, in.p->n, l32,
-                                        c->mixed_log2_tol, q_work.data());
+            const int cpt32 = bs_chunks_per_task(in.p->kind, BS_PREC_FP32, in.p->K);
+            const int l32 = bs_choose_log2L_single(in.p->C, cpt32, c->log2max[BS_PREC_FP32], BS_TARGET_TASKS_SINGLE_FP32);
+            rule = bs_mixed_uses_fp32(in.p->radix, in.p->nrows, in.p->pinned_m, in.p->K, in.p->n, l32,
+                                      c->mixed_log2_tol, q_work.data());
         }
+        r.prec = job_prec(mode, rule);
         r.kind = in.p->kind;
-        r.bucket = (in.p->K + 3) >> 2;
-        r.cpt = bs_chunks_per_task(r.kind, r.fp32, in.p->K);
-        r.log2L = bs_choose_log2L_single(in.p->C, r.cpt, c->log2max[r.fp32],
-                                         r.fp32 ? BS_TARGET_TASKS_SINGLE_FP32 : BS_TARGET_TASKS_SINGLE);
+        r.bucket = r.prec == BS_PREC_DF ? (in.p->K + 7) >> 3 : (in.p->K + 3) >> 2;
+        r.cpt = bs_chunks_per_task(r.kind, r.prec, in.p->K);
+        r.log2L = bs_choose_log2L_single(in.p->C, r.cpt, c->log2max[r.prec],
+                                         r.prec == BS_PREC_FP32 ? BS_TARGET_TASKS_SINGLE_FP32 : BS_TARGET_TASKS_SINGLE);
         uint64_t per = (uint64_t)r.cpt << r.log2L;
         r.ntasks = (uint32_t)((in.p->C + per - 1) / per);
         r.ncols = r.kind == BS_KIND_PERM ? 1 : in.p->K;
@@ -323,7 +344,7 @@ int plan_upload(bs_ctx* c, std::vector<JobIn>& ins, bs_mode mode, Prepared& P) {
     if (rows.empty()) return BS_OK;
     // groups of equal (precision, kind, bucket); largest jobs first inside
     std::stable_sort(rows.begin(), rows.end(), [](const Row& a, const Row& b) {
-        if (a.fp32 != b.fp32) return a.fp32 < b.fp32;
+        if (a.prec != b.prec) return a.prec < b.prec;
         if (a.kind != b.kind) return a.kind < b.kind;
         if (a.bucket != b.bucket) return a.bucket < b.bucket;
         return a.in.p->C > b.in.p->C;
@@ -331,7 +352,7 @@ int plan_upload(bs_ctx* c, std::vector<JobIn>& ins, bs_mode mode, Prepared& P) {
     std::vector<std::pair<size_t, size_t>> groups;
     for (size_t i = 0; i < rows.size();) {
         size_t j = i;
-        while (j < rows.size() && rows[j].fp32 == rows[i].fp32 && rows[j].kind == rows[i].kind &&
+        while (j < rows.size() && rows[j].prec == rows[i].prec && rows[j].kind == rows[i].kind &&
                rows[j].bucket == rows[i].bucket)
             ++j;
         groups.push_back({i, j});
@@ -361,9 +382,9 @@ int plan_upload(bs_ctx* c, std::vector<JobIn>& ins, bs_mode mode, Prepared& P) {
             jb.log2L = r.log2L;
             jb.out_index = r.in.out_index;
             jb.n = p.n;
-            jb.normalize = r.fp32;
-            jb.fp32 = r.fp32;
-            jb.data_off = data_off[r.fp32];
+            jb.normalize = r.prec != BS_PREC_FP64 ? 1 : 0;
+            jb.prec = r.prec;
+            jb.data_off = data_off[arena_of(r.prec)];
             jb.meta_off = (int64_t)meta.size();
             jb.partial_off = part_off;
             jb.src_off = r.in.src_off;
@@ -377,12 +398,12 @@ int plan_upload(bs_ctx* c, std::vector<JobIn>& ins, bs_mode mode, Prepared& P) {
             meta.push_back(p.pinned_src);
             meta.push_back(0);                                           // pad to 8 bytes
             meta.insert(meta.end(), (size_t)2 * (p.nrows + p.n), 0);     // binomial table (pack kernel)
-            data_off[r.fp32] += (int64_t)(1 + p.nrows) * BS_ROW_STRIDE(p.K);
+            data_off[arena_of(r.prec)] += (int64_t)(1 + p.nrows) * BS_ROW_STRIDE_P(p.K, r.prec);
             part_off += (int64_t)r.ntasks * r.ncols;
             tb += r.ntasks;
             max_cols = std::max(max_cols, r.ncols);
-            adds[r.fp32] += p.C;
-            flops[r.fp32] += p.C * (uint64_t)bs_flops_per_addend(p.K, r.kind);
+            adds[r.prec] += p.C;
+            flops[r.prec] += p.C * (uint64_t)bs_flops_per_addend(p.K, r.kind);
         }
     }
     const size_t jobs_b = jobs.size() * sizeof(bs_job), meta_b = meta.size() * sizeof(int);
@@ -402,13 +423,17 @@ int plan_upload(bs_ctx* c, std::vector<JobIn>& ins, bs_mode mode, Prepared& P) {
     BS_CUDA(cudaEventRecord(c->stage_ev[c->stage_cur], c->stream));
     c->buf_gen++;
     P.njobs = rows.size();
-    // FP64 jobs come first (sorted by precision), then FP32 jobs
-    while (P.n64 < rows.size() && !rows[P.n64].fp32) ++P.n64;
+    // jobs are sorted by precision: FP64, then FP32, then DF
+    for (int q = 0; q <= BS_NPREC; ++q) {
+        size_t at = 0;
+        while (at < rows.size() && rows[at].prec < q) ++at;
+        P.pbeg[q] = at;
+    }
     for (auto& g : groups) {
         Prepared::Group G;
         G.first = g.first;
         G.last = g.second;
-        G.fp32 = rows[g.first].fp32;
+        G.prec = rows[g.first].prec;
         G.kind = rows[g.first].kind;
         G.kmax = 0;
         G.tasks = 0;
@@ -430,11 +455,11 @@ int enqueue_device(bs_ctx* c, const Prepared& P, const double2* d_src, double2* 
     BS_CUDA(cudaMemsetAsync(c->ctl.p, 0, kCtlStats * 8, c->stream));
     BS_CUDA(cudaMemsetAsync(static_cast<unsigned long long*>(c->ctl.p) + kCtlListLen, 0, (kCtlSlots - kCtlListLen) * 8, c->stream));
     const bs_job* djobs = static_cast<const bs_job*>(c->jobs.p);
-    for (int prec = 0; prec < 2; ++prec) {
-        const size_t lo = prec ? P.n64 : 0, hi = prec ? P.njobs : P.n64;
+    for (int prec = 0; prec < BS_NPREC; ++prec) {
+        const size_t lo = P.pbeg[prec], hi = P.pbeg[prec + 1];
         if (hi == lo) continue;
         cudaError_t e = bs::launch_pack(djobs + lo, (int)(hi - lo), d_src, static_cast<int*>(c->meta.p),
-                                        prec ? c->data32.p : c->data64.p, prec, c->stream);
+                                        arena_of(prec) ? c->data32.p : c->data64.p, prec, c->stream);
         if (e != cudaSuccess) return fail(BS_ECUDA, "pack launch failed: %s", cudaGetErrorString(e));
         c->stats.kernel_launches++;
     }
@@ -445,7 +470,7 @@ int enqueue_device(bs_ctx* c, const Prepared& P, const double2* d_src, double2* 
         std::memset(&w, 0, sizeof(w));
         w.jobs = djobs + g.first;
         w.njobs = (int)(g.last - g.first);
-        w.data = g.fp32 ? c->data32.p : c->data64.p;
+        w.data = arena_of(g.prec) ? c->data32.p : c->data64.p;
         w.meta = static_cast<const int*>(c->meta.p);
         w.partials = static_cast<bs_zdd*>(c->partials.p);
         w.total_tasks = g.tasks;
@@ -453,7 +478,7 @@ int enqueue_device(bs_ctx* c, const Prepared& P, const double2* d_src, double2* 
         w.status = reinterpret_cast<int*>(ctl + kCtlStatus);
         w.deadline_rel_ns = c->deadline_s > 0 ? (unsigned long long)(c->deadline_s * 1e9) : 0ull;
         w.max_K = g.kmax;
-        if ((rc = launch_walk(c, w, g.fp32 != 0, g.kind))) return rc;
+        if ((rc = launch_walk(c, w, g.prec, g.kind))) return rc;
     }
     {
         cudaError_t e = bs::launch_reduce(djobs, (int)P.njobs, static_cast<const bs_zdd*>(c->partials.p),
@@ -470,7 +495,7 @@ int run_jobs(bs_ctx* c, std::vector<JobIn>& ins, const double2* d_src, bs_mode m
     int rc = plan_upload(c, ins, mode, P);
     if (rc || P.njobs == 0) return rc;
     if ((rc = enqueue_device(c, P, d_src, d_out, d_out_lo))) return rc;
-    for (int p = 0; p < 2; ++p) {
+    for (int p = 0; p < BS_NPREC; ++p) {
         c->stats.addends[p] += P.adds[p];
         c->stats.addend_flops[p] += P.flops[p];
     }
@@ -562,7 +587,7 @@ int batch_walk(bs_ctx* c, std::vector<IntPlan>& plans, const std::vector<int64_t
         BS_CUDA(cudaGraphLaunch(c->batch_exec, c->stream));
         c->stats.walk_launches += c->batch_walks;
         c->stats.kernel_launches += c->batch_kernels;
-        for (int p = 0; p < 2; ++p) {
+        for (int p = 0; p < BS_NPREC; ++p) {
             c->stats.addends[p] += c->batch_adds[p];
             c->stats.addend_flops[p] += c->batch_flops[p];
         }
@@ -600,13 +625,13 @@ int batch_walk(bs_ctx* c, std::vector<IntPlan>& plans, const std::vector<int64_t
         c->batch_out_lo = d_out_lo;
         c->batch_walks = c->stats.walk_launches - w0;
         c->batch_kernels = c->stats.kernel_launches - k0;
-        for (int p = 0; p < 2; ++p) {
+        for (int p = 0; p < BS_NPREC; ++p) {
             c->batch_adds[p] = P.adds[p];
             c->batch_flops[p] = P.flops[p];
         }
         BS_CUDA(cudaGraphLaunch(c->batch_exec, c->stream));
     }
-    for (int p = 0; p < 2; ++p) {
+    for (int p = 0; p < BS_NPREC; ++p) {
         c->stats.addends[p] += P.adds[p];
         c->stats.addend_flops[p] += P.flops[p];
     }
@@ -630,7 +655,8 @@ static std::vector<int64_t> plan_key(const bs_ctx* c, const IntPlan& p, int rows
     std::vector<int64_t> k = {-1, (int64_t)p.kind, (int64_t)p.formula, (int64_t)p.n, (int64_t)p.K,
                               (int64_t)p.nrows, (int64_t)p.nbin, (int64_t)p.C, (int64_t)p.trans,
                               (int64_t)p.pinned_src, (int64_t)rows, (int64_t)cols, (int64_t)mode,
-                              (int64_t)c->log2max[0], (int64_t)c->log2max[1], dl, tol_key(c)};
+                              (int64_t)c->log2max[0], (int64_t)c->log2max[1], (int64_t)c->log2max[2], dl,
+                              tol_key(c)};
     for (int j = 0; j < p.nrows; ++j) k.insert(k.end(), {(int64_t)p.radix[j], (int64_t)p.digit_src[j]});
     for (int j = 0; j < p.K; ++j) k.push_back(p.col_src[j]);
     return k;
@@ -675,22 +701,37 @@ int run_single(bs_ctx* c, const bs_c128* A, int rows, int cols, int ld, int kind
 int single_job(bs_ctx* c, const bs_c128* A, int rows, int cols, int ld, const int* M, const int* N, int kind,
                bs_mode mode, IntPlan& p, std::vector<double2>& hi, std::vector<double2>& lo) {
     if (!ok_ctx(c)) return BS_EINVAL;
-    if (mode != BS_FP64 && mode != BS_MIXED) return fail(BS_EINVAL, "unknown mode %d", (int)mode);
+    if (!valid_mode(mode)) return fail(BS_EINVAL, "unknown mode %d", (int)mode);
     int rc = plan_job(rows, cols, M, N, kind, p);
     if (rc) return rc;
     return run_single(c, A, rows, cols, ld, kind, mode, p, hi, lo);
 }
 
 // ------------------------------------------------------------------ sampler
-// Walk launches per sampler batch (steps 2..n; two kernels per step in MIXED).
-uint64_t kernels_walks(int n, bool mixed) { return n >= 2 ? (uint64_t)(n - 1) * (mixed ? 2 : 1) : 0; }
+// The walk kernels a sampler step launches under `mode`, in launch order:
+// MIXED runs the FP32 kernel and the fallback kernel, the others one each.
+int sampler_precs(bs_mode mode, int* precs) {
+    if (mode == BS_MIXED) {
+        precs[0] = BS_PREC_FP32;
+        precs[1] = kMixedFallback;
+        return 2;
+    }
+    precs[0] = mode == BS_DF64 ? BS_PREC_DF : BS_PREC_FP64;
+    return 1;
+}
+
+// Walk launches per sampler batch (steps 2..n).
+uint64_t kernels_walks(int n, bs_mode mode) {
+    int precs[2];
+    return n >= 2 ? (uint64_t)(n - 1) * sampler_precs(mode, precs) : 0;
+}
 
 // Enqueues one batch of the Clifford & Clifford loop on c->stream (eagerly or
 // into a stream capture): init, then for k = 1..n plan / scan / walk /
 // reduce (k >= 2) and draw, then the occupation counts.  Kernels read their
 // arguments from `da` (device); `a` gives launch shapes.  *kernels counts
 // the kernels enqueued.
-int enqueue_sampler_batch(bs_ctx* c, const bs::CcArgs& a, const bs::CcArgs* da, bool mixed, uint64_t* kernels) {
+int enqueue_sampler_batch(bs_ctx* c, const bs::CcArgs& a, const bs::CcArgs* da, bs_mode mode, uint64_t* kernels) {
     unsigned long long* ctl = static_cast<unsigned long long*>(c->ctl.p);
     int rc;
     cudaError_t e = bs::launch_cc_init(a, da, c->stream);
@@ -703,7 +744,10 @@ int enqueue_sampler_batch(bs_ctx* c, const bs::CcArgs& a, const bs::CcArgs* da, 
             if ((e = bs::launch_cc_scan(a, da, k, c->stream)) != cudaSuccess)
                 return fail(BS_ECUDA, "sampler scan: %s", cudaGetErrorString(e));
             *kernels += 2;
-            for (int prec = mixed ? 1 : 0; prec >= 0; --prec) {
+            int precs[2];
+            const int np = sampler_precs(mode, precs);
+            for (int pi = 0; pi < np; ++pi) {
+                const int prec = precs[pi];
                 bs::WalkArgs w;
                 std::memset(&w, 0, sizeof(w));
                 w.jobs = a.jobs;
@@ -719,7 +763,7 @@ int enqueue_sampler_batch(bs_ctx* c, const bs::CcArgs& a, const bs::CcArgs* da, 
                 w.status = reinterpret_cast<int*>(ctl + kCtlStatus);
                 w.deadline_rel_ns = c->deadline_s > 0 ? (unsigned long long)(c->deadline_s * 1e9) : 0ull;
                 w.max_K = k;
-                if ((rc = launch_walk(c, w, prec == 1, BS_KIND_MINORS))) return rc;
+                if ((rc = launch_walk(c, w, prec, BS_KIND_MINORS))) return rc;
                 c->stats.kernel_launches--;  // the caller counts every kernel
                 ++*kernels;
             }
@@ -758,17 +802,23 @@ int sample_dev(bs_ctx* c, const double2* dU, int m_rows, int m_cols, int ld, con
         BS_CUDA(cudaMemsetAsync(dout, 0, (size_t)n_samples * m_det * sizeof(int), c->stream));
         return BS_OK;
     }
-    const bool mixed = mode == BS_MIXED;
     // worst-case tasks of one chain at the last step (C <= 2^(n-2)), over
-    // both kernels a chain may be given
-    // (bs_choose_log2L gives at most 2 x target tasks unless the chunk
-    // length is capped, and then at most C / (cpt 2^log2max) + 1)
+    // the kernels a chain may be given (bs_choose_log2L gives at most
+    // 2 x target tasks unless the chunk length is capped, and then at most
+    // C / (cpt 2^log2max) + 1; cpt >= 16 for FP64 minors, 8 for FP32, 4 for DF)
     uint64_t cmax = n >= 2 ? (1ull << (n - 2)) : 1ull;
     uint64_t tasks_stride = 2 * BS_TARGET_TASKS_MANY + 1;
-    tasks_stride = std::max<uint64_t>(tasks_stride, cmax / (16ull << c->log2max[0]) + 2);
-    if (mixed) tasks_stride = std::max<uint64_t>(tasks_stride, cmax / (8ull << c->log2max[1]) + 2);
-    // a step-k job has <= k - 1 digit rows, K = k <= n columns, n' = k - 1
-    const int64_t meta_stride = BS_META_SIZE(n, n, n), data_stride = (int64_t)n * BS_ROW_STRIDE(n);
+    {
+        int precs[2];
+        const int np = sampler_precs(mode, precs);
+        for (int pi = 0; pi < np; ++pi) {
+            const uint64_t cpt_min = precs[pi] == BS_PREC_FP64 ? 16 : precs[pi] == BS_PREC_FP32 ? 8 : 4;
+            tasks_stride = std::max<uint64_t>(tasks_stride, cmax / (cpt_min << c->log2max[precs[pi]]) + 2);
+        }
+    }
+    // a step-k job has <= k - 1 digit rows, K = k <= n columns, n' = k - 1;
+    // a chain's data slot fits the widest row stride (DF: multiples of 8)
+    const int64_t meta_stride = BS_META_SIZE(n, n, n), data_stride = (int64_t)n * BS_ROW_STRIDE_DF(n);
     // chains per pass: bounded by the budget (or 2 GiB of partials per pass)
     const size_t per_chain = (size_t)tasks_stride * n * sizeof(bs_zdd) + (size_t)data_stride * 16 +
                              meta_stride * 4 + sizeof(bs_job) + (size_t)n * (8 + 16) + 8 + 64;
@@ -786,7 +836,7 @@ int sample_dev(bs_ctx* c, const double2* dU, int m_rows, int m_cols, int ld, con
     if ((rc = ensure(c, c->cc_jobs, (size_t)S0 * sizeof(bs_job)))) return rc;
     if ((rc = ensure(c, c->cc_meta, (size_t)S0 * meta_stride * sizeof(int)))) return rc;
     if ((rc = ensure(c, c->cc_data, (size_t)S0 * data_stride * 16))) return rc;
-    if ((rc = ensure(c, c->cc_lists, (size_t)S0 * 2 * sizeof(int)))) return rc;
+    if ((rc = ensure(c, c->cc_lists, (size_t)S0 * BS_NPREC * sizeof(int)))) return rc;
     if ((rc = ensure(c, c->cc_partials, (size_t)S0 * tasks_stride * n * sizeof(bs_zdd)))) return rc;
     if ((rc = ensure(c, c->cc_minors, (size_t)S0 * n * sizeof(double2)))) return rc;
     if ((rc = ensure(c, c->ctl, kCtlSlots * 8))) return rc;
@@ -831,10 +881,12 @@ int sample_dev(bs_ctx* c, const double2* dU, int m_rows, int m_cols, int ld, con
         a.meta_stride = meta_stride;
         a.data_stride = data_stride;
         a.tasks_stride = (int64_t)tasks_stride;
-        a.mixed = mixed ? 1 : 0;
-        a.log2max64 = c->log2max[0];
-        a.log2max32 = c->log2max[1];
+        a.mode = (int)mode;
+        a.log2max64 = c->log2max[BS_PREC_FP64];
+        a.log2max32 = c->log2max[BS_PREC_FP32];
+        a.log2maxdf = c->log2max[BS_PREC_DF];
         a.mixed_log2_tol = c->mixed_log2_tol;
+        a.mixed_fallback = kMixedFallback;
         // the kernels read the arguments from device memory (pageable copy:
         // staged before cudaMemcpyAsync returns, so `a` may go out of scope)
         BS_CUDA(cudaMemcpyAsync(da, &a, sizeof(a), cudaMemcpyHostToDevice, c->stream));
@@ -847,14 +899,15 @@ int sample_dev(bs_ctx* c, const double2* dU, int m_rows, int m_cols, int ld, con
         if (!c->use_graphs || c->stream == nullptr || c->stream == cudaStreamPerThread ||
             cap != cudaStreamCaptureStatusNone) {
             uint64_t kernels = 0;
-            if ((rc = enqueue_sampler_batch(c, a, da, mixed, &kernels))) return rc;
+            if ((rc = enqueue_sampler_batch(c, a, da, mode, &kernels))) return rc;
             c->stats.kernel_launches += kernels;
             continue;
         }
         // replay the captured step loop while shapes and buffers are unchanged
         const uint64_t dl = c->deadline_s > 0 ? (uint64_t)(c->deadline_s * 1e9) : 0;
         std::vector<uint64_t> key = {(uint64_t)a.S, (uint64_t)n, (uint64_t)m_rows, (uint64_t)m_det, (uint64_t)ld,
-                                     (uint64_t)a.mixed, (uint64_t)a.log2max64, (uint64_t)a.log2max32,
+                                     (uint64_t)a.mode, (uint64_t)a.log2max64, (uint64_t)a.log2max32,
+                                     (uint64_t)a.log2maxdf,
                                      (uint64_t)(uintptr_t)dU, (uint64_t)(uintptr_t)c->cc_cols.p,
                                      (uint64_t)(uintptr_t)c->cc_rows.p, (uint64_t)(uintptr_t)c->cc_jobs.p,
                                      (uint64_t)(uintptr_t)c->cc_meta.p, (uint64_t)(uintptr_t)c->cc_data.p,
@@ -877,7 +930,7 @@ int sample_dev(bs_ctx* c, const double2* dU, int m_rows, int m_cols, int ld, con
             BS_CUDA(cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal));
             uint64_t kernels = 0;
             const uint64_t walks_before = c->stats.walk_launches;
-            rc = enqueue_sampler_batch(c, a, da, mixed, &kernels);
+            rc = enqueue_sampler_batch(c, a, da, mode, &kernels);
             c->stats.walk_launches = walks_before;  // counted per replay below
             cudaGraph_t g = nullptr;
             cudaError_t e = cudaStreamEndCapture(c->stream, &g);
@@ -901,7 +954,7 @@ int sample_dev(bs_ctx* c, const double2* dU, int m_rows, int m_cols, int ld, con
         BS_CUDA(cudaGraphLaunch(c->cc_exec, c->stream));
         c->cc_timing_pending = !c->cc_graph_timed.empty();
         c->stats.kernel_launches += c->cc_graph_kernels;
-        c->stats.walk_launches += kernels_walks(n, mixed);
+        c->stats.walk_launches += kernels_walks(n, mode);
     }
     return BS_OK;
 }
@@ -1009,9 +1062,9 @@ int bs_ctx_set_deadline(bs_ctx* c, double seconds) {
 
 int bs_ctx_set_chunk_log2(bs_ctx* c, bs_mode mode, int log2_chunk_max) {
     if (!ok_ctx(c)) return BS_EINVAL;
-    if (mode != BS_FP64 && mode != BS_MIXED) return fail(BS_EINVAL, "unknown mode");
+    if (!valid_mode(mode)) return fail(BS_EINVAL, "unknown mode");
     if (log2_chunk_max < 4 || log2_chunk_max > 20) return fail(BS_EINVAL, "log2 chunk %d outside [4, 20]", log2_chunk_max);
-    c->log2max[mode == BS_MIXED ? 1 : 0] = log2_chunk_max;
+    c->log2max[mode] = log2_chunk_max;
     return BS_OK;
 }
 
@@ -1024,8 +1077,8 @@ int bs_ctx_set_mixed_tolerance(bs_ctx* c, double tol) {
 }
 
 int bs_ctx_get_chunk_log2(const bs_ctx* c, bs_mode mode) {
-    if (!c) return BS_EINVAL;
-    return c->log2max[mode == BS_MIXED ? 1 : 0];
+    if (!c || !valid_mode(mode)) return BS_EINVAL;
+    return c->log2max[mode];
 }
 
 int bs_perm(bs_ctx* c, const bs_c128* A, int rows, int cols, int ld, const int* row_mult, const int* col_mult,
@@ -1097,7 +1150,7 @@ static int batch_common(bs_ctx* c, int count, const bs_c128* A_packed, const int
                         const int64_t* col_mult_off, bs_mode mode, std::vector<IntPlan>& plans) {
     if (!ok_ctx(c)) return BS_EINVAL;
     if (count < 0) return fail(BS_EINVAL, "negative count");
-    if (mode != BS_FP64 && mode != BS_MIXED) return fail(BS_EINVAL, "unknown mode %d", (int)mode);
+    if (!valid_mode(mode)) return fail(BS_EINVAL, "unknown mode %d", (int)mode);
     if (count > 0 && (!a_offset || !rows || !cols || !mult_packed || !row_mult_off || !col_mult_off))
         return fail(BS_EINVAL, "NULL batch array");
     plans.resize(count);
@@ -1119,7 +1172,8 @@ static std::vector<int64_t> batch_key(const bs_ctx* c, int count, const int64_t*
     std::vector<int64_t> k;
     int64_t dl = 0;
     std::memcpy(&dl, &c->deadline_s, sizeof(dl));
-    k.insert(k.end(), {(int64_t)count, (int64_t)mode, (int64_t)c->log2max[0], (int64_t)c->log2max[1], dl, tol_key(c)});
+    k.insert(k.end(), {(int64_t)count, (int64_t)mode, (int64_t)c->log2max[0], (int64_t)c->log2max[1],
+                       (int64_t)c->log2max[2], dl, tol_key(c)});
     for (int b = 0; b < count; ++b) {
         k.insert(k.end(), {a_offset[b], (int64_t)rows[b], (int64_t)cols[b]});
         for (int r = 0; r < rows[b]; ++r) k.push_back(mult_packed[row_mult_off[b] + r]);
@@ -1204,7 +1258,7 @@ int bs_perm_batch_dev(bs_ctx* c, int count, const bs_c128* A_packed_dev, const i
 int bs_sample_dev(bs_ctx* c, const bs_c128* U_dev, int m_rows, int m_cols, int ld, const int* input_occupation,
                   int n_samples, uint64_t seed, int m_detected, bs_mode mode, int* out_dev) {
     if (!ok_ctx(c)) return BS_EINVAL;
-    if (mode != BS_FP64 && mode != BS_MIXED) return fail(BS_EINVAL, "unknown mode %d", (int)mode);
+    if (!valid_mode(mode)) return fail(BS_EINVAL, "unknown mode %d", (int)mode);
     if (!U_dev || (!out_dev && n_samples > 0)) return fail(BS_EINVAL, "NULL device pointer");
     std::lock_guard<std::mutex> lk(c->mu);
     BS_CUDA(cudaSetDevice(c->device));
@@ -1217,7 +1271,7 @@ int bs_sample_dev(bs_ctx* c, const bs_c128* U_dev, int m_rows, int m_cols, int l
 static int sample_host(bs_ctx* c, const bs_c128* U, int m_rows, int m_cols, int ld, const int* input_occupation,
                        int n_samples, uint64_t seed, int m_detected, bs_mode mode, int* out, int* rows_out) {
     if (!ok_ctx(c)) return BS_EINVAL;
-    if (mode != BS_FP64 && mode != BS_MIXED) return fail(BS_EINVAL, "unknown mode %d", (int)mode);
+    if (!valid_mode(mode)) return fail(BS_EINVAL, "unknown mode %d", (int)mode);
     if (!U || (!out && n_samples > 0)) return fail(BS_EINVAL, "NULL pointer");
     if (m_rows <= 0 || m_cols <= 0 || ld < m_cols) return fail(BS_EINVAL, "bad interferometer size");
     if (n_samples <= 0) return n_samples < 0 ? fail(BS_EINVAL, "negative sample count") : BS_OK;
@@ -1289,8 +1343,8 @@ static void collect_timed(bs_ctx* c) {
     for (auto& t : c->timed) {
         float ms = 0.f;
         if (cudaEventElapsedTime(&ms, t.e0, t.e1) == cudaSuccess) {
-            c->stats.walk_ms[t.fp32] += ms;
-            c->stats.timed_launches[t.fp32]++;
+            c->stats.walk_ms[t.prec] += ms;
+            c->stats.timed_launches[t.prec]++;
             c->walk_log.push_back(ms);
         } else {
             cudaGetLastError();
@@ -1322,7 +1376,7 @@ int bs_ctx_get_stats(bs_ctx* c, bs_stats* out) {
     if (e != cudaSuccess) return fail(BS_ECUDA, "stream synchronize: %s", cudaGetErrorString(e));
     collect_timed(c);
     *out = c->stats;
-    for (int p = 0; p < 2; ++p) {
+    for (int p = 0; p < BS_NPREC; ++p) {
         out->addends[p] += read_device_stat(c, 2 * p);
         out->addend_flops[p] += read_device_stat(c, 2 * p + 1);
     }
@@ -1342,7 +1396,7 @@ int bs_ctx_reset_stats(bs_ctx* c) {
     c->cc_timing_pending = false;
     c->walk_log.clear();
     c->stats = bs_stats();
-    if (c->ctl.p) cudaMemset(static_cast<unsigned long long*>(c->ctl.p) + kCtlStats, 0, 32);
+    if (c->ctl.p) cudaMemset(static_cast<unsigned long long*>(c->ctl.p) + kCtlStats, 0, 2 * BS_NPREC * 8);
     return BS_OK;
 }
 
@@ -1356,7 +1410,7 @@ int bs_measure_fma_rates(bs_ctx* c, double* fp64, double* fp32) {
 
 int bs_tune(bs_ctx* c, bs_mode mode, int kind, int K, int* best_log2, double* best_addends_per_s) {
     if (!ok_ctx(c)) return BS_EINVAL;
-    if (mode != BS_FP64 && mode != BS_MIXED) return fail(BS_EINVAL, "unknown mode %d", (int)mode);
+    if (!valid_mode(mode)) return fail(BS_EINVAL, "unknown mode %d", (int)mode);
     if (kind != 0 && kind != 1) return fail(BS_EINVAL, "kind must be 0 (permanent) or 1 (minors)");
     if (K < 4 || K > BS_MAX_COLS) return fail(BS_EINVAL, "K must be in [4, %d]", BS_MAX_COLS);
     // synthetic problem: K product columns, up to 25 distinct rows (at most
@@ -1373,14 +1427,14 @@ int bs_tune(bs_ctx* c, bs_mode mode, int kind, int K, int* best_log2, double* be
     }
     std::vector<int> M(R, 1), N(K, 1);
     for (int extra = n - R, r = 0; extra > 0; --extra, ++r) M[r % R] += 1;
-    const int saved = c->log2max[mode == BS_MIXED ? 1 : 0];
+    const int saved = c->log2max[mode];
     const bool prof = c->profiling;
     c->profiling = true;
     double best_ms = 1e300;
     int best = saved;
     uint64_t C = 0;
     for (int cand = 8; cand <= 14; cand += 2) {
-        c->log2max[mode == BS_MIXED ? 1 : 0] = cand;
+        c->log2max[mode] = cand;
         IntPlan p;
         std::vector<double2> hi, lo;
         double ms = 1e300;
@@ -1389,7 +1443,7 @@ int bs_tune(bs_ctx* c, bs_mode mode, int kind, int K, int* best_log2, double* be
             int rc = single_job(c, A.data(), R, K, K, M.data(), N.data(), kind == 0 ? BS_KIND_PERM : BS_KIND_MINORS,
                                 mode, p, hi, lo);
             if (rc) {
-                c->log2max[mode == BS_MIXED ? 1 : 0] = saved;
+                c->log2max[mode] = saved;
                 c->profiling = prof;
                 return rc;
             }
@@ -1410,7 +1464,7 @@ int bs_tune(bs_ctx* c, bs_mode mode, int kind, int K, int* best_log2, double* be
             best = cand;
         }
     }
-    c->log2max[mode == BS_MIXED ? 1 : 0] = best;
+    c->log2max[mode] = best;
     c->profiling = prof;
     if (best_log2) *best_log2 = best;
     if (best_addends_per_s) *best_addends_per_s = (double)C / (best_ms * 1e-3);

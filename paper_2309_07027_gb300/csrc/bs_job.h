@@ -40,7 +40,7 @@ struct bs_job {
     int32_t out_index;     // perm: output slot; minors: first of K output slots
     int32_t n;             // photons of the formula (prefactor 2^(1-n))
     int32_t normalize;     // 1: scale each column by a power of two (FP32 range)
-    int32_t fp32;          // 1: walked by the FP32 kernels, 0: by the FP64 kernels
+    int32_t prec;          // BS_PREC_*: which kernels walk the job
     int64_t data_off;      // complex elements: c0[KP] then 2a[nrows][KP], KP = BS_ROW_STRIDE(K)
     int64_t meta_off;      // ints, see BS_META_* below
     int64_t partial_off;   // double-double complex slots: ntasks * (perm ? 1 : K)
@@ -84,6 +84,19 @@ struct bs_job {
 // leaves every product unchanged (FP64 jobs keep c0 = 0 there and test
 // columns against K instead).
 #define BS_ROW_STRIDE(K) ((((K) + 3) / 4) * 4)
+// Double-float jobs: K rounded up to a multiple of 8 (the DF bucket width).
+#define BS_ROW_STRIDE_DF(K) ((((K) + 7) / 8) * 8)
+#define BS_ROW_STRIDE_P(K, prec) ((prec) == BS_PREC_DF ? BS_ROW_STRIDE_DF(K) : BS_ROW_STRIDE(K))
+
+// Precision of a job: the kernel family that walks it.
+//   FP64: double column sums, products and runs (data in complex doubles);
+//   FP32: single-precision packed pairs (data in complex floats);
+//   DF:   double-float (float pairs, exact fixed-point column sums; data in
+//         16-byte units like FP64).
+#define BS_PREC_FP64 0
+#define BS_PREC_FP32 1
+#define BS_PREC_DF 2
+#define BS_NPREC 3
 
 // Double-double complex partial: re = (re_hi, re_lo), im = (im_hi, im_lo).
 struct bs_zdd {

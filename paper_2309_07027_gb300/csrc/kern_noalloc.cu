@@ -51,7 +51,7 @@ constexpr size_t kMeta = 512;                                     // <= BS_META_
 constexpr size_t kOut = 2304;                                     // result hi / lo (2 x 16 bytes)
 constexpr size_t kSrc = 2560;                                     // compacted matrix, <= 48 x 48
 constexpr size_t kData = kSrc + (size_t)BS_MAX_N * BS_MAX_N * 16;  // packed c0 / 2a
-constexpr size_t kPart = kData + (size_t)(1 + BS_MAX_N) * BS_ROW_STRIDE(BS_MAX_N) * 16;
+constexpr size_t kPart = kData + (size_t)(1 + BS_MAX_N) * BS_ROW_STRIDE_DF(BS_MAX_N) * 16;
 constexpr size_t kPartSlots = (BS_NOALLOC_SCRATCH_BYTES - kPart) / sizeof(bs_zdd);
 static_assert(kPart % 256 == 0 && kData % 256 == 0, "scratch regions must stay aligned");
 static_assert(kMeta + BS_META_SIZE(BS_MAX_DIGITS, BS_MAX_COLS, BS_MAX_N) * 4 <= kOut, "metadata region too small");
@@ -88,7 +88,7 @@ int scratch_address(int dev, unsigned char** out) {
 extern "C" int bs_perm_noalloc(const bs_c128* A, int rows, int cols, int ld, const int* row_mult,
                                const int* col_mult, bs_mode mode, void* stream, bs_c128* out, bs_c128* out_lo) {
     if (!out) return bs::fail(BS_EINVAL, "out is NULL");
-    if (mode != BS_FP64 && mode != BS_MIXED) return bs::fail(BS_EINVAL, "unknown mode %d", (int)mode);
+    if (mode != BS_FP64 && mode != BS_MIXED && mode != BS_DF64) return bs::fail(BS_EINVAL, "unknown mode %d", (int)mode);
     if (rows < 0 || cols < 0) return bs::fail(BS_EINVAL, "negative matrix size %d x %d", rows, cols);
     if ((rows > 0 && !row_mult) || (cols > 0 && !col_mult)) return bs::fail(BS_EINVAL, "multiplicity array is NULL");
     // compact away zero multiplicities (at most BS_MAX_N rows / columns remain)
@@ -119,16 +119,18 @@ extern "C" int bs_perm_noalloc(const bs_c128* A, int rows, int cols, int ld, con
     }
     if (!A) return bs::fail(BS_EINVAL, "matrix pointer is NULL");
     if (ld < cols) return bs::fail(BS_EINVAL, "leading dimension %d < columns %d", ld, cols);
-    int fp32 = 0;
+    int prec = mode == BS_DF64 ? BS_PREC_DF : BS_PREC_FP64;
     if (mode == BS_MIXED) {
         double q_work[BS_MIXED_QMAX + 1];  // the rule's scratch, on the stack
-        const int l32 = bs_choose_log2L_single(p.C, bs_chunks_per_task(BS_KIND_PERM, 1, p.K), 12,
+        const int l32 = bs_choose_log2L_single(p.C, bs_chunks_per_task(BS_KIND_PERM, BS_PREC_FP32, p.K), 12,
                                                BS_TARGET_TASKS_SINGLE_FP32);
-        fp32 = bs_mixed_uses_fp32(p.radix, p.nrows, p.pinned_m, p.K, p.n, l32, BS_MIXED_LOG2_TOL_DEFAULT, q_work);
+        prec = bs_mixed_uses_fp32(p.radix, p.nrows, p.pinned_m, p.K, p.n, l32, BS_MIXED_LOG2_TOL_DEFAULT, q_work)
+                   ? BS_PREC_FP32
+                   : BS_MIXED_FALLBACK_PREC;
     }
-    const int cpt = bs_chunks_per_task(BS_KIND_PERM, fp32, p.K);
+    const int cpt = bs_chunks_per_task(BS_KIND_PERM, prec, p.K);
     const int log2L = bs_choose_log2L_single(p.C, cpt, 12,
-                                             fp32 ? BS_TARGET_TASKS_SINGLE_FP32 : BS_TARGET_TASKS_SINGLE);
+                                             prec == BS_PREC_FP32 ? BS_TARGET_TASKS_SINGLE_FP32 : BS_TARGET_TASKS_SINGLE);
     const uint64_t per = (uint64_t)cpt << log2L;
     const uint64_t ntasks = (p.C + per - 1) / per;
     if (ntasks > kPartSlots)
@@ -151,8 +153,8 @@ extern "C" int bs_perm_noalloc(const bs_c128* A, int rows, int cols, int ld, con
     jb.kind = BS_KIND_PERM;
     jb.log2L = log2L;
     jb.n = p.n;
-    jb.normalize = fp32;
-    jb.fp32 = fp32;
+    jb.normalize = prec != BS_PREC_FP64 ? 1 : 0;
+    jb.prec = prec;
     jb.src_ld = nc;
     jb.src_trans = p.trans ? 1 : 0;
     int meta[BS_META_SIZE(BS_MAX_DIGITS, BS_MAX_COLS, BS_MAX_N)];
@@ -175,7 +177,7 @@ extern "C" int bs_perm_noalloc(const bs_c128* A, int rows, int cols, int ld, con
     NA_CUDA(cudaMemcpyAsync(scr + kSrc, Ac, (size_t)nr * nc * sizeof(bs_c128), cudaMemcpyHostToDevice, s));
     const bs_job* djob = reinterpret_cast<const bs_job*>(scr + kJob);
     int* dmeta = reinterpret_cast<int*>(scr + kMeta);
-    NA_CUDA(bs::launch_pack(djob, 1, reinterpret_cast<const double2*>(scr + kSrc), dmeta, scr + kData, fp32, s));
+    NA_CUDA(bs::launch_pack(djob, 1, reinterpret_cast<const double2*>(scr + kSrc), dmeta, scr + kData, prec, s));
     bs::WalkArgs w;
     std::memset(&w, 0, sizeof(w));
     w.jobs = djob;
@@ -187,7 +189,9 @@ extern "C" int bs_perm_noalloc(const bs_c128* A, int rows, int cols, int ld, con
     w.counter = reinterpret_cast<unsigned long long*>(scr + kCtl);
     w.status = reinterpret_cast<int*>(scr + kCtl + 8);
     w.max_K = p.K;
-    NA_CUDA(fp32 ? bs::launch_walk_fp32_perm(w, s) : bs::launch_walk_fp64_perm(w, s));
+    NA_CUDA(prec == BS_PREC_DF     ? bs::launch_walk_df_perm(w, s)
+            : prec == BS_PREC_FP32 ? bs::launch_walk_fp32_perm(w, s)
+                                   : bs::launch_walk_fp64_perm(w, s));
     NA_CUDA(bs::launch_reduce(djob, 1, w.partials, dmeta, reinterpret_cast<double2*>(scr + kOut),
                               reinterpret_cast<double2*>(scr + kOut + 16), 1, s));
     double2 res[2];

@@ -20,15 +20,15 @@
 namespace bs {
 
 __global__ void pack_kernel(const bs_job* __restrict__ jobs, const double2* __restrict__ src, int* __restrict__ meta,
-                            void* __restrict__ data, int fp32) {
+                            void* __restrict__ data, int prec) {
     const bs_job jb = jobs[blockIdx.x];
-    pack_job(jb, src, meta, data, fp32, threadIdx.x, blockDim.x);
+    pack_job(jb, src, meta, data, prec, threadIdx.x, blockDim.x);
 }
 
-cudaError_t launch_pack(const bs_job* jobs, int njobs, const double2* src, int* meta, void* data, int fp32,
+cudaError_t launch_pack(const bs_job* jobs, int njobs, const double2* src, int* meta, void* data, int prec,
                         cudaStream_t s) {
     if (njobs <= 0) return cudaSuccess;
-    pack_kernel<<<njobs, 64, 0, s>>>(jobs, src, meta, data, fp32);
+    pack_kernel<<<njobs, 64, 0, s>>>(jobs, src, meta, data, prec);
     return cudaGetLastError();
 }
 

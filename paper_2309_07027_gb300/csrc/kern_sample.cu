@@ -157,20 +157,23 @@ __global__ void cc_plan_kernel(const CcArgs* __restrict__ pa, int k) {
         jb.nbin = nbin;
         uint64_t C = 1;
         for (int j = 0; j < nrows; ++j) C *= (uint64_t)drad[j];
-        int fp32 = 0;
-        if (a.mixed) {
-            // decided with the chunk length the FP32 kernel would use
-            const int l32 = bs_choose_log2L(C, bs_chunks_per_task(BS_KIND_MINORS, 1, k), BS_LOG2L_MIN_MANY,
+        int prec = a.mode == 2 ? BS_PREC_DF : BS_PREC_FP64;
+        if (a.mode == 1) {
+            // MIXED: decided with the chunk length the FP32 kernel would use
+            const int l32 = bs_choose_log2L(C, bs_chunks_per_task(BS_KIND_MINORS, BS_PREC_FP32, k), BS_LOG2L_MIN_MANY,
                                             a.log2max32, BS_TARGET_TASKS_MANY);
-            fp32 = bs_mixed_uses_fp32(drad, nrows, ucnt[p], k, k - 1, l32, a.mixed_log2_tol, q_work);
+            prec = bs_mixed_uses_fp32(drad, nrows, ucnt[p], k, k - 1, l32, a.mixed_log2_tol, q_work)
+                       ? BS_PREC_FP32
+                       : a.mixed_fallback;
         }
-        jb.fp32 = fp32;
-        jb.normalize = fp32;
+        jb.prec = prec;
+        jb.normalize = prec != BS_PREC_FP64 ? 1 : 0;
         // the chain's data slot holds data_stride complex doubles; an FP32
-        // job indexes it in complex floats (twice as many, same bytes)
-        jb.data_off = (int64_t)s * a.data_stride * (fp32 ? 2 : 1);
-        const int cpt = bs_chunks_per_task(BS_KIND_MINORS, fp32, k);
-        const int log2max = fp32 ? a.log2max32 : a.log2max64;
+        // job indexes it in complex floats (twice as many, same bytes), a DF
+        // job in 16-byte units
+        jb.data_off = (int64_t)s * a.data_stride * (prec == BS_PREC_FP32 ? 2 : 1);
+        const int cpt = bs_chunks_per_task(BS_KIND_MINORS, prec, k);
+        const int log2max = prec == BS_PREC_FP32 ? a.log2max32 : prec == BS_PREC_DF ? a.log2maxdf : a.log2max64;
         for (int j = 0; j < nrows; ++j) {
             meta[j] = drad[j];
             meta[nrows + j] = dsrc[j];
@@ -185,7 +188,7 @@ __global__ void cc_plan_kernel(const CcArgs* __restrict__ pa, int k) {
         sjb = jb;
     }
     __syncthreads();
-    pack_job(sjb, a.U, a.meta, a.data, sjb.fp32, threadIdx.x, blockDim.x);
+    pack_job(sjb, a.U, a.meta, a.data, sjb.prec, threadIdx.x, blockDim.x);
 }
 
 // Inclusive block scan of 64-bit values (Hillis-Steele, blockDim <= 1024).
@@ -203,7 +206,7 @@ __device__ unsigned long long block_scan(unsigned long long v, unsigned long lon
     return r;
 }
 
-// One CTA: for each precision p (0 = FP64, 1 = FP32) the compacted list of
+// One CTA: for each precision p (BS_PREC_*) the compacted list of
 // chains walked by that kernel, their task offsets (exclusive scan of ntasks
 // in list order), the task total, a zeroed work counter, and the addend /
 // flop counters used for the roofline.
@@ -211,7 +214,7 @@ __global__ void cc_scan_kernel(const CcArgs* __restrict__ pa, int k) {
     const CcArgs& a = *pa;
     __shared__ unsigned long long buf[1024];
     __shared__ unsigned long long carry_t, carry_n, adds;
-    for (int p = 0; p < 2; ++p) {
+    for (int p = 0; p < BS_NPREC; ++p) {
         if (threadIdx.x == 0) {
             carry_t = 0;
             carry_n = 0;
@@ -220,7 +223,7 @@ __global__ void cc_scan_kernel(const CcArgs* __restrict__ pa, int k) {
         __syncthreads();
         for (int base = 0; base < a.S; base += blockDim.x) {
             const int s = base + threadIdx.x;
-            const bool mine = s < a.S && a.jobs[s].fp32 == p;
+            const bool mine = s < a.S && a.jobs[s].prec == p;
             const unsigned long long nt = mine ? a.jobs[s].ntasks : 0ull;
             if (mine) atomicAdd(&adds, (unsigned long long)a.jobs[s].C);
             const unsigned long long pos = block_scan(mine ? 1ull : 0ull, buf);

@@ -28,10 +28,14 @@ cudaError_t launch_walk_fp64_perm(const WalkArgs& a, cudaStream_t s);
 cudaError_t launch_walk_fp64_minors(const WalkArgs& a, cudaStream_t s);
 cudaError_t launch_walk_fp32_perm(const WalkArgs& a, cudaStream_t s);
 cudaError_t launch_walk_fp32_minors(const WalkArgs& a, cudaStream_t s);
+// Double-float kernels: 8-column buckets (max_K selects (K + 7) / 8).
+cudaError_t launch_walk_df_perm(const WalkArgs& a, cudaStream_t s);
+cudaError_t launch_walk_df_minors(const WalkArgs& a, cudaStream_t s);
 
 // Builds c0 / 2a (and column scales) of every job from its source matrix.
-// fp32 != 0 writes the float arena, else the double arena.
-cudaError_t launch_pack(const bs_job* jobs, int njobs, const double2* src, int* meta, void* data, int fp32,
+// prec (BS_PREC_*) selects the layout: complex doubles (FP64), packed float
+// pairs (FP32, the float arena) or double-float pairs (DF, 16-byte units).
+cudaError_t launch_pack(const bs_job* jobs, int njobs, const double2* src, int* meta, void* data, int prec,
                         cudaStream_t s);
 
 // Sums each job's task partials in a fixed order and applies 2^(1-n) and the

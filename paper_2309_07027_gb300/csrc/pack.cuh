@@ -8,6 +8,12 @@
 // factor) and 0 in FP64 jobs.  With normalize set, column col
 // is scaled by 2^-e (e: smallest integer with sum_rows M_row (|Re a| + |Im a|)
 // <= 2^e) and e is stored in colexp[col] for the reduce kernel.
+// Double-float (DF) jobs: rows of stride BS_ROW_STRIDE_DF(K) (a multiple of
+// 8), column col scaled by 2^(2 - e) (colexp = e - 2) so that every column
+// sum has |Re|, |Im| <= 4, and every entry quantised to a high part on the
+// grid 2^-20 and a low part on the grid 2^-44, both exact floats
+// (walk_df.cuh); pair p of a row is {re h, re h, im h, im h} of columns
+// (2p, 2p+1), then the same for the low parts; pad columns have c0 = 1.
 #pragma once
 #include <cuda_runtime.h>
 #include "bs_job.h"
@@ -27,8 +33,29 @@ __device__ __forceinline__ void put_f32(void* data, const bs_job& jb, int KP, in
     q[2] = im;
 }
 
+// The DF split of v (|v| < 16): hi = v rounded to the grid 2^-20, lo = the
+// rest rounded to the grid 2^-44; vlo: a low-order double added to v
+// (double-double input), 0 otherwise.
+__device__ __forceinline__ float2 df_quantise(double v, double vlo) {
+    const double hi = rint(v * 0x1p20) * 0x1p-20;
+    const double rest = (v - hi) + vlo;  // v - hi is exact
+    const double lo = rint(rest * 0x1p44) * 0x1p-44;
+    return make_float2((float)hi, (float)lo);
+}
+
+// Element (row r, column col) of a DF job's packed rows.
+__device__ __forceinline__ void put_df(void* data, const bs_job& jb, int KP, int r, int col, float2 re, float2 im) {
+    float* q = static_cast<float*>(data) + 4 * (jb.data_off + (int64_t)r * KP) + 8 * (col >> 1) + (col & 1);
+    q[0] = re.x;
+    q[2] = im.x;
+    q[4] = re.y;
+    q[6] = im.y;
+}
+
 __device__ __forceinline__ void pack_job(const bs_job& jb, const double2* __restrict__ src, int* __restrict__ meta,
-                         void* __restrict__ data, int fp32, int tid, int nthreads) {
+                         void* __restrict__ data, int prec, int tid, int nthreads) {
+    const int fp32 = prec == BS_PREC_FP32;
+    const int df = prec == BS_PREC_DF;
     const int* radix = meta + BS_META_RADIX(jb);
     const int* dsrc = meta + BS_META_DIGIT_SRC(jb);
     const int* csrc = meta + BS_META_COL_SRC(jb);
@@ -41,7 +68,7 @@ __device__ __forceinline__ void pack_job(const bs_job& jb, const double2* __rest
         for (int j = 0; j < jb.nrows; ++j)
             for (int d = 0; d < radix[j]; ++d) binom[at++] = bs_binom(radix[j] - 1, d);
     }
-    const int KP = BS_ROW_STRIDE(jb.K);
+    const int KP = df ? BS_ROW_STRIDE_DF(jb.K) : BS_ROW_STRIDE(jb.K);
     if (jb.formula != BS_JOB_BBFG) {
         // Ryser / Nijenhuis-Wilf (FP64): product column col is matrix row
         // sc; digit j is matrix column dsrc[j], added with +1 when it enters
@@ -77,7 +104,10 @@ __device__ __forceinline__ void pack_job(const bs_job& jb, const double2* __rest
     }
     for (int col = tid; col < KP; col += nthreads) {
         if (col >= jb.K) {  // pad column
-            if (fp32) {
+            if (df) {
+                put_df(data, jb, KP, 0, col, make_float2(1.f, 0.f), make_float2(0.f, 0.f));
+                for (int j = 1; j <= jb.nrows; ++j) put_df(data, jb, KP, j, col, make_float2(0.f, 0.f), make_float2(0.f, 0.f));
+            } else if (fp32) {
                 put_f32(data, jb, KP, 0, col, 1.f, 0.f);
                 for (int j = 1; j <= jb.nrows; ++j) put_f32(data, jb, KP, j, col, 0.f, 0.f);
             } else {
@@ -96,6 +126,7 @@ __device__ __forceinline__ void pack_job(const bs_job& jb, const double2* __rest
                 b += (double)(radix[j] - 1) * (fabs(d.x) + fabs(d.y));
             }
             if (b > 0.0) (void)frexp(b, &e);  // b = f 2^e, f in [0.5, 1)
+            if (df) e -= 2;                   // DF: column sums up to 4 (walk_df.cuh)
         }
         colexp[col] = e;
         // c0 in double-double (each product split exactly with an FMA), rounded
@@ -110,7 +141,14 @@ __device__ __forceinline__ void pack_job(const bs_job& jb, const double2* __rest
             sre = dd_add_d(dd_add_d(sre, pre), ere);
             sim = dd_add_d(dd_add_d(sim, pim), eim);
         }
-        if (fp32) {
+        if (df) {
+            put_df(data, jb, KP, 0, col, df_quantise(sre.hi, sre.lo), df_quantise(sim.hi, sim.lo));
+            for (int j = 0; j < jb.nrows; ++j) {
+                double2 d = src_elem(src, jb, dsrc[j], sc);
+                put_df(data, jb, KP, 1 + j, col, df_quantise(ldexp(d.x, 1 - e), 0.0),
+                       df_quantise(ldexp(d.y, 1 - e), 0.0));
+            }
+        } else if (fp32) {
             put_f32(data, jb, KP, 0, col, (float)sre.hi, (float)sim.hi);
             for (int j = 0; j < jb.nrows; ++j) {
                 double2 d = src_elem(src, jb, dsrc[j], sc);

@@ -70,9 +70,16 @@ BS_HD int bs_choose_log2L_single(uint64_t C, int cpt, int log2max, int target) {
 // the permanent kernels give each lane its own chunk (32 per task).
 #define BS_MINORS_FP32_GROUP_KB(KB) (((KB) == 24 || (KB) == 48) ? 4 : 2)
 BS_HD int bs_minors_fp32_group(int K) { return BS_MINORS_FP32_GROUP_KB((K + 3) & ~3); }
-BS_HD int bs_chunks_per_task(int kind, int fp32, int K) {
+// Lanes per chunk of the double-float kernels (permanent and minors), by
+// 8-column bucket width KB: each lane owns KB / (2G) column pairs
+// (8 -> 1 x 4, 16 -> 2 x 4, 24 -> 4 x 3, 32 -> 4 x 4, 40 -> 4 x 5,
+// 48 -> 8 x 3), so a lane's double-float state fits its registers.
+#define BS_DF_GROUP_KB(KB) ((KB) <= 8 ? 1 : (KB) <= 16 ? 2 : (KB) <= 40 ? 4 : 8)
+BS_HD int bs_df_group(int K) { return BS_DF_GROUP_KB((K + 7) & ~7); }
+BS_HD int bs_chunks_per_task(int kind, int prec, int K) {
+    if (prec == BS_PREC_DF) return 32 / bs_df_group(K);
     if (kind != BS_KIND_MINORS) return 32;
-    return fp32 ? 32 / bs_minors_fp32_group(K) : 16;  // FP64 minors: lane pairs
+    return prec == BS_PREC_FP32 ? 32 / bs_minors_fp32_group(K) : 16;  // FP64 minors: lane pairs
 }
 
 // Algorithmic flops of one addend (the roofline numerator):
@@ -110,6 +117,8 @@ BS_HD int64_t bs_flops_per_addend(int K, int kind) {
 // The model assumes unstructured inputs; matrices with many exact zeros
 // (block structure) cancel far more than it predicts and belong in FP64.
 #define BS_MIXED_LOG2_TOL_DEFAULT (-19.93f)  // log2(1e-6)
+// Kernels of the MIXED jobs that fail the FP32 rule.
+#define BS_MIXED_FALLBACK_PREC BS_PREC_FP64
 #define BS_MIXED_QMAX (BS_MAX_PHOTONS * BS_MAX_PHOTONS)  // Q <= sum M_k^2 <= n^2
 #define BS_MIXED_RESIDUAL (-21.02)
 
@@ -186,17 +195,18 @@ struct CcArgs {
     void* data;                   // device arena (double or float complex)
     bs_zdd* partials;             // device, S x tasks_stride x n
     double2* minors;              // device, S x n
-    unsigned long long* total;    // device task totals [FP64, FP32]
-    unsigned long long* counter;  // device work counters [FP64, FP32]
-    unsigned long long* stats;    // device [addends64, flops64, addends32, flops32]
-    int* lists;                   // device job lists: [FP64: S][FP32: S]
-    int* list_len;                // device list lengths [FP64, FP32]
+    unsigned long long* total;    // device task totals, one per precision (BS_PREC_*)
+    unsigned long long* counter;  // device work counters, one per precision
+    unsigned long long* stats;    // device [addends, flops] per precision
+    int* lists;                   // device job lists, S per precision
+    int* list_len;                // device list lengths, one per precision
     int* out;                     // device, S x m_det
     int* trace;                   // device, S x n drawn rows in draw order (nullable)
     int64_t meta_stride, data_stride, tasks_stride;
-    int mixed;                    // 1: MIXED mode (per-chain FP32 / FP64 rule)
+    int mode;                     // bs_mode: FP64, MIXED (per-chain rule) or DF64
     float mixed_log2_tol;         // the rule's threshold, log2 of the MIXED tolerance
-    int log2max64, log2max32;
+    int mixed_fallback;           // MIXED: precision of the jobs that fail the rule
+    int log2max64, log2max32, log2maxdf;
 };
 
 cudaError_t launch_cc_init(const CcArgs& a, const CcArgs* da, cudaStream_t st);

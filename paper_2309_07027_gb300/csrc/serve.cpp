@@ -103,7 +103,7 @@ struct Request {
     size_t off = 0, bytes = 0;
     int64_t src_off = 0, data_off = 0, meta_off = 0, part_off = 0;
     int slot = -1;                     // result slot (BS_MAX_COLS values)
-    int fp32 = 0, cpt = 32, log2L = 6, ncols = 1;
+    int prec = BS_PREC_FP64, cpt = 32, log2L = 6, ncols = 1;
     uint32_t ntasks = 0, done = 0;
     int status = 0;                    // 0 pending, 1 done, <0 error code
     std::vector<bs_c128> result;
@@ -165,7 +165,7 @@ size_t request_bytes(const Request& r) {
     auto up = [](size_t b) { return (b + kAlign - 1) / kAlign * kAlign; };
     size_t b = 0;
     b += up((size_t)r.rows * r.cols * 16);                          // source matrix
-    b += up((size_t)(1 + p.nrows) * BS_ROW_STRIDE(p.K) * 16);       // packed c0 / 2a
+    b += up((size_t)(1 + p.nrows) * BS_ROW_STRIDE_P(p.K, r.prec) * 16);  // packed c0 / 2a
     b += up((size_t)BS_META_SIZE(p.nrows, p.K, p.n) * 4);                // metadata
     b += up((size_t)r.ntasks * r.ncols * sizeof(bs_zdd));            // task partials
     return b;
@@ -185,7 +185,7 @@ void finish(bs_server* s, Request* r, int status) {
 int run_tick(bs_server* s, std::vector<Request*>& admit, std::vector<Request*>& resident) {
     char* base = static_cast<char*>(s->arena_base);
     // 1. upload and pack the admitted jobs
-    std::vector<bs_job> packjobs[2];
+    std::vector<bs_job> packjobs[BS_NPREC];
     for (Request* r : admit) {
         const bs::IntPlan& p = r->plan;
         size_t at = r->off;
@@ -195,11 +195,11 @@ int run_tick(bs_server* s, std::vector<Request*>& admit, std::vector<Request*>& 
             return o;
         };
         const size_t src_b = take((size_t)r->rows * r->cols * 16);
-        const size_t data_b = take((size_t)(1 + p.nrows) * BS_ROW_STRIDE(p.K) * 16);
+        const size_t data_b = take((size_t)(1 + p.nrows) * BS_ROW_STRIDE_P(p.K, r->prec) * 16);
         const size_t meta_b = take((size_t)BS_META_SIZE(p.nrows, p.K, p.n) * 4);
         const size_t part_b = take((size_t)r->ntasks * r->ncols * sizeof(bs_zdd));
         r->src_off = (int64_t)(src_b / 16);
-        r->data_off = (int64_t)(data_b / (r->fp32 ? 8 : 16));
+        r->data_off = (int64_t)(data_b / (r->prec == BS_PREC_FP32 ? 8 : 16));
         r->meta_off = (int64_t)(meta_b / 4);
         r->part_off = (int64_t)(part_b / sizeof(bs_zdd));
         int meta[BS_META_SIZE(BS_MAX_DIGITS, BS_MAX_COLS, BS_MAX_N)];
@@ -226,8 +226,8 @@ int run_tick(bs_server* s, std::vector<Request*>& admit, std::vector<Request*>& 
         jb.kind = r->kind;
         jb.log2L = r->log2L;
         jb.n = p.n;
-        jb.normalize = r->fp32;
-        jb.fp32 = r->fp32;
+        jb.normalize = r->prec != BS_PREC_FP64 ? 1 : 0;
+        jb.prec = r->prec;
         jb.data_off = r->data_off;
         jb.meta_off = r->meta_off;
         jb.partial_off = r->part_off;
@@ -235,7 +235,7 @@ int run_tick(bs_server* s, std::vector<Request*>& admit, std::vector<Request*>& 
         jb.src_off = r->src_off;
         jb.src_ld = r->cols;
         jb.src_trans = p.trans ? 1 : 0;
-        packjobs[r->fp32].push_back(jb);
+        packjobs[r->prec].push_back(jb);
     }
     // 2. this tick's slices: equal share of the task budget per resident job
     std::vector<bs_job> walk;
@@ -255,7 +255,7 @@ int run_tick(bs_server* s, std::vector<Request*>& admit, std::vector<Request*>& 
         jb.kind = r->kind;
         jb.log2L = r->log2L;
         jb.n = p.n;
-        jb.fp32 = r->fp32;
+        jb.prec = r->prec;
         jb.data_off = r->data_off;
         jb.meta_off = r->meta_off;
         jb.partial_off = r->part_off;
@@ -265,11 +265,13 @@ int run_tick(bs_server* s, std::vector<Request*>& admit, std::vector<Request*>& 
     // sort into kernel groups, largest slices first
     std::vector<size_t> order(walk.size());
     for (size_t i = 0; i < order.size(); ++i) order[i] = i;
+    // kernel bucket of a job: 4-column buckets, 8-column for double-float
+    auto bucket = [](const bs_job& j) { return j.prec == BS_PREC_DF ? (j.K + 7) / 8 : (j.K + 3) / 4; };
     std::stable_sort(order.begin(), order.end(), [&](size_t a, size_t b) {
         const bs_job &x = walk[a], &y = walk[b];
-        if (x.fp32 != y.fp32) return x.fp32 < y.fp32;
+        if (x.prec != y.prec) return x.prec < y.prec;
         if (x.kind != y.kind) return x.kind < y.kind;
-        if ((x.K + 3) / 4 != (y.K + 3) / 4) return (x.K + 3) / 4 < (y.K + 3) / 4;
+        if (bucket(x) != bucket(y)) return bucket(x) < bucket(y);
         return x.ntasks > y.ntasks;
     });
     std::vector<bs_job> tick;
@@ -279,8 +281,8 @@ int run_tick(bs_server* s, std::vector<Request*>& admit, std::vector<Request*>& 
         const bs_job& g0 = walk[order[i]];
         uint64_t tb = 0;
         const size_t gstart = tick.size();
-        while (j < order.size() && walk[order[j]].fp32 == g0.fp32 && walk[order[j]].kind == g0.kind &&
-               (walk[order[j]].K + 3) / 4 == (g0.K + 3) / 4) {
+        while (j < order.size() && walk[order[j]].prec == g0.prec && walk[order[j]].kind == g0.kind &&
+               bucket(walk[order[j]]) == bucket(g0)) {
             bs_job jb = walk[order[j]];
             jb.task_begin = tb;
             tb += jb.ntasks;
@@ -304,7 +306,9 @@ int run_tick(bs_server* s, std::vector<Request*>& admit, std::vector<Request*>& 
             fin_req.push_back(r);
         }
     }
-    const size_t nb_pack = (packjobs[0].size() + packjobs[1].size()) * sizeof(bs_job);
+    size_t npack = 0;
+    for (int q = 0; q < BS_NPREC; ++q) npack += packjobs[q].size();
+    const size_t nb_pack = npack * sizeof(bs_job);
     const size_t nb_tick = tick.size() * sizeof(bs_job), nb_fin = fin.size() * sizeof(bs_job);
     size_t out_bytes = 0;
     for (Request* r : fin_req) out_bytes += (size_t)r->ncols * 16;
@@ -312,8 +316,13 @@ int run_tick(bs_server* s, std::vector<Request*>& admit, std::vector<Request*>& 
     if (rc) return rc;
     // descriptors go to the tail of the arena's control block
     char* hp = static_cast<char*>(s->h_pinned);
-    std::memcpy(hp, packjobs[0].data(), packjobs[0].size() * sizeof(bs_job));
-    std::memcpy(hp + packjobs[0].size() * sizeof(bs_job), packjobs[1].data(), packjobs[1].size() * sizeof(bs_job));
+    {
+        size_t at = 0;
+        for (int q = 0; q < BS_NPREC; ++q) {
+            std::memcpy(hp + at, packjobs[q].data(), packjobs[q].size() * sizeof(bs_job));
+            at += packjobs[q].size() * sizeof(bs_job);
+        }
+    }
     std::memcpy(hp + nb_pack, tick.data(), nb_tick);
     std::memcpy(hp + nb_pack + nb_tick, fin.data(), nb_fin);
     const size_t desc_bytes = nb_pack + nb_tick + nb_fin;
@@ -324,12 +333,15 @@ int run_tick(bs_server* s, std::vector<Request*>& admit, std::vector<Request*>& 
     const bs_job* d_pack = reinterpret_cast<const bs_job*>(base + desc_off);
     const bs_job* d_tick = reinterpret_cast<const bs_job*>(base + desc_off + nb_pack);
     const bs_job* d_fin = reinterpret_cast<const bs_job*>(base + desc_off + nb_pack + nb_tick);
-    if (!packjobs[0].empty())
-        e = bs::launch_pack(d_pack, (int)packjobs[0].size(), reinterpret_cast<const double2*>(base),
-                            reinterpret_cast<int*>(base), base, 0, s->stream);
-    if (e == cudaSuccess && !packjobs[1].empty())
-        e = bs::launch_pack(d_pack + packjobs[0].size(), (int)packjobs[1].size(),
-                            reinterpret_cast<const double2*>(base), reinterpret_cast<int*>(base), base, 1, s->stream);
+    {
+        size_t at = 0;
+        for (int q = 0; q < BS_NPREC && e == cudaSuccess; ++q) {
+            if (!packjobs[q].empty())
+                e = bs::launch_pack(d_pack + at, (int)packjobs[q].size(), reinterpret_cast<const double2*>(base),
+                                    reinterpret_cast<int*>(base), base, q, s->stream);
+            at += packjobs[q].size();
+        }
+    }
     if (e == cudaSuccess) e = cudaMemsetAsync(s->d_ctl, 0, 66 * 8, s->stream);
     unsigned long long* ctl = static_cast<unsigned long long*>(s->d_ctl);
     for (size_t gi = 0; gi < groups.size() && e == cudaSuccess; ++gi) {
@@ -351,7 +363,9 @@ int run_tick(bs_server* s, std::vector<Request*>& admit, std::vector<Request*>& 
         w.status = reinterpret_cast<int*>(ctl + 64);
         w.max_K = kmax;
         const bs_job& g0 = tick[groups[gi].first];
-        if (g0.fp32)
+        if (g0.prec == BS_PREC_DF)
+            e = g0.kind == BS_KIND_PERM ? bs::launch_walk_df_perm(w, s->stream) : bs::launch_walk_df_minors(w, s->stream);
+        else if (g0.prec == BS_PREC_FP32)
             e = g0.kind == BS_KIND_PERM ? bs::launch_walk_fp32_perm(w, s->stream) : bs::launch_walk_fp32_minors(w, s->stream);
         else
             e = g0.kind == BS_KIND_PERM ? bs::launch_walk_fp64_perm(w, s->stream) : bs::launch_walk_fp64_minors(w, s->stream);
@@ -469,7 +483,7 @@ int bs_server_create(bs_server** out, int device, size_t mem_budget_bytes, int m
                      bs_mode mode) {
     if (!out) return bs::fail(BS_EINVAL, "out is NULL");
     *out = nullptr;
-    if (mode != BS_FP64 && mode != BS_MIXED) return bs::fail(BS_EINVAL, "unknown mode %d", (int)mode);
+    if (mode != BS_FP64 && mode != BS_MIXED && mode != BS_DF64) return bs::fail(BS_EINVAL, "unknown mode %d", (int)mode);
     if (max_active < 1 || tick_tasks < 1 || mem_budget_bytes < (64u << 10))
         return bs::fail(BS_EINVAL, "need max_active >= 1, tick_tasks >= 1, budget >= 64 KiB");
     int count = 0;
@@ -561,15 +575,17 @@ int64_t bs_server_submit(bs_server* s, int kind, const bs_c128* A, int rows, int
     }
     r->mat.resize((size_t)rows * cols);
     for (int i = 0; i < rows; ++i) std::memcpy(&r->mat[(size_t)i * cols], A + (size_t)i * ld, sizeof(bs_c128) * cols);
-    r->fp32 = 0;
+    r->prec = s->mode == BS_DF64 ? BS_PREC_DF : BS_PREC_FP64;
     if (s->mode == BS_MIXED) {
         double q_work[BS_MIXED_QMAX + 1];
-        const int l32 = bs_choose_log2L(r->plan.C, bs_chunks_per_task(r->kind, 1, r->plan.K), BS_LOG2L_MIN_MANY, 12,
-                                        BS_TARGET_TASKS_MANY);
-        r->fp32 = bs_mixed_uses_fp32(r->plan.radix, r->plan.nrows, r->plan.pinned_m, r->plan.K, r->plan.n, l32,
-                                     BS_MIXED_LOG2_TOL_DEFAULT, q_work);
+        const int l32 = bs_choose_log2L(r->plan.C, bs_chunks_per_task(r->kind, BS_PREC_FP32, r->plan.K),
+                                        BS_LOG2L_MIN_MANY, 12, BS_TARGET_TASKS_MANY);
+        r->prec = bs_mixed_uses_fp32(r->plan.radix, r->plan.nrows, r->plan.pinned_m, r->plan.K, r->plan.n, l32,
+                                     BS_MIXED_LOG2_TOL_DEFAULT, q_work)
+                      ? BS_PREC_FP32
+                      : BS_MIXED_FALLBACK_PREC;
     }
-    r->cpt = bs_chunks_per_task(r->kind, r->fp32, r->plan.K);
+    r->cpt = bs_chunks_per_task(r->kind, r->prec, r->plan.K);
     r->log2L = bs_choose_log2L(r->plan.C, r->cpt, BS_LOG2L_MIN_MANY, 12, BS_TARGET_TASKS_MANY);
     const uint64_t per = (uint64_t)r->cpt << r->log2L;
     r->ntasks = (uint32_t)((r->plan.C + per - 1) / per);

@@ -1,7 +1,8 @@
 """GPU parity: the CUDA path (through the C ABI) against the CPU oracle.
 
 Tolerances (from the accuracy targets of the method, Sec. 3.2):
-  FP64 mode   |perm_gpu - perm_oracle| <= 1e-10 * prod_j ||a_j||_2^{N_j}
+  FP64 and double-float modes
+              |perm_gpu - perm_oracle| <= 1e-10 * prod_j ||a_j||_2^{N_j}
   MIXED mode  |perm_gpu - perm_oracle| <= 1e-6  * prod_j ||a_j||_2^{N_j}
 with ||a_j|| the 2-norm of column j over the rows repeated by their
 multiplicities (a Hadamard-type scale of the permanent).  Heavily repeated
@@ -22,7 +23,7 @@ import synthetic as S
 
 pytestmark = pytest.mark.gpu
 
-TOL = {0: 1e-10, 1: 1e-6}
+TOL = {0: 1e-10, 1: 1e-6, 2: 1e-10}  # FP64, MIXED, double-float
 TOL_L1 = 1e-12
 
 
@@ -45,7 +46,7 @@ def ref_perm(a, M, N):
     return v + t
 
 
-@pytest.mark.parametrize("mode", [0, 1])
+@pytest.mark.parametrize("mode", [0, 1, 2])
 def test_config_single_perm(ctx, mode):
     a, M, N, _, _ = S.config_single(seed=1)
     got = ctx.perm(a, M, N, mode=mode)
@@ -56,7 +57,7 @@ def test_config_single_perm(ctx, mode):
         assert abs((got2 + tail) - ref) <= 1e-13 * scale(a, M, N)
 
 
-@pytest.mark.parametrize("mode", [0, 1])
+@pytest.mark.parametrize("mode", [0, 1, 2])
 def test_config_single_minors(ctx, mode):
     a, M, N, _, _ = S.config_single(seed=1)
     # remove one photon from the last multiplicity-1 row: 11 rows x 12 columns
@@ -72,7 +73,7 @@ def test_config_single_minors(ctx, mode):
     assert abs(lap - full) <= 10 * TOL[mode] * scale(a, M, N)
 
 
-@pytest.mark.parametrize("mode", [0, 1])
+@pytest.mark.parametrize("mode", [0, 1, 2])
 @pytest.mark.parametrize("n", [1, 2, 3, 4, 5, 7, 8, 9, 12, 13, 16, 17, 20, 21])
 def test_distinct_sizes(ctx, mode, n):
     """Distinct rows and columns: C = 2^(n-1) addends, spanning many chunks
@@ -85,7 +86,7 @@ def test_distinct_sizes(ctx, mode, n):
     assert abs(got - (v + t)) <= TOL[mode] * scale(a, ones, ones), (n, got, v)
 
 
-@pytest.mark.parametrize("mode", [0, 1])
+@pytest.mark.parametrize("mode", [0, 1, 2])
 @pytest.mark.parametrize("K", [4, 6, 11, 15, 19, 24, 27, 30, 32, 33, 36, 38, 41, 44, 45, 48])
 def test_every_column_bucket(ctx, mode, K):
     """Few distinct rows with large multiplicities: every K bucket (up to 48
@@ -122,7 +123,7 @@ def test_mixed_routes_heavy_collisions_to_fp64(ctx):
     assert abs(r32 - ref_perm(b, Mb, Nb)) <= TOL[1] * scale(b, Mb, Nb)
 
 
-@pytest.mark.parametrize("mode", [0, 1])
+@pytest.mark.parametrize("mode", [0, 1, 2])
 def test_edge_cases(ctx, mode):
     # n = 0: the empty permanent
     assert ctx.perm(np.zeros((2, 2)), [0, 0], [0, 0], mode=mode) == 1
@@ -162,7 +163,7 @@ def test_invalid_arguments(ctx, bslib):
     assert abs(ctx.perm(np.array([[2.0]]), [1], [1]) - 2.0) < 1e-15
 
 
-@pytest.mark.parametrize("mode", [0, 1])
+@pytest.mark.parametrize("mode", [0, 1, 2])
 def test_minors_with_repeats_and_empty(ctx, mode):
     g = S.rng(55)
     for trial in range(6):
@@ -229,8 +230,9 @@ def test_fp32_minors_block_schedule(ctx, M, nbin):
 MINOR_WIDTHS = [13, 17, 20, 21, 24, 25, 26, 28, 29, 31, 32, 33, 36, 37, 40, 41, 44, 45, 48]
 
 
+@pytest.mark.parametrize("mode", [0, 2])
 @pytest.mark.parametrize("K", MINOR_WIDTHS)
-def test_fp64_minors_every_width_against_oracle(ctx, K):
+def test_fp64_minors_every_width_against_oracle(ctx, mode, K):
     """FP64 fused minors of a (K-1)-photon row set over K columns, for every
     column width up to 48: three distinct rows with large multiplicities keep
     the oracle's term-by-term formula cheap; every minor is checked against
@@ -242,11 +244,11 @@ def test_fp64_minors_every_width_against_oracle(ctx, K):
     u = S.haar_unitary(64, 500 + K)
     a = u[g.permutation(64)[:R]][:, g.permutation(64)[:K]]
     N = np.ones(K, dtype=np.int32)
-    got = ctx.laplace_minors(a, M, N, mode=0)
+    got = ctx.laplace_minors(a, M, N, mode=mode)
     for l in range(K):
         keep = [j for j in range(K) if j != l]
         ref = ref_perm(a[:, keep], M, N[keep])
-        bound = TOL[0] * minor_scale(a, M, N, l) + TOL_L1 * oracle.perm_mult_abs(a[:, keep], M, N[keep])
+        bound = TOL[mode] * minor_scale(a, M, N, l) + TOL_L1 * oracle.perm_mult_abs(a[:, keep], M, N[keep])
         assert abs(got[l] - ref) <= bound, (K, l, got[l], ref, bound)
 
 
@@ -291,7 +293,7 @@ def test_fp32_minors_every_width(ctx, bslib, K):
     assert abs(lap - full) <= 10 * bound * scale(np.vstack([a, v]), np.append(M, 1), N), (K, lap, full)
 
 
-@pytest.mark.parametrize("mode", [0, 1])
+@pytest.mark.parametrize("mode", [0, 1, 2])
 def test_batch_matches_oracle_and_single_calls(ctx, mode):
     items = S.config_batch(count=48, seed=7, kmin=6, kmax=18, m=60, group=16)
     items.append((np.zeros((1, 1)), np.array([0]), np.array([0])))       # trivial item
@@ -304,7 +306,7 @@ def test_batch_matches_oracle_and_single_calls(ctx, mode):
         assert alone == got[b], (b, alone, got[b])
 
 
-@pytest.mark.parametrize("mode", [0, 1])
+@pytest.mark.parametrize("mode", [0, 1, 2])
 def test_full_batch_config_sampled(ctx, mode):
     """4096 uneven permanents (k in [10, 28]) in one call; the oracle checks
     the cheapest items one by one, and FP64 / MIXED agree on every item."""
@@ -337,7 +339,7 @@ def test_batch_device_pointers(ctx):
     assert np.array_equal(out.cpu().numpy(), host)
 
 
-@pytest.mark.parametrize("mode", [0, 1])
+@pytest.mark.parametrize("mode", [0, 1, 2])
 def test_batch_graph_replay(ctx, mode):
     """A repeated batch replays its captured device sequence: the results
     equal the eager launches bit for bit, new matrix data in the same buffer
@@ -387,7 +389,7 @@ def test_batch_graph_replay(ctx, mode):
     assert np.array_equal(host, eager)
 
 
-@pytest.mark.parametrize("mode", [0, 1])
+@pytest.mark.parametrize("mode", [0, 1, 2])
 def test_single_call_graph_replay(ctx, mode):
     """Repeated single calls of one plan replay a captured graph (from the
     second call on): permanents with their double-double tails and minors
@@ -457,12 +459,14 @@ def test_deadline_returns_timeout_and_context_survives(ctx, bslib):
 
 
 # ---------------------------------------------------------------- sampling
-def test_sampler_matches_oracle_sampler_fp64(ctx):
-    """Same seed, same Philox counters: the GPU chain and the oracle chain draw
-    the same rows, except a draw that lands within 1e-9 of a CDF boundary."""
+@pytest.mark.parametrize("mode", [0, 2])
+def test_sampler_matches_oracle_sampler_fp64(ctx, mode):
+    """Same seed, same Philox counters: the GPU chain (FP64 or double-float)
+    and the oracle chain draw the same rows, except a draw that lands within
+    1e-9 of a CDF boundary."""
     u, occ = S.config_cc(n=6, m=12, seed=3)
     ns = 200
-    got = ctx.sample(u, occ, ns, seed=2024, mode=0)
+    got = ctx.sample(u, occ, ns, seed=2024, mode=mode)
     ref, margin, _ = oracle.cc_sample(u, occ, ns, seed=2024)
     mismatch = [s for s in range(ns) if not np.array_equal(got[s], ref[s])]
     assert all(margin[s] < 1e-9 for s in mismatch), (mismatch, margin[mismatch])
@@ -470,15 +474,16 @@ def test_sampler_matches_oracle_sampler_fp64(ctx):
     assert np.all(got.sum(axis=1) == 6)
 
 
+@pytest.mark.parametrize("mode", [0, 2])
 @pytest.mark.parametrize("n,m", [(6, 12), (8, 16)])
-def test_lossy_sampler_matches_oracle_sampler_fp64(ctx, n, m):
+def test_lossy_sampler_matches_oracle_sampler_fp64(ctx, n, m, mode):
     """Lossy sampling (one loss mode per photon, transmissivity 0.5): the GPU
     chains and the oracle's draw the same rows, seed for seed, only modes
     below m counted, except a draw within 1e-9 of a CDF boundary."""
     v, mdet = S.config_lossy(n=n, m=m, eta=0.5, seed=40 + n)
     ns = 120
     occ = np.ones(n, dtype=np.int32)
-    got = ctx.sample_ex(v, occ, ns, seed=4040 + n, m_detected=mdet, mode=0)
+    got = ctx.sample_ex(v, occ, ns, seed=4040 + n, m_detected=mdet, mode=mode)
     ref, margin, _ = oracle.cc_sample(v, occ, ns, seed=4040 + n, m_detected=mdet)
     assert got.shape == ref.shape == (ns, m)
     mismatch = [s_ for s_ in range(ns) if not np.array_equal(got[s_], ref[s_])]

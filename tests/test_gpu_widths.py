@@ -30,7 +30,7 @@ import synthetic as S
 
 pytestmark = pytest.mark.gpu
 
-TOL = {0: 1e-10, 1: 1e-6}
+TOL = {0: 1e-10, 1: 1e-6, 2: 1e-10}  # FP64, MIXED, double-float
 
 
 def scale(a, M, N):
@@ -152,7 +152,7 @@ def test_fp32_perm_dense_against_oracle(ctx, bslib):
 # ---------------------------------------------------------------- block diagonal, every width
 # Block-diagonal inputs cancel far more than unstructured ones (the modulus-
 # sum of the addends exceeds the permanent by up to 6e6 at K = 48), so they
-# pin the FP64 kernels at every width; the MIXED rule keeps such jobs in FP64.
+# pin the FP64 and double-float kernels at every width, not the FP32 ones.
 BLOCK_WIDTHS = [13, 17, 21, 24, 25, 28, 29, 30, 32, 33, 36, 37, 40, 41, 44, 45, 48]
 
 
@@ -161,21 +161,23 @@ def block_case(K, n, seed):
     return S.block_diagonal(K, n, seed, width=12, mult=mult)
 
 
+@pytest.mark.parametrize("mode", [0, 2])
 @pytest.mark.parametrize("K", BLOCK_WIDTHS)
-def test_minors_block_diagonal_every_width(ctx, K):
+def test_minors_block_diagonal_every_width(ctx, mode, K):
     a, M, N, groups = block_case(K, K - 1, 4500 + K)
-    got = ctx.laplace_minors(a, M, N, mode=0)
+    got = ctx.laplace_minors(a, M, N, mode=mode)
     ref = block_reference(a, M, N, groups, 1)
     for l in range(K):
-        assert abs(got[l] - ref[l]) <= TOL[0] * minor_scale(a, M, N, l), (K, l, got[l], ref[l])
+        assert abs(got[l] - ref[l]) <= TOL[mode] * minor_scale(a, M, N, l), (K, l, got[l], ref[l])
 
 
+@pytest.mark.parametrize("mode", [0, 2])
 @pytest.mark.parametrize("K", BLOCK_WIDTHS)
-def test_perm_block_diagonal_every_width(ctx, K):
+def test_perm_block_diagonal_every_width(ctx, mode, K):
     a, M, N, groups = block_case(K, K, 4600 + K)
-    got = ctx.perm(a, M, N, mode=0)
+    got = ctx.perm(a, M, N, mode=mode)
     ref = block_reference(a, M, N, groups, 0)
-    assert abs(got - ref) <= TOL[0] * scale(a, M, N), (K, got, ref)
+    assert abs(got - ref) <= TOL[mode] * scale(a, M, N), (K, got, ref)
 
 
 # ---------------------------------------------------------------- power-of-two column normalisation
@@ -221,7 +223,7 @@ def test_mixed_column_normalisation_extreme_ranges(ctx, bslib, kind):
 # draw margins below which a row may legitimately differ from the oracle's:
 # the mode's error in the CDF (FP64 ~1e-13 relative; MIXED minors ~1e-10
 # prod ||a_j||, i.e. ~1e-7 of a k <= 18 weight, with headroom)
-MARGIN = {0: 1e-9, 1: 1e-5}
+MARGIN = {0: 1e-9, 1: 1e-5, 2: 1e-9}
 TRACE_STEPS, TRACE_SAMPLES = 18, 8
 
 
@@ -232,7 +234,7 @@ def oracle_trace():
     return u, occ, rows, smargin
 
 
-@pytest.mark.parametrize("mode", [0, 1])
+@pytest.mark.parametrize("mode", [0, 1, 2])
 def test_sampler_rows_match_oracle_at_workload_size(ctx, oracle_trace, mode):
     """n = 30 photons, m = 60 modes (the sampling workload): the drawn row
     r_k of every step k <= 18 of every chain equals the oracle chain's, seed
