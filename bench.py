@@ -55,7 +55,7 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="mine", choices=["mine", "reference"])
     ap.add_argument("--samples", type=int, default=200)
-    ap.add_argument("--mode", default="fp64", choices=["mixed", "fp64"])
+    ap.add_argument("--mode", default="fp64", choices=["fp64", "mixed", "df"])
     ap.add_argument("--side-steps", type=int, default=3,
                     help="steps of the other precision's side measurement (0: skip)")
     ap.add_argument("--profile-steps", type=int, default=2, help="steps of the per-walk profiled pass")
@@ -285,10 +285,24 @@ def aggregate_rate(world, units_per_rank, seconds):
 
 
 # ---------------------------------------------------------------- GPU arm
+# Arithmetic of each form (the headline's dtype and the side forms').
+DTYPES = {"fp64": "f64", "mixed": "f32", "df": "f32x2"}
+DTYPE_DETAIL = {
+    "fp64": ("f64 column sums, products and weights; per-lane double runs folded into double-double, "
+             "double-double task partials (Sum2 reduce)"),
+    "mixed": ("f32 column sums and products where the MIXED rule predicts an error below 1e-6 prod ||a_j|| "
+              "(the rule is oracle-checked in tests/test_gpu_widths.py), double-float otherwise; float-float runs "
+              "folded into double-double partials"),
+    "df": ("double-float: each value a pair of f32 (about 48 significant bits) on the FP32 pipe; exact "
+           "fixed-point column sums, FMA-based exact products, Sum2 runs, double-double partials; within the FP64 "
+           "tolerance 1e-10 prod ||a_j||, with errors against the oracle about 100x the FP64 kernels' "
+           "(tests/test_gpu_parity.py, tests/test_gpu_widths.py)"),
+}
+
 # DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) of one k = 30
 # fused-minor launch of this workload under ncu, and the chains it ran; by
 # precision [FP64, FP32].  None where the kernel changed since the capture.
-TRAFFIC_K30 = [{"bytes": 0.52e6, "chains": 8}, {"bytes": 1.197e6, "chains": 32}]
+TRAFFIC_K30 = [{"bytes": 0.52e6, "chains": 8}, {"bytes": 1.197e6, "chains": 32}, None]
 
 def run_mine(args):
     import numpy as np
@@ -310,7 +324,7 @@ def run_mine(args):
         if dist is not None:
             dist.barrier()
 
-    modes = {"fp64": bs.BS_FP64, "mixed": bs.BS_MIXED}
+    modes = {"fp64": bs.BS_FP64, "mixed": bs.BS_MIXED, "df": bs.BS_DF64}
     mode = modes[args.mode]
     u, occ = S.config_cc(N_PHOTONS, M_MODES, SEED)
     ctx = bs.Context(local)
@@ -379,9 +393,11 @@ def run_mine(args):
     # roofline of the dominant walk kernel: the fused minors of the run's
     # precision (MIXED sends heavy-collision chains to the FP64 kernel, whose
     # time and work are reported beside)
-    p = 1 if mode == bs.BS_MIXED else 0
+    p = {bs.BS_FP64: 0, bs.BS_MIXED: 1, bs.BS_DF64: 2}[mode]
     walk_s = st["walk_ms"][p] / 1000.0
     fl = st["addend_flops"][p]
+    # (the double-float form's algorithmic flops are FP64-equivalent ones,
+    # set against the FP64 pipe's peak: its fraction exceeds 1 by design)
     peak = 2.0 * (fp32_rate if p == 1 else fp64_rate) / 1e12
     achieved = fl / walk_s / 1e12 if walk_s > 0 else 0.0
     # DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) of the k = 30
@@ -400,7 +416,7 @@ def run_mine(args):
             "frac": achieved / peak if peak else None, "traffic": traffic,
             "traffic_launch": (f"the k = 30 launch (ncu capture of {TRAFFIC_K30[p]['chains']} chains, scaled)"
                                if TRAFFIC_K30[p] else None),
-            "kernel": "walk_fp32_minors_kernel" if p == 1 else "walk_fp64_minors_kernel",
+            "kernel": ("walk_fp64_minors_kernel", "walk_fp32_minors_kernel", "walk_df_minors_kernel")[p],
             "peak_source": ("measured on this GPU by bs_measure_fma_rates (2 flops per lane-FMA), "
                             + ("FP32 FMA pipe" if p == 1 else "FP64 pipe")),
             "peak_nominal": peak_nominal, "frac_of_nominal": achieved / peak_nominal,
@@ -410,8 +426,8 @@ def run_mine(args):
             "measured_over": f"{psteps} profiled steps on the first timed steps' seeds, right after the timed "
                              f"pass ({statistics.mean(prof_step_ms):.1f} ms per profiled step)",
             "addends_per_s": st["addends"][p] / walk_s if walk_s > 0 else 0.0,
-            "other_precision": {"walk_ms_per_step": st["walk_ms"][1 - p] / psteps,
-                                "addends": st["addends"][1 - p]}}
+            "other_kernels": {name: {"walk_ms_per_step": st["walk_ms"][q] / psteps, "addends": st["addends"][q]}
+                              for q, name in enumerate(("fp64", "fp32", "df")) if q != p}}
 
     # end to end through the host API (U from host memory, counts back), on
     # the first timed steps' seeds, hence the same samples and work; the L2
@@ -433,54 +449,62 @@ def run_mine(args):
                "d2h_bytes_per_step": int(S_ * M_MODES * 4), "steps": esteps}
         ctx.set_stream(stream)
 
-    # the other precision on the same workload: samples/s over a few steps
-    # and, on the last timed step's seed, how many of its samples equal the
-    # headline run's
-    side = None
+    # the other forms on the same workload: samples/s over a few steps and,
+    # on the last timed step's seeds, how many of their samples equal the
+    # headline run's (the oracle comparisons of every form are in tests/)
+    side = {}
     if args.side_steps > 0:
-        other = bs.BS_MIXED if mode == bs.BS_FP64 else bs.BS_FP64
-        out2 = torch.zeros((S_, M_MODES), dtype=torch.int32, device="cuda")
-        ctx.sample_dev(u_dev, occ, S_, seed_base + 98, out2, mode=other)  # warm-up / capture
-        ctx.sync()
-        sms_ = timed_steps(min(args.side_steps, args.steps), False, other, out2)
-        ctx.sample_dev(u_dev, occ, S_, seed_base + 100 + args.steps - 1, out2, mode=other)
-        ctx.sync()
-        same = float(np.mean(np.all(out2.cpu().numpy() == counts, axis=1)))
-        side = {"mode": "mixed" if other == bs.BS_MIXED else "fp64",
-                "samples_per_s": S_ * len(sms_) / (sum(sms_) / 1000.0), "steps": len(sms_),
-                "dtype": "f32" if other == bs.BS_MIXED else "f64",
-                "samples_equal_to_headline_run": same,
-                "what": ("same workload and seeds; MIXED runs FP32 column sums and products where its precision rule "
-                         "predicts an error below 1e-6 prod ||a_j|| (oracle-checked at widths 13-48 in "
-                         "tests/test_gpu_widths.py), FP64 otherwise")}
+        for name in ("df", "mixed", "fp64"):
+            other = modes[name]
+            if other == mode:
+                continue
+            out2 = torch.zeros((S_, M_MODES), dtype=torch.int32, device="cuda")
+            ctx.sample_dev(u_dev, occ, S_, seed_base + 98, out2, mode=other)  # warm-up / capture
+            ctx.sync()
+            sms_ = timed_steps(min(args.side_steps, args.steps), False, other, out2)
+            ctx.sample_dev(u_dev, occ, S_, seed_base + 100 + args.steps - 1, out2, mode=other)
+            ctx.sync()
+            same = float(np.mean(np.all(out2.cpu().numpy() == counts, axis=1)))
+            side[name] = {"samples_per_s": S_ * len(sms_) / (sum(sms_) / 1000.0), "steps": len(sms_),
+                          "dtype": DTYPES[name], "dtype_detail": DTYPE_DETAIL[name],
+                          "samples_equal_to_headline_run": same}
 
     # the plain FP64 kernels on single k = 30 jobs, as fractions of the FP64
     # peak (the FP64 form is meant to keep the FP64 pipe >= 60 % busy for
     # k >= 30): permanent 30 x 30, minors 29 x 30
-    fp64_k30 = {}
+    fp64_k30, df_k30 = {}, {}
     ctx.set_profiling(True)
     u60 = S.haar_unitary(60, 77)
     for kind, rows in (("perm", 30), ("minors", 29)):
         a = u60[:rows, :30]
         M, N = np.ones(rows, np.int32), np.ones(30, np.int32)
-        for rep in range(2):
-            ctx.reset_stats()
-            if kind == "perm":
-                ctx.perm(a, M, N, mode=bs.BS_FP64)
-            else:
-                ctx.laplace_minors(a, M, N, mode=bs.BS_FP64)
-            s2 = ctx.stats()
-        secs = s2["walk_ms"][0] / 1000.0
-        rate = s2["addends"][0] / secs
+        res = {}
+        for md, p in ((bs.BS_FP64, 0), (bs.BS_DF64, 2)):
+            for rep in range(2):
+                ctx.reset_stats()
+                if kind == "perm":
+                    v = ctx.perm(a, M, N, mode=md)
+                else:
+                    v = ctx.laplace_minors(a, M, N, mode=md)
+                s2 = ctx.stats()
+            res[p] = (np.atleast_1d(v), s2["walk_ms"][p] / 1000.0, s2["addends"][p], s2["addend_flops"][p])
+        _, secs, adds, flops = res[0]
+        rate = adds / secs
         # FP64-pipe operations the walk needs per addend at K = 30 columns:
         # permanent 2K (update) + 4(K - 1) (product) + 2 (weighted sum);
         # lane-pair minors about 14K (each lane: update K, suffix and prefix
         # chains 2K - 4 each, accumulate 2K, exchange and weight about 6)
         ops = 6 * 30 - 2 if kind == "perm" else 14 * 30
         fp64_k30[kind] = {"addends_per_s": rate,
-                          "frac_of_fp64_peak": s2["addend_flops"][0] / secs / (2.0 * fp64_rate),
+                          "frac_of_fp64_peak": flops / secs / (2.0 * fp64_rate),
                           "fp64_pipe_ops_per_addend": ops,
                           "frac_of_fp64_pipe": rate * ops / fp64_rate}
+        vd, secs_d, adds_d, flops_d = res[2]
+        norms = np.sqrt((np.abs(a) ** 2).sum(axis=0))
+        scale = float(np.prod(norms)) / (float(norms.max()) if kind == "minors" else 1.0)
+        df_k30[kind] = {"addends_per_s": adds_d / secs_d, "speedup_over_fp64": secs / secs_d,
+                        "fp64_equivalent_tflops": flops_d / secs_d / 1e12,
+                        "max_diff_from_fp64_over_prod_norms": float(np.max(np.abs(vd - res[0][0]))) / scale}
     ctx.set_profiling(False)
     if rank != 0:
         ctx.close()
@@ -494,11 +518,7 @@ def run_mine(args):
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": statistics.mean(step_ms), "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None,
-        "dtype": "f32" if mode == bs.BS_MIXED else "f64",
-        "dtype_detail": ("f32 column sums and products where the MIXED rule allows (else f64), float-float runs "
-                         "folded into double-double partials" if mode == bs.BS_MIXED else
-                         "f64 column sums, products and weights; per-lane double runs folded into double-double, "
-                         "double-double task partials (Sum2 reduce)"),
+        "dtype": DTYPES[args.mode], "dtype_detail": DTYPE_DETAIL[args.mode],
         "data": "synthetic (seeded Haar-random 60-mode unitary)",
         "config": {"workload": "cc_sampling_n30_m60", "n": N_PHOTONS, "m": M_MODES, "samples_per_step": S_,
                    "mode": args.mode, "l2": "flushed between steps (256 MiB write)",
@@ -508,7 +528,7 @@ def run_mine(args):
                                 "steps; per-request p50 / p99 come from the serving workload")},
         "paper_model": paper_model(value / world),
         "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
-        "clocks": clk, "other_precision_form": side, "fp64_kernels_k30": fp64_k30, "wall_s": wall,
+        "clocks": clk, "other_forms": side, "fp64_kernels_k30": fp64_k30, "df_kernels_k30": df_k30, "wall_s": wall,
         "fma_rates_measured": {"fp64_per_s": fp64_rate, "fp32_per_s": fp32_rate},
     }
     print(json.dumps(line), flush=True)
@@ -610,7 +630,7 @@ def run_batch(args):
     dev = torch.from_numpy(packed).cuda()
     out = {}
     res = {}
-    for mode, name in ((bs.BS_FP64, "fp64"), (bs.BS_MIXED, "mixed")):
+    for mode, name in ((bs.BS_FP64, "fp64"), (bs.BS_MIXED, "mixed"), (bs.BS_DF64, "df")):
         o = torch.zeros(len(items), dtype=torch.complex128, device="cuda")
         ctx.set_stream(torch.cuda.current_stream())
         for w in range(args.warmup):
@@ -628,13 +648,16 @@ def run_batch(args):
         ctx.set_profiling(False)
         ms = e0.elapsed_time(e1) / args.steps
         res[name] = o.cpu().numpy()
-        p = 1 if mode == bs.BS_MIXED else 0
+        p = {bs.BS_FP64: 0, bs.BS_MIXED: 1, bs.BS_DF64: 2}[mode]
+        rates = ctx.measure_fma_rates()
         out[name] = {"permanents_per_s": len(items) / (ms / 1000), "ms_per_batch": ms,
-                     "addends_per_s": (st["addends"][0] + st["addends"][1]) / (ms / 1000) / args.steps,
+                     "addends_per_s": sum(st["addends"]) / (ms / 1000) / args.steps,
+                     # FP64 and double-float against the FP64 pipe (FP64-equivalent flops), FP32 against its own
                      "walk_kernel_frac_of_peak": (st["addend_flops"][p] / (st["walk_ms"][p] / 1000) /
-                                                  (2 * ctx.measure_fma_rates()[p])) if st["walk_ms"][p] else None}
+                                                  (2 * rates[1 if p == 1 else 0])) if st["walk_ms"][p] else None}
     sc = np.array([np.prod(np.sqrt((np.abs(a) ** 2 * M[:, None]).sum(0)) ** N) for a, M, N in items])
     rel = np.abs(res["mixed"] - res["fp64"]) / sc
+    rel_df = np.abs(res["df"] - res["fp64"]) / sc
     costs = np.argsort([int(np.prod(np.asarray(M) + 1)) for _, M, _ in items])[:16]
     orc = {"fp64_max": 0.0, "mixed_max": 0.0}
     for b_ in costs:
@@ -665,7 +688,9 @@ def run_batch(args):
     ctx.set_graphs(True)
     ctx.set_stream(None)
     line = {"workload": "batch_4096_k10_28", "metric": "permanents/s", "fp64": out["fp64"], "mixed": out["mixed"],
+            "df": out["df"],
             "mixed_vs_fp64_err_over_prod_norms": {"max": float(rel.max()), "p99": float(np.percentile(rel, 99))},
+            "df_vs_fp64_err_over_prod_norms": {"max": float(rel_df.max()), "p99": float(np.percentile(rel_df, 99))},
             "err_vs_oracle_over_prod_norms_16_cheapest": orc,
             "small_batch_64_k10_16_mixed_us_per_call": small_us,
             "cpu_oracle": None if args.no_cpu_baseline else oracle_batch_timing(items, args.cpu_seconds)}

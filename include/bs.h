@@ -59,7 +59,8 @@ typedef struct {
  *             of two), addends summed in float-float runs, partial sums in
  *             double-double (Sec. 3.2 discusses the accuracy trade-off), for
  *             every job whose predicted FP32 error meets the MIXED tolerance
- *             (bs_ctx_set_mixed_tolerance); other jobs run in FP64.
+ *             (bs_ctx_set_mixed_tolerance); other jobs run in the double-float
+ *             kernels of BS_DF64 (FP64-class, the cancellation-prone jobs).
  *   BS_DF64:  double-float: every quantity an unevaluated pair of floats
  *             (about 48 significant bits) on the single-precision pipe --
  *             column sums exact in fixed point (no drift), products by

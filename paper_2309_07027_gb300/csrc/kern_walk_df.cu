@@ -29,12 +29,29 @@ __global__ void __launch_bounds__(kDfBlock) walk_df_perm_kernel(WalkArgs a) {
     }
 }
 
+// Resident CTAs per SM the fused-minor kernel is compiled for (register
+// cap 65536 / (128 x value)): 3 at widths 24 and 48 (three pairs per lane,
+// no spill at 168 registers; width 24 measured 8 % faster than uncapped), 1
+// (no cap) elsewhere (widths 16, 32 and 40 spill at 168 registers; width 32
+// measured 4 % slower with the cap).  A build may override it for every
+// width with -DBS_DF_MINORS_MIN_BLOCKS=n to time the alternatives.
 template <int KB>
-__global__ void __launch_bounds__(kDfBlock) walk_df_minors_kernel(WalkArgs a) {
+struct DfMinorsMinBlocks {
+#ifdef BS_DF_MINORS_MIN_BLOCKS
+    static constexpr int value = BS_DF_MINORS_MIN_BLOCKS;
+#else
+    static constexpr int value = (KB == 24 || KB == 48) ? 3 : 1;
+#endif
+};
+
+template <int KB>
+__global__ void __launch_bounds__(kDfBlock, DfMinorsMinBlocks<KB>::value) walk_df_minors_kernel(WalkArgs a) {
     extern __shared__ float4 smem_df[];
     const int lane = threadIdx.x & 31;
     const int stride = blockDim.x;
+    // [column][thread] double-float sums, then [column][thread] staging
     float4* sm = smem_df + threadIdx.x;
+    float4* stage = smem_df + (size_t)(KB / BS_DF_GROUP_KB(KB)) * stride + threadIdx.x;
     const bs_job* __restrict__ jobs = a.jobs;
     const unsigned long long total = task_total(a);
     const int njobs = job_count(a);
@@ -48,7 +65,7 @@ __global__ void __launch_bounds__(kDfBlock) walk_df_minors_kernel(WalkArgs a) {
             continue;
         }
         walk_task_minors_df<KB>(jb, a.data, a.meta + BS_META_RADIX(jb), a.partials,
-                                (uint32_t)(t - jb.task_begin) + jb.task_offset, lane, sm, stride);
+                                (uint32_t)(t - jb.task_begin) + jb.task_offset, lane, sm, stage, stride);
     }
 }
 
@@ -78,8 +95,8 @@ static cudaError_t run_perm(const WalkArgs& a, cudaStream_t s) {
 
 template <int KB>
 static cudaError_t run_minors(const WalkArgs& a, cudaStream_t s) {
-    // one float4 fold slot per owned column and thread
-    const size_t smem = (size_t)kDfBlock * (KB / BS_DF_GROUP_KB(KB)) * sizeof(float4);
+    // per owned column and thread: a float4 fold slot and a float4 staging slot
+    const size_t smem = (size_t)kDfBlock * (KB / BS_DF_GROUP_KB(KB)) * 2 * sizeof(float4);
     cudaError_t e =
         cudaFuncSetAttribute(walk_df_minors_kernel<KB>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;

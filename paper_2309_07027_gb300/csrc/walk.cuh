@@ -373,6 +373,22 @@ __device__ void walk_task_perm_fp64(const bs_job& jb, const cx<double>* __restri
     if (lane == 0) store_partial(partials + jb.partial_off + local, sre, sim);
 }
 
+// Fold the plain-double runs of a lane's columns (t < KH) into their
+// double-double totals and clear the runs.
+template <int H>
+__device__ __forceinline__ void minors_fold_fp64(cx<double>* __restrict__ sm_acc, double4* __restrict__ sm_tot,
+                                                 int stride, int KH) {
+    // a rolled loop: its few temporaries stay out of the walk's registers
+#pragma unroll 1
+    for (int t = 0; t < KH; ++t) {
+        const cx<double> a = sm_acc[t * stride];
+        const double4 v = sm_tot[t * stride];
+        const ddv re = dd_add_d(ddv{v.x, v.y}, a.re), im = dd_add_d(ddv{v.z, v.w}, a.im);
+        sm_tot[t * stride] = make_double4(re.hi, re.lo, im.hi, im.lo);
+        sm_acc[t * stride] = cx<double>{0.0, 0.0};
+    }
+}
+
 // ---------------------------------------------------------------- one task: minors, FP64
 // Two lanes share one chunk: lane (2p + h) owns the columns
 // [h Hr, h Hr + KH), Hr = ceil(K / 2), KH = Hr (h = 0) or K - Hr (h = 1), so
@@ -383,7 +399,10 @@ __device__ void walk_task_perm_fp64(const bs_job& jb, const cx<double>* __restri
 //   2. swaps Q_own with its partner (one shuffle of a complex double),
 //   3. runs the prefix pass from X = (+-W) Q_partner:
 //          acc[l] += X * prefix_l * suffix_l,
-// with the per-column accumulators in shared memory, [col][thread].  Each
+// with the per-column accumulators in shared memory, [col][thread]: plain
+// double runs of FOLD addends, folded into double-double totals (a second
+// [col][thread] array of {re hi, re lo, im hi, im lo}) that the lanes then
+// combine in double-double.  Each
 // lane holds half the column sums and suffixes of the one-lane form, so twice
 // as many warps fit on an SM and the dependent product chains are half as
 // long, for the same FP64 work plus one real-by-complex product per lane and
@@ -393,7 +412,12 @@ __device__ void walk_task_perm_fp64(const bs_job& jb, const cx<double>* __restri
 template <int KB>
 __device__ void walk_task_minors_fp64(const bs_job& jb, const cx<double>* __restrict__ data,
                                       const int* __restrict__ radix, bs_zdd* __restrict__ partials, uint32_t local,
-                                      int lane, cx<double>* __restrict__ sm_acc, int stride) {
+                                      int lane, cx<double>* __restrict__ sm_acc, double4* __restrict__ sm_tot,
+                                      int stride) {
+    // fold interval: each lane spends about 7 FP64 operations per column and
+    // addend, a fold about 20 per column, so folds every 256 addends cost
+    // about 1 % (every 64: 4.8 %, measured on the 29 x 30 minors)
+    constexpr uint32_t FOLD = 256;
     constexpr int H = KB / 2;  // most columns a lane can own
     const int K = jb.K;
     constexpr int KP = KB;  // = BS_ROW_STRIDE(K) for every K of the bucket
@@ -406,7 +430,10 @@ __device__ void walk_task_minors_fp64(const bs_job& jb, const cx<double>* __rest
 #define BS_OWN(t) ((t) < H - 2 || (t) < KH)
 #pragma unroll
     for (int t = 0; t < H; ++t)
-        if (BS_OWN(t)) sm_acc[t * stride] = cx<double>{0.0, 0.0};
+        if (BS_OWN(t)) {
+            sm_acc[t * stride] = cx<double>{0.0, 0.0};
+            sm_tot[t * stride] = make_double4(0.0, 0.0, 0.0, 0.0);
+        }
     const uint64_t i0_own = ((uint64_t)local * 16u + (uint64_t)(lane >> 1)) << jb.log2L;
     const bool has = i0_own < jb.C;
     const uint64_t i0 = has ? i0_own : 0ull;
@@ -480,6 +507,7 @@ __device__ void walk_task_minors_fp64(const bs_job& jb, const cx<double>* __rest
                 sm_acc[t * stride] = a;
                 if (BS_OWN(t + 1)) pre = cmul(pre, c[t]);
             }
+        if (((s + 1u) & (FOLD - 1u)) == 0) minors_fold_fp64<H>(sm_acc, sm_tot, stride, KH);
         if (s + 1 >= len) {  // this lane's chunk is done: weight 0 from here on
             ws = 0.0;
             continue;
@@ -498,19 +526,20 @@ __device__ void walk_task_minors_fp64(const bs_job& jb, const cx<double>* __rest
                 c[t].im = bfma(cf, v.im, c[t].im);
             }
     }
-    // The 16 chunk sums per column are plain-double running sums, combined in
-    // plain double over lanes of equal parity (fixed butterfly order); the
+    minors_fold_fp64<H>(sm_acc, sm_tot, stride, KH);
+    // The 16 chunk totals per column (double-double) are combined in
+    // double-double over lanes of equal parity (fixed butterfly order); the
     // partials of different tasks are summed in twice double precision by
     // the reduce kernel.  Lane h < 2 ends with the sums of its columns.
     for (int t = 0; t < H; ++t) {
-        cx<double> a = BS_OWN(t) ? sm_acc[t * stride] : cx<double>{0.0, 0.0};
+        const double4 v = BS_OWN(t) ? sm_tot[t * stride] : make_double4(0.0, 0.0, 0.0, 0.0);
+        ddv re = {v.x, v.y}, im = {v.z, v.w};
 #pragma unroll
         for (int off = 16; off > 1; off >>= 1) {
-            a.re += __shfl_down_sync(0xffffffffu, a.re, off);
-            a.im += __shfl_down_sync(0xffffffffu, a.im, off);
+            re = dd_add(re, shfl_down_dd(re, off));
+            im = dd_add(im, shfl_down_dd(im, off));
         }
-        if (lane < 2 && t < KH)
-            store_partial(partials + jb.partial_off + (int64_t)local * K + cbase + t, ddv{a.re, 0.0}, ddv{a.im, 0.0});
+        if (lane < 2 && t < KH) store_partial(partials + jb.partial_off + (int64_t)local * K + cbase + t, re, im);
     }
 #undef BS_OWN
 }

@@ -315,18 +315,27 @@ __device__ __forceinline__ void df_seed(dfst (&c)[NP], const bs_gray& g, const f
     }
 }
 
-// Fold a Sum2 accumulator pair into the double-float sums in shared memory
-// ([column][thread] float4 {re h, re l, im h, im l}) and clear it.
-__device__ __forceinline__ void df_fold(float4* __restrict__ sm, int stride, int p, dfacc& a) {
+// Fold the Sum2 accumulators into the double-float sums in shared memory
+// ([column][thread] float4 {re h, re l, im h, im l}) and clear them.  The
+// accumulators are first staged to a second [column][thread] array; the
+// additions then run in a rolled loop, so their temporaries stay out of the
+// walk's registers.
+template <int NP>
+__device__ __forceinline__ void df_fold(float4* __restrict__ sm, float4* __restrict__ stage, int stride,
+                                        dfacc (&a)[NP]) {
 #pragma unroll
-    for (int hh = 0; hh < 2; ++hh) {
-        float4* slot = sm + (2 * p + hh) * stride;
-        float4 f = *slot;
-        const dfs re = s_add(dfs{f.x, f.y}, s_two_sum(hh ? a.rh.y : a.rh.x, hh ? a.rl.y : a.rl.x));
-        const dfs im = s_add(dfs{f.z, f.w}, s_two_sum(hh ? a.ih.y : a.ih.x, hh ? a.il.y : a.il.x));
-        *slot = make_float4(re.h, re.l, im.h, im.l);
+    for (int p = 0; p < NP; ++p) {
+        stage[(2 * p) * stride] = make_float4(a[p].rh.x, a[p].rl.x, a[p].ih.x, a[p].il.x);
+        stage[(2 * p + 1) * stride] = make_float4(a[p].rh.y, a[p].rl.y, a[p].ih.y, a[p].il.y);
+        a[p] = dfacc{make_float2(0.f, 0.f), make_float2(0.f, 0.f), make_float2(0.f, 0.f), make_float2(0.f, 0.f)};
     }
-    a = dfacc{make_float2(0.f, 0.f), make_float2(0.f, 0.f), make_float2(0.f, 0.f), make_float2(0.f, 0.f)};
+#pragma unroll 1
+    for (int t = 0; t < 2 * NP; ++t) {
+        const float4 f = sm[t * stride], g = stage[t * stride];
+        const dfs re = s_add(dfs{f.x, f.y}, s_two_sum(g.x, g.y));
+        const dfs im = s_add(dfs{f.z, f.w}, s_two_sum(g.z, g.w));
+        sm[t * stride] = make_float4(re.h, re.l, im.h, im.l);
+    }
 }
 
 // ---------------------------------------------------------------- one task: minors
@@ -344,7 +353,7 @@ __device__ __forceinline__ void df_fold(float4* __restrict__ sm, int stride, int
 template <int KB>
 __device__ void walk_task_minors_df(const bs_job& jb, const void* __restrict__ data_v,
                                     const int* __restrict__ radix, bs_zdd* __restrict__ partials, uint32_t local,
-                                    int lane, float4* __restrict__ sm, int stride) {
+                                    int lane, float4* __restrict__ sm, float4* __restrict__ stage, int stride) {
     constexpr uint32_t FOLD = 64;
     constexpr int G = BS_DF_GROUP_KB(KB);
     constexpr int NP = KB / (2 * G);
@@ -415,10 +424,7 @@ __device__ void walk_task_minors_df(const bs_job& jb, const void* __restrict__ d
             df_cmul_acc(acc[p], suf[p], pre);
             if (p + 1 < NP) pre = df_cmul_neg(df_norm(c[p]), pre);
         }
-        if (((s + 1u) & (FOLD - 1u)) == 0) {
-#pragma unroll
-            for (int p = 0; p < NP; ++p) df_fold(sm, stride, p, acc[p]);
-        }
+        if (((s + 1u) & (FOLD - 1u)) == 0) df_fold<NP>(sm, stage, stride, acc);
         if (s + 1u >= steps) break;
         if (s + 1u >= len) {  // this lane's chunk is done: weight 0 from here on
             ws = dfs{0.f, 0.f};
@@ -437,8 +443,7 @@ __device__ void walk_task_minors_df(const bs_job& jb, const void* __restrict__ d
             df_update(c[p], h, l, sg);
         }
     }
-#pragma unroll
-    for (int p = 0; p < NP; ++p) df_fold(sm, stride, p, acc[p]);
+    df_fold<NP>(sm, stage, stride, acc);
     // combine the chunks of the task (lanes of equal q) in double-float;
     // lane q < G ends with the sums of its columns
     const int KH = min(2 * NP, max(K - cbase, 0));

@@ -30,8 +30,11 @@ def test_bench_line_has_the_contract_keys():
     assert d["unit"] == "samples/s" and d["n_gpus"] == 1 and d["steps"] == 3 and d["warmup"] == 3
     assert d["dtype"] == "f64" and d["higher_is_better"] is True and d["scaling"] == "weak"
     assert d["config"]["mode"] == "fp64" and d["roofline"]["kernel"] == "walk_fp64_minors_kernel"
-    side = d["other_precision_form"]
-    assert side["mode"] == "mixed" and side["samples_per_s"] > 0 and 0 <= side["samples_equal_to_headline_run"] <= 1
+    side = d["other_forms"]
+    assert set(side) == {"mixed", "df"}
+    for name, f in side.items():
+        assert f["samples_per_s"] > 0 and 0 <= f["samples_equal_to_headline_run"] <= 1, name
+    assert d["df_kernels_k30"]["minors"]["speedup_over_fp64"] > 1
     assert d["latency_ms"]["max"] >= d["latency_ms"]["p50"] > 0
     assert d["config"]["workload"] == "cc_sampling_n30_m60" and d["config"]["samples_per_step"] == 16
     assert abs(d["value"] - 16 / (d["ms_per_step"] / 1000.0)) <= 1e-6 * d["value"]

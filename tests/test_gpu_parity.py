@@ -104,16 +104,21 @@ def test_every_column_bucket(ctx, mode, K):
     assert abs(got - ref) <= bound, (K, got, ref, bound)
 
 
-def test_mixed_routes_heavy_collisions_to_fp64(ctx):
+def test_mixed_routes_heavy_collisions_to_double_float(ctx):
     """The MIXED rule sends heavily repeated rows (here 7, 7, 6: predicted
-    FP32 error 2^-7.9 of prod ||a_j||) to the FP64 kernels, which give exactly
-    the FP64-mode result; light repeats (2, 2, 2 and distinct rows: 2^-23.8)
-    stay in FP32."""
+    FP32 error 2^-7.9 of prod ||a_j||) to the double-float kernels, which give
+    exactly the double-float-mode result; light repeats (2, 2, 2 and distinct
+    rows: 2^-23.8) stay in FP32."""
     u = S.haar_unitary(40, 9)
     a = u[:3, :20]
     M = np.array([7, 7, 6], dtype=np.int32)
     N = np.ones(20, dtype=np.int32)
-    assert ctx.perm(a, M, N, mode=1) == ctx.perm(a, M, N, mode=0)
+    ctx.reset_stats()
+    got = ctx.perm(a, M, N, mode=1)
+    st = ctx.stats()
+    assert st["addends"][2] > 0 and st["addends"][1] == 0 and st["addends"][0] == 0
+    assert got == ctx.perm(a, M, N, mode=2)
+    assert abs(got - ref_perm(a, M, N)) <= TOL[0] * scale(a, M, N) + TOL_L1 * oracle.perm_mult_abs(a, M, N)
     b = u[:12, :14]
     Mb = np.array([2, 2, 2] + [1] * 9, dtype=np.int32)
     Nb = np.ones(14, dtype=np.int32)
@@ -526,7 +531,7 @@ def test_profiled_sampler_graph_times_every_walk(ctx):
         for rep in range(3):
             got.append(ctx.sample(u, occ, 32, seed=5, mode=1))
             t = ctx.walk_times()
-            assert len(t) == 2 * (n - 1), (rep, len(t))  # FP64 and FP32 walk per step k = 2..n
+            assert len(t) == 2 * (n - 1), (rep, len(t))  # FP32 and double-float walk per step k = 2..n
             assert np.all(t >= 0) and np.sum(t) > 0
         for g in got:
             assert np.array_equal(g, eager)
