@@ -66,6 +66,8 @@ def parse():
     ap.add_argument("--workload", default="cc", choices=["cc", "single", "batch", "serving", "lossy", "formulas"],
                     help="cc: the headline line; the others print their own line for the other configs")
     ap.add_argument("--chains", type=int, default=64)
+    ap.add_argument("--serving-chains", type=int, default=64,
+                    help="chains of the serving side measurement on the headline line (0: skip)")
     ap.add_argument("--lossy-samples", type=int, default=20, help="samples of the lossy workload")
     return ap.parse_args()
 
@@ -506,6 +508,7 @@ def run_mine(args):
                         "fp64_equivalent_tflops": flops_d / secs_d / 1e12,
                         "max_diff_from_fp64_over_prod_norms": float(np.max(np.abs(vd - res[0][0]))) / scale}
     ctx.set_profiling(False)
+    serving_c4 = serving_measure(args.serving_chains) if rank == 0 and args.serving_chains > 0 else None
     if rank != 0:
         ctx.close()
         if dist is not None:
@@ -528,7 +531,8 @@ def run_mine(args):
                                 "steps; per-request p50 / p99 come from the serving workload")},
         "paper_model": paper_model(value / world),
         "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
-        "clocks": clk, "other_forms": side, "fp64_kernels_k30": fp64_k30, "df_kernels_k30": df_k30, "wall_s": wall,
+        "clocks": clk, "other_forms": side, "fp64_kernels_k30": fp64_k30, "df_kernels_k30": df_k30,
+        "serving": serving_c4, "wall_s": wall,
         "fma_rates_measured": {"fp64_per_s": fp64_rate, "fp32_per_s": fp32_rate},
     }
     print(json.dumps(line), flush=True)
@@ -698,28 +702,43 @@ def run_batch(args):
     return 0
 
 
-def run_serving(args):
-    """64 C&C chains (n ~ U[16, 34], m = 60) with Poisson arrivals served by
-    the continuous-batching engine (MIXED) vs one FP64 call per request."""
+def serving_measure(chains, modes=("fp64", "mixed")):
+    """Serving workload (C4): ``chains`` C&C samples, each with its own Haar
+    60 x 60 unitary and n ~ U[16, 34], Poisson arrivals at 200 Hz, served by
+    the continuous-batching engine (every chain on the device) in each of
+    ``modes``, and the same requests answered by one sample_ex call each in
+    FP64.  Samples/s over the wall time and per-request latency (arrival to
+    counts)."""
+    import numpy as np
     import paper_2309_07027_gb300 as bs
     from paper_2309_07027_gb300 import serving
     import synthetic as S
-    cfg = S.config_serving(chains=args.chains)
-    mk = lambda: [serving.Chain(c["unitary"], c["occupation"], c["seed"]) for c in cfg]
-    arr = [c["arrival_s"] for c in cfg]
-    with bs.Server(0, mem_budget_bytes=40 << 30, max_active=64, tick_tasks=8192, mode=bs.BS_MIXED) as srv:
-        ch = mk()
-        wall, lat = serving.run_served(ch, arr, srv)
-        st = srv.stats()
-    served = serving.summarize(wall, lat, len(ch))
-    served["server"] = {k: st[k] for k in ("ticks", "walk_launches", "max_resident", "mem_peak_bytes")}
+    cfg = S.config_serving(chains=chains)
+    mode_of = {"fp64": bs.BS_FP64, "mixed": bs.BS_MIXED, "df": bs.BS_DF64}
+    out = {"workload": f"serving_{chains}_chains_n16_34_m60_poisson200hz",
+           "latency_what": "per request: arrival (submission) to counts available"}
+    ref = None
+    for name in modes:
+        with bs.Server(0, mem_budget_bytes=40 << 30, max_active=64, tick_tasks=8192, mode=mode_of[name]) as srv:
+            wall, lat, counts = serving.run_served(cfg, srv)
+            st = srv.stats()
+        r = serving.summarize(wall, lat, len(cfg))
+        r["server"] = {k: st[k] for k in ("ticks", "walk_launches", "max_resident", "mem_peak_bytes")}
+        out[f"served_{name}"] = r
+        if name == "fp64":
+            ref = counts
     ctx = bs.Context(0)
-    ch = mk()
-    wall, lat = serving.run_one_call_per_permanent(ch, arr, ctx, mode=bs.BS_FP64)
-    base = serving.summarize(wall, lat, len(ch))
-    print(json.dumps({"workload": f"serving_{args.chains}_chains_n16_34_m60", "metric": "samples/s",
-                      "served_mixed": served, "one_call_per_permanent_fp64": base,
-                      "budget_bytes": 40 << 30}), flush=True)
+    ctx.sample_ex(cfg[0]["unitary"], cfg[0]["occupation"], 1, 1)  # load and warm the kernels
+    wall, lat, counts = serving.run_one_call_per_sample(cfg, ctx, mode=bs.BS_FP64)
+    ctx.close()
+    out["one_call_per_sample_fp64"] = serving.summarize(wall, lat, len(cfg))
+    if ref is not None:
+        out["served_fp64_equal_to_calls"] = float(np.mean([np.array_equal(a, b) for a, b in zip(ref, counts)]))
+    return out
+
+
+def run_serving(args):
+    print(json.dumps(serving_measure(args.chains, ("fp64", "mixed", "df"))), flush=True)
     return 0
 
 

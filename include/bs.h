@@ -44,7 +44,8 @@ enum {
     BS_ENOMEM = -2,    /* device memory budget or allocation exhausted */
     BS_ECUDA = -3,     /* CUDA runtime error (message in bs_last_error) */
     BS_ETIMEOUT = -4,  /* a kernel deadline expired (status word) */
-    BS_ENODEV = -5     /* no usable CUDA device */
+    BS_ENODEV = -5,    /* no usable CUDA device */
+    BS_ECANCELED = -6  /* a served request was cancelled (bs_server_cancel) */
 };
 
 typedef struct {
@@ -297,12 +298,40 @@ int64_t bs_server_submit(bs_server* server, int kind, const bs_c128* A, int rows
 int bs_server_poll(bs_server* server, int64_t ticket, bs_c128* out, int out_len, double* latency_s);
 int bs_server_wait(bs_server* server, int64_t ticket, bs_c128* out, int out_len, double* latency_s);
 
+/* A sampling request: one Clifford & Clifford chain (one sample, Sec. 4)
+ * served by the engine.  U is m_rows x m_cols (row-major, leading dimension
+ * ld, copied before returning), one input occupation per column; rows >=
+ * m_detected are loss modes (m_detected <= 0: all rows counted).  The
+ * chain's interferometer, permuted inputs and drawn rows stay on the device;
+ * each step's minors job (planned on the device) joins the shared walk
+ * launches of the next tick, and the row r_k is drawn on the device with the
+ * random numbers of bs_sample: sample `sample` of `seed` gives exactly the
+ * counts of sample `sample` of bs_sample / bs_sample_ex with that seed and the
+ * server's mode.  Returns a ticket >= 0, or a negative BS_E* code. */
+int64_t bs_server_submit_sample(bs_server* server, const bs_c128* U, int m_rows, int m_cols, int ld,
+                                const int* input_occupation, uint64_t seed, uint64_t sample, int m_detected);
+/* 1 and the occupation counts (m_detected ints) when the chain is done, 0
+ * while pending, negative on error (BS_ECANCELED after bs_server_cancel);
+ * the wait form blocks.  Either releases the ticket once it returns a
+ * result. */
+int bs_server_poll_sample(bs_server* server, int64_t ticket, int* counts, int len, double* latency_s);
+int bs_server_wait_sample(bs_server* server, int64_t ticket, int* counts, int len, double* latency_s);
+
+/* Cancels a pending request (any kind).  A request still waiting for
+ * admission is dropped at once; an admitted one is released after the
+ * current tick, when none of its kernels is in flight.  Its waiter then
+ * receives BS_ECANCELED.  Errors: BS_EINVAL (unknown or finished ticket). */
+int bs_server_cancel(bs_server* server, int64_t ticket);
+
 typedef struct {
     uint64_t submitted, completed, ticks, walk_launches;
     double busy_s;            /* time spent in ticks */
     double p50_ms, p99_ms, max_ms;  /* submit-to-completion latency of completed requests */
     int max_resident;         /* largest number of requests resident at once */
     size_t mem_peak_bytes;    /* peak bytes of the budget in use */
+    size_t mem_in_use_bytes;  /* bytes of the budget in use now (requests and a tick's descriptors) */
+    int resident, waiting;    /* requests admitted / waiting for admission now */
+    uint64_t cancelled;       /* requests ended by bs_server_cancel */
 } bs_server_stats;
 int bs_server_get_stats(bs_server* server, bs_server_stats* out);
 

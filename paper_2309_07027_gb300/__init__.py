@@ -33,9 +33,9 @@ PRECISIONS = ("fp64", "fp32", "df")
 FORMULAS = {"bbfg": 0, "ryser": 1, "nw": 2}
 MAX_N = 48
 
-BS_OK, BS_EINVAL, BS_ENOMEM, BS_ECUDA, BS_ETIMEOUT, BS_ENODEV = 0, -1, -2, -3, -4, -5  # noqa: E501
+BS_OK, BS_EINVAL, BS_ENOMEM, BS_ECUDA, BS_ETIMEOUT, BS_ENODEV, BS_ECANCELED = 0, -1, -2, -3, -4, -5, -6  # noqa: E501
 _CODES = {BS_EINVAL: "BS_EINVAL", BS_ENOMEM: "BS_ENOMEM", BS_ECUDA: "BS_ECUDA", BS_ETIMEOUT: "BS_ETIMEOUT",
-          BS_ENODEV: "BS_ENODEV"}
+          BS_ENODEV: "BS_ENODEV", BS_ECANCELED: "BS_ECANCELED"}
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 
@@ -51,7 +51,7 @@ class BsError(RuntimeError):
 
 
 class _Stats(C.Structure):
-    # index 0: FP64 walk kernels, index 1: FP32 walk kernels
+    # index 0: FP64 walk kernels, 1: FP32 walk kernels, 2: double-float walk kernels
     _fields_ = [("walk_launches", C.c_uint64), ("kernel_launches", C.c_uint64), ("addends", C.c_uint64 * 3),
                 ("addend_flops", C.c_uint64 * 3), ("walk_ms", C.c_double * 3), ("timed_launches", C.c_uint64 * 3)]
 
@@ -60,7 +60,8 @@ class _ServerStats(C.Structure):
     _fields_ = [("submitted", C.c_uint64), ("completed", C.c_uint64), ("ticks", C.c_uint64),
                 ("walk_launches", C.c_uint64), ("busy_s", C.c_double), ("p50_ms", C.c_double),
                 ("p99_ms", C.c_double), ("max_ms", C.c_double), ("max_resident", C.c_int),
-                ("mem_peak_bytes", C.c_size_t)]
+                ("mem_peak_bytes", C.c_size_t), ("mem_in_use_bytes", C.c_size_t), ("resident", C.c_int),
+                ("waiting", C.c_int), ("cancelled", C.c_uint64)]
 
 
 _lib = None
@@ -117,6 +118,11 @@ def load():
         "bs_server_submit": ([vp, C.c_int, vp, C.c_int, C.c_int, C.c_int, ip, ip], C.c_int64),
         "bs_server_poll": ([vp, C.c_int64, vp, C.c_int, dp], C.c_int),
         "bs_server_wait": ([vp, C.c_int64, vp, C.c_int, dp], C.c_int),
+        "bs_server_submit_sample": ([vp, vp, C.c_int, C.c_int, C.c_int, ip, C.c_uint64, C.c_uint64, C.c_int],
+                                    C.c_int64),
+        "bs_server_poll_sample": ([vp, C.c_int64, ip, C.c_int, dp], C.c_int),
+        "bs_server_wait_sample": ([vp, C.c_int64, ip, C.c_int, dp], C.c_int),
+        "bs_server_cancel": ([vp, C.c_int64], C.c_int),
         "bs_server_get_stats": ([vp, C.POINTER(_ServerStats)], C.c_int),
     }
     for name, (args, res) in sig.items():
@@ -442,6 +448,43 @@ class Server:
         if rc < 0:
             _check(rc)
         return (True, out[:n], lat.value) if rc == 1 else (False, None, None)
+
+    def submit_sample(self, u, occupation, seed: int, sample: int = 0, m_detected: int = 0):
+        """One Clifford & Clifford sample, run by the engine: the counts of
+        sample ``sample`` of bs_sample_ex(u, occupation, seed) in the server's
+        mode.  Returns a ticket for wait_sample / poll_sample / cancel."""
+        u = _c128(u)
+        mr, mc = u.shape
+        occ = _i32(occupation, mc)
+        mdet = mr if m_detected <= 0 or m_detected > mr else int(m_detected)
+        t = self._L.bs_server_submit_sample(self._p, u.ctypes.data, mr, mc, mc, _ip(occ),
+                                            C.c_uint64(int(seed) & ((1 << 64) - 1)),
+                                            C.c_uint64(int(sample) & ((1 << 64) - 1)), int(mdet))
+        if t < 0:
+            _check(int(t))
+        return int(t), -mdet  # negative width marks a sampling ticket
+
+    def wait_sample(self, ticket):
+        """Blocks; returns (counts[m_detected], latency seconds)."""
+        t, w = ticket
+        out = np.zeros(max(-w, 1), dtype=np.int32)
+        lat = C.c_double()
+        _check(self._L.bs_server_wait_sample(self._p, t, _ip(out), len(out), C.byref(lat)))
+        return out[:-w], lat.value
+
+    def poll_sample(self, ticket):
+        """(done, counts or None, latency or None)."""
+        t, w = ticket
+        out = np.zeros(max(-w, 1), dtype=np.int32)
+        lat = C.c_double()
+        rc = self._L.bs_server_poll_sample(self._p, t, _ip(out), len(out), C.byref(lat))
+        if rc < 0:
+            _check(rc)
+        return (True, out[:-w], lat.value) if rc == 1 else (False, None, None)
+
+    def cancel(self, ticket):
+        """Cancels a pending request; its waiter gets BsError(BS_ECANCELED)."""
+        _check(self._L.bs_server_cancel(self._p, ticket[0]))
 
     def stats(self):
         s = _ServerStats()

@@ -183,6 +183,15 @@ BS_HD int bs_mixed_uses_fp32(const int* radix, int nrows, int pinned_m, int K, i
 
 namespace bs {
 
+// The precision choice of a sampling step: bs_mode, the MIXED threshold and
+// fallback, and the chunk-length caps by precision.
+struct StepRule {
+    int mode;
+    float mixed_log2_tol;
+    int mixed_fallback;
+    int log2max[BS_NPREC];
+};
+
 struct CcArgs {
     int S;                        // chains (samples) in this batch
     int n;                        // photons
@@ -211,6 +220,33 @@ struct CcArgs {
     int mixed_fallback;           // MIXED: precision of the jobs that fail the rule
     int log2max64, log2max32, log2maxdf;
 };
+
+// One served Clifford & Clifford chain (one sample) resident in a server's
+// device arena.  Offsets count from the arena base.
+struct ChainDesc {
+    const double2* U;       // m_rows x m_cols, leading dimension m_cols
+    int m_rows, m_cols, m_det, n;
+    uint64_t seed, sample;  // the Philox key and counter of the sample
+    const int* inputs;      // n expanded input columns
+    int* cols;              // n permuted columns
+    int* rows;              // n drawn rows
+    int* counts;            // m_det occupation counts (written after step n)
+    bs_job* job;            // the chain's job descriptor
+    int64_t meta_off;       // int units
+    int64_t data_byte_off;  // bytes (16-byte aligned)
+    int64_t partial_off;    // bs_zdd units
+    int out_index;          // minors slot in the server's output block (double2 units)
+    int k;                  // the step whose row is drawn now (1 = the first)
+    StepRule rule;
+};
+
+// Fisher-Yates permutation of every chain's input columns (as cc_init).
+cudaError_t launch_chain_init(const ChainDesc* d, int count, cudaStream_t st);
+// For every chain: draw r_k from the step-k minors in minors_base +
+// out_index (k >= 2), then plan and pack its step k + 1 minors job, or,
+// after step n, write its occupation counts.  One CTA per chain.
+cudaError_t launch_chain_advance(const ChainDesc* d, int count, int max_m_rows, void* arena,
+                                 const double2* minors_base, cudaStream_t st);
 
 cudaError_t launch_cc_init(const CcArgs& a, const CcArgs* da, cudaStream_t st);
 cudaError_t launch_cc_plan(const CcArgs& a, const CcArgs* da, int k, cudaStream_t st);

@@ -1,6 +1,9 @@
-// Serving engine: continuous batching of permanent and minors requests from
-// many concurrent clients (for example Clifford & Clifford sampling chains,
-// Sec. 4, which ask for the minors of one step, draw a row, and ask again).
+// Serving engine: continuous batching of permanent, minors and sampling
+// requests from many concurrent clients.  A sampling request is a whole
+// Clifford & Clifford chain (Sec. 4): its interferometer, permuted inputs
+// and drawn rows stay resident on the device, and each step's minors job
+// joins the shared walk launches of the next tick while the draw of the next
+// row and the planning of the next job run on the device (chain_advance).
 //
 // A scheduler thread runs ticks.  Each tick
 //   1. admits waiting requests in arrival order while a slot is free and the
@@ -20,6 +23,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <atomic>
 #include <chrono>
 #include <condition_variable>
 #include <cstring>
@@ -40,6 +44,9 @@ namespace {
 
 using clock_type = std::chrono::steady_clock;
 constexpr size_t kAlign = 256;
+// chunk-length cap of served chains' step jobs: the default of a context, so
+// that a served sample plans every step as bs_sample does
+constexpr int kChainLog2Max = 12;
 
 // First-fit allocator over [0, size) with coalescing free ranges.
 class Arena {
@@ -59,7 +66,7 @@ class Arena {
                 free_.erase(it);
                 if (len > bytes) free_[off + bytes] = len - bytes;
                 used_ += bytes;
-                peak_ = std::max(peak_, used_);
+                peak_ = std::max(peak_.load(), used_.load());
                 return off;
             }
         }
@@ -87,7 +94,9 @@ class Arena {
 
   private:
     std::map<size_t, size_t> free_;
-    size_t used_ = 0, peak_ = 0;
+    // the engine thread alone allocates and releases (a tick's descriptors
+    // outside the lock); the counters are read by bs_server_get_stats
+    std::atomic<size_t> used_{0}, peak_{0};
 };
 
 struct Request {
@@ -107,6 +116,19 @@ struct Request {
     uint32_t ntasks = 0, done = 0;
     int status = 0;                    // 0 pending, 1 done, <0 error code
     std::vector<bs_c128> result;
+    bool cancel = false;               // set by bs_server_cancel; released between ticks
+    // sampling chains: one Clifford & Clifford sample
+    bool chain = false;
+    int k = 0;                         // step whose row is drawn next (1 = first)
+    bool chain_done = false;
+    int m_rows = 0, m_cols = 0, m_det = 0, n = 0;
+    uint64_t seed = 0, sample = 0;
+    std::vector<int> inputs;           // expanded input columns
+    std::vector<int> counts;           // result: m_det occupation counts
+    bs_job job_host{};                 // the pending step's job, as planned on the device
+    uint64_t tasks_stride = 0;         // task partial slots per step
+    // byte offsets of the chain's regions inside its arena block
+    size_t c_u = 0, c_in = 0, c_cols = 0, c_rows = 0, c_cnt = 0, c_job = 0, c_meta = 0, c_data = 0, c_part = 0;
 };
 
 }  // namespace
@@ -137,7 +159,7 @@ struct bs_server {
     std::string fatal;
 
     // statistics
-    uint64_t submitted = 0, completed = 0, ticks = 0, walk_launches = 0;
+    uint64_t submitted = 0, completed = 0, ticks = 0, walk_launches = 0, cancelled = 0;
     double busy_s = 0;
     int max_resident = 0;
     std::vector<double> latencies_ms;
@@ -159,6 +181,30 @@ int ensure_pinned(bs_server* s, size_t bytes) {
     return BS_OK;
 }
 
+// Lays out a chain's regions (byte offsets from the start of its block) and
+// returns the block size: U, inputs, permuted columns, drawn rows, counts,
+// the job descriptor, metadata, packed data (widest row stride) and task
+// partials for its largest step.
+size_t chain_layout(Request& r) {
+    auto up = [](size_t b) { return (b + kAlign - 1) / kAlign * kAlign; };
+    size_t at = 0;
+    auto take = [&](size_t b) {
+        const size_t o = at;
+        at += up(std::max<size_t>(b, 1));
+        return o;
+    };
+    r.c_u = take((size_t)r.m_rows * r.m_cols * 16);
+    r.c_in = take((size_t)r.n * 4);
+    r.c_cols = take((size_t)r.n * 4);
+    r.c_rows = take((size_t)r.n * 4);
+    r.c_cnt = take((size_t)r.m_det * 4);
+    r.c_job = take(sizeof(bs_job));
+    r.c_meta = take((size_t)BS_META_SIZE(r.n, r.n, r.n) * 4);
+    r.c_data = take((size_t)r.n * BS_ROW_STRIDE_DF(r.n) * 16);
+    r.c_part = take((size_t)r.tasks_stride * r.n * sizeof(bs_zdd));
+    return at;
+}
+
 // Bytes a request needs on the device.
 size_t request_bytes(const Request& r) {
     const bs::IntPlan& p = r.plan;
@@ -177,6 +223,8 @@ void finish(bs_server* s, Request* r, int status) {
     if (status == 1) {
         s->completed++;
         s->latencies_ms.push_back(std::chrono::duration<double, std::milli>(r->t_done - r->t_submit).count());
+    } else if (status == BS_ECANCELED) {
+        s->cancelled++;
     }
 }
 
@@ -187,6 +235,15 @@ int run_tick(bs_server* s, std::vector<Request*>& admit, std::vector<Request*>& 
     // 1. upload and pack the admitted jobs
     std::vector<bs_job> packjobs[BS_NPREC];
     for (Request* r : admit) {
+        if (r->chain) {  // U and the input columns; the chain's kernels start it (below)
+            cudaError_t e = cudaMemcpyAsync(base + r->off + r->c_u, r->mat.data(), r->mat.size() * 16,
+                                            cudaMemcpyHostToDevice, s->stream);
+            if (e == cudaSuccess)
+                e = cudaMemcpyAsync(base + r->off + r->c_in, r->inputs.data(), r->inputs.size() * 4,
+                                    cudaMemcpyHostToDevice, s->stream);
+            if (e != cudaSuccess) return bs::fail(BS_ECUDA, "server upload: %s", cudaGetErrorString(e));
+            continue;
+        }
         const bs::IntPlan& p = r->plan;
         size_t at = r->off;
         auto take = [&](size_t b) {
@@ -240,25 +297,31 @@ int run_tick(bs_server* s, std::vector<Request*>& admit, std::vector<Request*>& 
     // 2. this tick's slices: equal share of the task budget per resident job
     std::vector<bs_job> walk;
     std::vector<Request*> walk_req;
-    const uint32_t share =
-        std::max<uint32_t>(1, (uint32_t)(s->tick_tasks / std::max<size_t>(1, resident.size())));
+    size_t walking = 0;
+    for (Request* r : resident) walking += r->done < r->ntasks ? 1 : 0;
+    const uint32_t share = std::max<uint32_t>(1, (uint32_t)(s->tick_tasks / std::max<size_t>(1, walking)));
     for (Request* r : resident) {
-        const bs::IntPlan& p = r->plan;
+        if (r->done >= r->ntasks) continue;  // a chain between steps, or a newly admitted chain
         bs_job jb;
-        std::memset(&jb, 0, sizeof(jb));
-        jb.C = p.C;
+        if (r->chain) {
+            jb = r->job_host;
+        } else {
+            const bs::IntPlan& p = r->plan;
+            std::memset(&jb, 0, sizeof(jb));
+            jb.C = p.C;
+            jb.K = p.K;
+            jb.nrows = p.nrows;
+            jb.nbin = p.nbin;
+            jb.kind = r->kind;
+            jb.log2L = r->log2L;
+            jb.n = p.n;
+            jb.prec = r->prec;
+            jb.data_off = r->data_off;
+            jb.meta_off = r->meta_off;
+            jb.partial_off = r->part_off;
+        }
         jb.ntasks = std::min(share, r->ntasks - r->done);
         jb.task_offset = r->done;
-        jb.K = p.K;
-        jb.nrows = p.nrows;
-        jb.nbin = p.nbin;
-        jb.kind = r->kind;
-        jb.log2L = r->log2L;
-        jb.n = p.n;
-        jb.prec = r->prec;
-        jb.data_off = r->data_off;
-        jb.meta_off = r->meta_off;
-        jb.partial_off = r->part_off;
         walk.push_back(jb);
         walk_req.push_back(r);
     }
@@ -306,13 +369,55 @@ int run_tick(bs_server* s, std::vector<Request*>& admit, std::vector<Request*>& 
             fin_req.push_back(r);
         }
     }
+    // chains that draw a row this tick: the admitted ones (step 1) first,
+    // then those whose step job finishes now
+    std::vector<Request*> adv;
+    int n_init = 0, max_m_rows = 1;
+    for (Request* r : admit)
+        if (r->chain) adv.push_back(r);
+    n_init = (int)adv.size();
+    for (Request* r : fin_req)
+        if (r->chain) adv.push_back(r);
+    std::vector<bs::ChainDesc> descs;
+    size_t back_bytes = 0;
+    for (Request* r : adv) {
+        char* cb = base + r->off;
+        bs::ChainDesc d;
+        std::memset(&d, 0, sizeof(d));
+        d.U = reinterpret_cast<const double2*>(cb + r->c_u);
+        d.m_rows = r->m_rows;
+        d.m_cols = r->m_cols;
+        d.m_det = r->m_det;
+        d.n = r->n;
+        d.seed = r->seed;
+        d.sample = r->sample;
+        d.inputs = reinterpret_cast<const int*>(cb + r->c_in);
+        d.cols = reinterpret_cast<int*>(cb + r->c_cols);
+        d.rows = reinterpret_cast<int*>(cb + r->c_rows);
+        d.counts = reinterpret_cast<int*>(cb + r->c_cnt);
+        d.job = reinterpret_cast<bs_job*>(cb + r->c_job);
+        d.meta_off = (int64_t)((r->off + r->c_meta) / 4);
+        d.data_byte_off = (int64_t)(r->off + r->c_data);
+        d.partial_off = (int64_t)((r->off + r->c_part) / sizeof(bs_zdd));
+        d.out_index = r->slot * BS_MAX_COLS;
+        d.k = r->k;
+        d.rule.mode = (int)s->mode;
+        d.rule.mixed_log2_tol = BS_MIXED_LOG2_TOL_DEFAULT;
+        d.rule.mixed_fallback = BS_MIXED_FALLBACK_PREC;
+        for (int q = 0; q < BS_NPREC; ++q) d.rule.log2max[q] = kChainLog2Max;
+        descs.push_back(d);
+        max_m_rows = std::max(max_m_rows, r->m_rows);
+        back_bytes += r->k < r->n ? sizeof(bs_job) : (size_t)r->m_det * 4;
+    }
     size_t npack = 0;
     for (int q = 0; q < BS_NPREC; ++q) npack += packjobs[q].size();
     const size_t nb_pack = npack * sizeof(bs_job);
     const size_t nb_tick = tick.size() * sizeof(bs_job), nb_fin = fin.size() * sizeof(bs_job);
+    const size_t nb_chain = descs.size() * sizeof(bs::ChainDesc);
     size_t out_bytes = 0;
-    for (Request* r : fin_req) out_bytes += (size_t)r->ncols * 16;
-    int rc = ensure_pinned(s, nb_pack + nb_tick + nb_fin + out_bytes + 64);
+    for (Request* r : fin_req)
+        if (!r->chain) out_bytes += (size_t)r->ncols * 16;
+    int rc = ensure_pinned(s, nb_pack + nb_tick + nb_fin + nb_chain + out_bytes + back_bytes + 64);
     if (rc) return rc;
     // descriptors go to the tail of the arena's control block
     char* hp = static_cast<char*>(s->h_pinned);
@@ -325,7 +430,8 @@ int run_tick(bs_server* s, std::vector<Request*>& admit, std::vector<Request*>& 
     }
     std::memcpy(hp + nb_pack, tick.data(), nb_tick);
     std::memcpy(hp + nb_pack + nb_tick, fin.data(), nb_fin);
-    const size_t desc_bytes = nb_pack + nb_tick + nb_fin;
+    std::memcpy(hp + nb_pack + nb_tick + nb_fin, descs.data(), nb_chain);
+    const size_t desc_bytes = nb_pack + nb_tick + nb_fin + nb_chain;
     size_t desc_off = s->arena.alloc(std::max<size_t>(desc_bytes, 16));
     if (desc_off == SIZE_MAX) return bs::fail(BS_ENOMEM, "server: no arena space for tick descriptors");
     cudaError_t e = cudaMemcpyAsync(base + desc_off, hp, desc_bytes, cudaMemcpyHostToDevice, s->stream);
@@ -333,6 +439,8 @@ int run_tick(bs_server* s, std::vector<Request*>& admit, std::vector<Request*>& 
     const bs_job* d_pack = reinterpret_cast<const bs_job*>(base + desc_off);
     const bs_job* d_tick = reinterpret_cast<const bs_job*>(base + desc_off + nb_pack);
     const bs_job* d_fin = reinterpret_cast<const bs_job*>(base + desc_off + nb_pack + nb_tick);
+    const bs::ChainDesc* d_chain =
+        reinterpret_cast<const bs::ChainDesc*>(base + desc_off + nb_pack + nb_tick + nb_fin);
     {
         size_t at = 0;
         for (int q = 0; q < BS_NPREC && e == cudaSuccess; ++q) {
@@ -359,7 +467,7 @@ int run_tick(bs_server* s, std::vector<Request*>& admit, std::vector<Request*>& 
             kmax = std::max(kmax, tick[i].K);
         }
         w.total_tasks = tot;
-        w.counter = ctl + gi;  // at most 2 x 2 x 12 = 48 groups
+        w.counter = ctl + gi;  // at most 2 x 2 x 12 + 2 x 6 = 60 groups
         w.status = reinterpret_cast<int*>(ctl + 64);
         w.max_K = kmax;
         const bs_job& g0 = tick[groups[gi].first];
@@ -377,13 +485,34 @@ int run_tick(bs_server* s, std::vector<Request*>& admit, std::vector<Request*>& 
         e = bs::launch_reduce(d_fin, (int)fin.size(), reinterpret_cast<const bs_zdd*>(base),
                               reinterpret_cast<const int*>(base), static_cast<double2*>(s->d_out), nullptr, maxc,
                               s->stream);
+    // chains: permute the admitted chains' inputs, then draw this tick's rows
+    // and plan their next jobs (their step minors are in d_out)
+    if (e == cudaSuccess && n_init > 0) e = bs::launch_chain_init(d_chain, n_init, s->stream);
+    if (e == cudaSuccess && !descs.empty())
+        e = bs::launch_chain_advance(d_chain, (int)descs.size(), max_m_rows, base,
+                                     static_cast<const double2*>(s->d_out), s->stream);
     char* hout = hp + desc_bytes + 16;
     size_t at = 0;
     for (Request* r : fin_req) {
         if (e != cudaSuccess) break;
+        if (r->chain) continue;
         e = cudaMemcpyAsync(hout + at, static_cast<double2*>(s->d_out) + (size_t)r->slot * BS_MAX_COLS,
                             (size_t)r->ncols * 16, cudaMemcpyDeviceToHost, s->stream);
         at += (size_t)r->ncols * 16;
+    }
+    char* hback = hout + at;
+    size_t bat = 0;
+    for (Request* r : adv) {
+        if (e != cudaSuccess) break;
+        if (r->k < r->n) {
+            e = cudaMemcpyAsync(hback + bat, base + r->off + r->c_job, sizeof(bs_job), cudaMemcpyDeviceToHost,
+                                s->stream);
+            bat += sizeof(bs_job);
+        } else {
+            e = cudaMemcpyAsync(hback + bat, base + r->off + r->c_cnt, (size_t)r->m_det * 4, cudaMemcpyDeviceToHost,
+                                s->stream);
+            bat += (size_t)r->m_det * 4;
+        }
     }
     int status = 0;
     if (e == cudaSuccess) e = cudaMemcpyAsync(hp + desc_bytes, ctl + 64, 4, cudaMemcpyDeviceToHost, s->stream);
@@ -393,8 +522,24 @@ int run_tick(bs_server* s, std::vector<Request*>& admit, std::vector<Request*>& 
     std::memcpy(&status, hp + desc_bytes, 4);
     if (status != BS_STATUS_OK) return bs::fail(BS_ECUDA, "server walk status %d", status);
     for (size_t i = 0; i < walk.size(); ++i) walk_req[i]->done += walk[i].ntasks;
+    bat = 0;
+    for (Request* r : adv) {
+        if (r->k < r->n) {
+            std::memcpy(&r->job_host, hback + bat, sizeof(bs_job));
+            bat += sizeof(bs_job);
+            r->k += 1;  // the planned job is step k + 1's; its row is drawn when it completes
+            r->ntasks = r->job_host.ntasks;
+            r->done = 0;
+            r->prec = r->job_host.prec;
+        } else {
+            r->counts.assign(reinterpret_cast<const int*>(hback + bat), reinterpret_cast<const int*>(hback + bat) + r->m_det);
+            bat += (size_t)r->m_det * 4;
+            r->chain_done = true;
+        }
+    }
     at = 0;
     for (Request* r : fin_req) {
+        if (r->chain) continue;
         const double2* v = reinterpret_cast<const double2*>(hout + at);
         at += (size_t)r->ncols * 16;
         if (r->kind == BS_KIND_PERM) {
@@ -461,10 +606,12 @@ void engine_loop(bs_server* s) {
         }
         std::vector<Request*> still;
         for (Request* r : s->active) {
-            if (r->done == r->ntasks) {
+            const bool complete = r->chain ? r->chain_done : r->done == r->ntasks;
+            if (complete || r->cancel) {
+                // between ticks: no kernel of this request is in flight
                 s->arena.release(r->off, r->bytes);
                 s->free_slots.push_back(r->slot);
-                finish(s, r, 1);
+                finish(s, r, complete ? 1 : BS_ECANCELED);
             } else {
                 still.push_back(r);
             }
@@ -598,6 +745,7 @@ int64_t bs_server_submit(bs_server* s, int kind, const bs_c128* A, int rows, int
 
 static int take_result(bs_server* s, Request* r, bs_c128* out, int out_len, double* latency_s) {
     int st = r->status;
+    if (r->chain) return bs::fail(BS_EINVAL, "ticket %lld is a sampling request: use bs_server_wait_sample", (long long)r->id);
     if (st == 1) {
         const int need = (int)r->result.size();
         if (out_len < need) return bs::fail(BS_EINVAL, "output holds %d values, %d needed", out_len, need);
@@ -606,7 +754,22 @@ static int take_result(bs_server* s, Request* r, bs_c128* out, int out_len, doub
     }
     s->all.erase(r->id);
     delete r;
-    return st == 1 ? BS_OK : bs::fail(st, "request failed: %s", s->fatal.c_str());
+    return st == 1 ? BS_OK
+                   : bs::fail(st, "request %s", st == BS_ECANCELED ? "cancelled" : ("failed: " + s->fatal).c_str());
+}
+
+static int take_counts(bs_server* s, Request* r, int* counts, int len, double* latency_s) {
+    int st = r->status;
+    if (!r->chain) return bs::fail(BS_EINVAL, "ticket %lld is not a sampling request", (long long)r->id);
+    if (st == 1) {
+        if (len < r->m_det) return bs::fail(BS_EINVAL, "output holds %d counts, %d needed", len, r->m_det);
+        if (counts) std::memcpy(counts, r->counts.data(), sizeof(int) * (size_t)r->m_det);
+        if (latency_s) *latency_s = std::chrono::duration<double>(r->t_done - r->t_submit).count();
+    }
+    s->all.erase(r->id);
+    delete r;
+    return st == 1 ? BS_OK
+                   : bs::fail(st, "request %s", st == BS_ECANCELED ? "cancelled" : ("failed: " + s->fatal).c_str());
 }
 
 int bs_server_poll(bs_server* s, int64_t ticket, bs_c128* out, int out_len, double* latency_s) {
@@ -629,6 +792,110 @@ int bs_server_wait(bs_server* s, int64_t ticket, bs_c128* out, int out_len, doub
     return take_result(s, r, out, out_len, latency_s);
 }
 
+int64_t bs_server_submit_sample(bs_server* s, const bs_c128* U, int m_rows, int m_cols, int ld,
+                                const int* input_occupation, uint64_t seed, uint64_t sample, int m_detected) {
+    if (!s) return bs::fail(BS_EINVAL, "server is NULL");
+    if (!U || !input_occupation) return bs::fail(BS_EINVAL, "NULL pointer");
+    if (m_rows <= 0 || m_cols <= 0 || ld < m_cols) return bs::fail(BS_EINVAL, "bad interferometer size");
+    if (m_rows > 8192) return bs::fail(BS_EINVAL, "at most 8192 output modes are supported");
+    Request* r = new Request();
+    r->chain = true;
+    r->kind = BS_KIND_MINORS;
+    for (int i = 0; i < m_cols; ++i) {
+        if (input_occupation[i] < 0) {
+            delete r;
+            return bs::fail(BS_EINVAL, "negative occupation in mode %d", i);
+        }
+        for (int t = 0; t < input_occupation[i]; ++t) r->inputs.push_back(i);
+    }
+    r->n = (int)r->inputs.size();
+    if (r->n > BS_MAX_N) {
+        delete r;
+        return bs::fail(BS_EINVAL, "n = %d photons exceeds the limit %d", r->n, BS_MAX_N);
+    }
+    r->m_rows = m_rows;
+    r->m_cols = m_cols;
+    r->m_det = (m_detected <= 0 || m_detected > m_rows) ? m_rows : m_detected;
+    r->seed = seed;
+    r->sample = sample;
+    r->k = 1;
+    r->rows = m_rows;
+    r->cols = m_cols;
+    r->ncols = r->n;
+    r->t_submit = clock_type::now();
+    if (r->n > 0) {
+        r->mat.resize((size_t)m_rows * m_cols);
+        for (int i = 0; i < m_rows; ++i)
+            std::memcpy(&r->mat[(size_t)i * m_cols], U + (size_t)i * ld, sizeof(bs_c128) * m_cols);
+        // task partial slots of the largest step (C <= 2^(n-2)) over the
+        // kernels the mode may use (chunks per task >= 16 FP64, 8 FP32, 4 DF)
+        const uint64_t cmax = r->n >= 2 ? (1ull << (r->n - 2)) : 1ull;
+        uint64_t ts = 2 * BS_TARGET_TASKS_MANY + 1;
+        const int precs_mixed[2] = {BS_PREC_FP32, BS_MIXED_FALLBACK_PREC};
+        const int prec_one = s->mode == BS_DF64 ? BS_PREC_DF : BS_PREC_FP64;
+        const int np = s->mode == BS_MIXED ? 2 : 1;
+        for (int i = 0; i < np; ++i) {
+            const int q = s->mode == BS_MIXED ? precs_mixed[i] : prec_one;
+            const uint64_t cpt_min = q == BS_PREC_FP64 ? 16 : q == BS_PREC_FP32 ? 8 : 4;
+            ts = std::max<uint64_t>(ts, cmax / (cpt_min << kChainLog2Max) + 2);
+        }
+        r->tasks_stride = ts;
+        r->bytes = chain_layout(*r);
+    }
+    std::lock_guard<std::mutex> lk(s->mu);
+    r->id = s->next_id++;
+    s->all[r->id] = r;
+    s->submitted++;
+    if (r->n == 0) {  // no photons: the empty pattern
+        r->counts.assign(r->m_det, 0);
+        r->chain_done = true;
+        finish(s, r, 1);
+        s->cv_done.notify_all();
+        return r->id;
+    }
+    s->waiting.push_back(r);
+    s->cv_work.notify_one();
+    return r->id;
+}
+
+int bs_server_poll_sample(bs_server* s, int64_t ticket, int* counts, int len, double* latency_s) {
+    if (!s) return bs::fail(BS_EINVAL, "server is NULL");
+    std::lock_guard<std::mutex> lk(s->mu);
+    auto it = s->all.find(ticket);
+    if (it == s->all.end()) return bs::fail(BS_EINVAL, "unknown ticket %lld", (long long)ticket);
+    if (it->second->status == 0) return 0;
+    int rc = take_counts(s, it->second, counts, len, latency_s);
+    return rc == BS_OK ? 1 : rc;
+}
+
+int bs_server_wait_sample(bs_server* s, int64_t ticket, int* counts, int len, double* latency_s) {
+    if (!s) return bs::fail(BS_EINVAL, "server is NULL");
+    std::unique_lock<std::mutex> lk(s->mu);
+    auto it = s->all.find(ticket);
+    if (it == s->all.end()) return bs::fail(BS_EINVAL, "unknown ticket %lld", (long long)ticket);
+    Request* r = it->second;
+    s->cv_done.wait(lk, [&] { return r->status != 0; });
+    return take_counts(s, r, counts, len, latency_s);
+}
+
+int bs_server_cancel(bs_server* s, int64_t ticket) {
+    if (!s) return bs::fail(BS_EINVAL, "server is NULL");
+    std::lock_guard<std::mutex> lk(s->mu);
+    auto it = s->all.find(ticket);
+    if (it == s->all.end()) return bs::fail(BS_EINVAL, "unknown ticket %lld", (long long)ticket);
+    Request* r = it->second;
+    if (r->status != 0) return bs::fail(BS_EINVAL, "ticket %lld has already finished", (long long)ticket);
+    auto w = std::find(s->waiting.begin(), s->waiting.end(), r);
+    if (w != s->waiting.end()) {  // not admitted: nothing on the device
+        s->waiting.erase(w);
+        finish(s, r, BS_ECANCELED);
+        s->cv_done.notify_all();
+        return BS_OK;
+    }
+    r->cancel = true;  // the engine releases it after the current tick
+    return BS_OK;
+}
+
 int bs_server_get_stats(bs_server* s, bs_server_stats* out) {
     if (!s || !out) return bs::fail(BS_EINVAL, "NULL argument");
     std::lock_guard<std::mutex> lk(s->mu);
@@ -640,6 +907,10 @@ int bs_server_get_stats(bs_server* s, bs_server_stats* out) {
     out->busy_s = s->busy_s;
     out->max_resident = s->max_resident;
     out->mem_peak_bytes = s->arena.peak();
+    out->mem_in_use_bytes = s->arena.used();
+    out->resident = (int)s->active.size();
+    out->waiting = (int)s->waiting.size();
+    out->cancelled = s->cancelled;
     std::vector<double> l = s->latencies_ms;
     if (!l.empty()) {
         std::sort(l.begin(), l.end());
