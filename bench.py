@@ -69,6 +69,7 @@ def parse():
     ap.add_argument("--serving-chains", type=int, default=64,
                     help="chains of the serving side measurement on the headline line (0: skip)")
     ap.add_argument("--lossy-samples", type=int, default=20, help="samples of the lossy workload")
+    ap.add_argument("--lossy-modes", default="mixed,df", help="modes of the lossy workload, comma-separated")
     return ap.parse_args()
 
 
@@ -745,18 +746,29 @@ def run_serving(args):
 
 def run_lossy(args):
     """n = 40 photons, m = 60, eta = 0.5: the 100 x 40 isometry, only the
-    first 60 outputs counted; seconds per sample (MIXED)."""
+    first 60 outputs counted; seconds per sample in each of --lossy-modes
+    (every chain draws all 40 photons, loss modes included)."""
     import numpy as np
     import paper_2309_07027_gb300 as bs
     import synthetic as S
     v, mdet = S.config_lossy()
     ctx = bs.Context(0)
     ns = max(1, args.lossy_samples)
-    t0 = time.perf_counter()
-    counts = ctx.sample_ex(v, np.ones(v.shape[1], np.int32), ns, seed=5, m_detected=mdet, mode=bs.BS_MIXED)
-    dt = time.perf_counter() - t0
-    print(json.dumps({"workload": "lossy_n40_m60_eta0.5", "metric": "s/sample", "value": dt / ns, "samples": ns,
-                      "detected_mean": float(counts.sum(1).mean()),
+    mode_of = {"fp64": bs.BS_FP64, "mixed": bs.BS_MIXED, "df": bs.BS_DF64}
+    res = {}
+    for name in args.lossy_modes.split(","):
+        t0 = time.perf_counter()
+        counts = ctx.sample_ex(v, np.ones(v.shape[1], np.int32), ns, seed=5, m_detected=mdet, mode=mode_of[name])
+        dt = time.perf_counter() - t0
+        res[name] = {"s_per_sample": dt / ns, "samples": ns, "detected_mean": float(counts.sum(1).mean()),
+                     "counts": counts.tolist() if ns <= 4 else None}
+    same = None
+    if "mixed" in res and "df" in res and res["mixed"]["counts"] is not None and res["df"]["counts"] is not None:
+        same = float(np.mean([a == b for a, b in zip(res["mixed"]["counts"], res["df"]["counts"])]))
+    for r in res.values():
+        r.pop("counts")
+    print(json.dumps({"workload": "lossy_n40_m60_eta0.5", "metric": "s/sample", "modes": res,
+                      "samples_equal_mixed_df": same,
                       "paper_context_s_per_sample": {"ideal_4_fpga": 80, "lossy_4_fpga": 360}}), flush=True)
     return 0
 
