@@ -92,6 +92,33 @@ __device__ __forceinline__ ddv dd_add(ddv a, ddv b) {
     return r;
 }
 
+// Double-double addition in Sum2 form (Ogita, Rump and Oishi 2005): TwoSum
+// of the high parts, its error and both low parts added in double, one
+// renormalisation; 11 FP64 operations instead of 20.  Sums of many terms
+// formed this way are as accurate as summation in twice double precision,
+// which is what the task and cross-lane combinations need (the FP64 pipe is
+// 1/64 of the FP32 pipe here, and a small job's latency is its warps' FP64
+// instruction count).
+__device__ __forceinline__ ddv dd_add_sum2(ddv a, ddv b) {
+    const double s = __dadd_rn(a.hi, b.hi);
+    const double bb = __dsub_rn(s, a.hi);
+    double e = __dadd_rn(__dsub_rn(a.hi, __dsub_rn(s, bb)), __dsub_rn(b.hi, bb));
+    e = __dadd_rn(e, __dadd_rn(a.lo, b.lo));
+    ddv r;
+    r.hi = __dadd_rn(s, e);
+    r.lo = __dsub_rn(e, __dsub_rn(r.hi, s));
+    return r;
+}
+
+// Sum2 accumulation of single doubles: s holds the rounded sum, e the
+// running sum of the TwoSum errors.
+__device__ __forceinline__ void sum2_acc(double& s, double& e, double x) {
+    const double t = __dadd_rn(s, x);
+    const double bb = __dsub_rn(t, s);
+    e = __dadd_rn(e, __dadd_rn(__dsub_rn(s, __dsub_rn(t, bb)), __dsub_rn(x, bb)));
+    s = t;
+}
+
 struct ffv {
     float hi, lo;
 };
@@ -150,8 +177,8 @@ __device__ __forceinline__ void warp_reduce_zdd(ddv& re, ddv& im) {
     for (int off = 16; off > 0; off >>= 1) {
         ddv ore = shfl_down_dd(re, off);
         ddv oim = shfl_down_dd(im, off);
-        re = dd_add(re, ore);
-        im = dd_add(im, oim);
+        re = dd_add_sum2(re, ore);
+        im = dd_add_sum2(im, oim);
     }
 }
 
@@ -402,7 +429,7 @@ __device__ __forceinline__ void minors_fold_fp64(cx<double>* __restrict__ sm_acc
 // with the per-column accumulators in shared memory, [col][thread]: plain
 // double runs of FOLD addends, folded into double-double totals (a second
 // [col][thread] array of {re hi, re lo, im hi, im lo}) that the lanes then
-// combine in double-double.  Each
+// combine in Sum2 form (below).  Each
 // lane holds half the column sums and suffixes of the one-lane form, so twice
 // as many warps fit on an SM and the dependent product chains are half as
 // long, for the same FP64 work plus one real-by-complex product per lane and
@@ -526,21 +553,37 @@ __device__ void walk_task_minors_fp64(const bs_job& jb, const cx<double>* __rest
                 c[t].im = bfma(cf, v.im, c[t].im);
             }
     }
-    minors_fold_fp64<H>(sm_acc, sm_tot, stride, KH);
-    // The 16 chunk totals per column (double-double) are combined in
-    // double-double over lanes of equal parity (fixed butterfly order); the
-    // partials of different tasks are summed in twice double precision by
-    // the reduce kernel.  Lane h < 2 ends with the sums of its columns.
-    for (int t = 0; t < H; ++t) {
-        const double4 v = BS_OWN(t) ? sm_tot[t * stride] : make_double4(0.0, 0.0, 0.0, 0.0);
-        ddv re = {v.x, v.y}, im = {v.z, v.w};
-#pragma unroll
-        for (int off = 16; off > 1; off >>= 1) {
-            re = dd_add(re, shfl_down_dd(re, off));
-            im = dd_add(im, shfl_down_dd(im, off));
+    // Combine the 16 chunks of each column in Sum2 form: lane 16 h + u sums
+    // column t = u + 16 r of half h (rounds r) over lanes 2p + h, reading
+    // their double-double totals and their last plain runs from shared
+    // memory; the reduce kernel sums the task partials the same way.  The
+    // warp spends about 32 x 15 FP64 operations per 16 columns here, where a
+    // final fold and a shuffle tree of double-double additions took about
+    // 200 per column (a small job's latency is its FP64 instruction count).
+    __syncwarp();
+    const cx<double>* wacc = sm_acc - lane;  // this warp's thread 0
+    const double4* wtot = sm_tot - lane;
+    const int hh = lane >> 4;
+    const int Kh = hh ? K - Hr : Hr;
+#pragma unroll 1
+    for (int t = lane & 15; t < Kh; t += 16) {
+        double sr = 0.0, er = 0.0, si = 0.0, ei = 0.0;
+#pragma unroll 4
+        for (int p = 0; p < 16; ++p) {
+            const int th = 2 * p + hh;
+            const double4 v = wtot[t * stride + th];
+            const cx<double> r = wacc[t * stride + th];
+            sum2_acc(sr, er, v.x);
+            sum2_acc(sr, er, r.re);
+            er = __dadd_rn(er, v.y);
+            sum2_acc(si, ei, v.z);
+            sum2_acc(si, ei, r.im);
+            ei = __dadd_rn(ei, v.w);
         }
-        if (lane < 2 && t < KH) store_partial(partials + jb.partial_off + (int64_t)local * K + cbase + t, re, im);
+        const ddv re = dd_add_d(ddv{sr, 0.0}, er), im = dd_add_d(ddv{si, 0.0}, ei);
+        store_partial(partials + jb.partial_off + (int64_t)local * K + hh * Hr + t, re, im);
     }
+    __syncwarp();  // the next task's initialisation overwrites the arrays
 #undef BS_OWN
 }
 
