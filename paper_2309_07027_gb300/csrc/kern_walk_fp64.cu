@@ -36,9 +36,9 @@ __global__ void __launch_bounds__(kMinorsBlock) walk_fp64_minors_kernel(WalkArgs
     extern __shared__ double2 smem_fp64[];
     const int lane = threadIdx.x & 31;
     const int stride = blockDim.x;
-    // [col][thread] plain-double runs, then [col][thread] double-double totals
+    // [col][thread] plain-double runs, then per warp KB double-double totals
     cx<double>* sm_acc = reinterpret_cast<cx<double>*>(smem_fp64) + threadIdx.x;
-    double4* sm_tot = reinterpret_cast<double4*>(smem_fp64 + (size_t)(KB / 2) * stride) + threadIdx.x;
+    double4* wtot = reinterpret_cast<double4*>(smem_fp64 + (size_t)(KB / 2) * stride) + (threadIdx.x >> 5) * KB;
     const bs_job* __restrict__ jobs = a.jobs;
     const cx<double>* __restrict__ data = static_cast<const cx<double>*>(a.data);
     const unsigned long long total = task_total(a);
@@ -53,7 +53,7 @@ __global__ void __launch_bounds__(kMinorsBlock) walk_fp64_minors_kernel(WalkArgs
             continue;
         }
         walk_task_minors_fp64<KB>(jb, data, a.meta + BS_META_RADIX(jb), a.partials, (uint32_t)(t - jb.task_begin) + jb.task_offset,
-                                  lane, sm_acc, sm_tot, stride);
+                                  lane, sm_acc, wtot, stride);
     }
 }
 
@@ -83,8 +83,9 @@ static cudaError_t run_perm(const WalkArgs& a, cudaStream_t s) {
 
 template <int KB>
 static cudaError_t run_minors(const WalkArgs& a, cudaStream_t s) {
-    // per thread and owned column: a 16-byte run and a 32-byte double-double total
-    size_t smem = (size_t)kMinorsBlock * (KB / 2) * (sizeof(cx<double>) + sizeof(double4));
+    // per thread and owned column a 16-byte run; per warp and column a
+    // 32-byte double-double total
+    size_t smem = (size_t)kMinorsBlock * (KB / 2) * sizeof(cx<double>) + (size_t)(kMinorsBlock / 32) * KB * sizeof(double4);
     cudaError_t e =
         cudaFuncSetAttribute(walk_fp64_minors_kernel<KB>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;

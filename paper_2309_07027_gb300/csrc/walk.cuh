@@ -400,20 +400,35 @@ __device__ void walk_task_perm_fp64(const bs_job& jb, const cx<double>* __restri
     if (lane == 0) store_partial(partials + jb.partial_off + local, sre, sim);
 }
 
-// Fold the plain-double runs of a lane's columns (t < KH) into their
-// double-double totals and clear the runs.
-template <int H>
-__device__ __forceinline__ void minors_fold_fp64(cx<double>* __restrict__ sm_acc, double4* __restrict__ sm_tot,
-                                                 int stride, int KH) {
-    // a rolled loop: its few temporaries stay out of the walk's registers
+// Fold the plain-double runs of the warp's 16 chunks into the warp's
+// double-double column totals and clear the runs: lane 16 h + u takes
+// column t = u + 16 r of half h (rounds r), sums the runs of lanes 2p + h
+// in Sum2 form and adds them to the total of that column (only it touches
+// that total and those runs).  wacc: the warp's runs ([col][thread], thread
+// 0 of the warp at column 0); wtot: its K totals {re hi, re lo, im hi, im lo}.
+__device__ __forceinline__ void minors_fold_fp64(cx<double>* __restrict__ wacc, double4* __restrict__ wtot,
+                                                 int stride, int lane, int K, int Hr, int H) {
+    const int hh = lane >> 4;
+    const int Kh = hh ? K - Hr : Hr;
+    __syncwarp();
 #pragma unroll 1
-    for (int t = 0; t < KH; ++t) {
-        const cx<double> a = sm_acc[t * stride];
-        const double4 v = sm_tot[t * stride];
-        const ddv re = dd_add_d(ddv{v.x, v.y}, a.re), im = dd_add_d(ddv{v.z, v.w}, a.im);
-        sm_tot[t * stride] = make_double4(re.hi, re.lo, im.hi, im.lo);
-        sm_acc[t * stride] = cx<double>{0.0, 0.0};
+    for (int t = lane & 15; t < Kh && t < H; t += 16) {
+        double sr = 0.0, er = 0.0, si = 0.0, ei = 0.0;
+#pragma unroll 4
+        for (int p = 0; p < 16; ++p) {
+            cx<double>* q = wacc + t * stride + 2 * p + hh;
+            const cx<double> r = *q;
+            *q = cx<double>{0.0, 0.0};
+            sum2_acc(sr, er, r.re);
+            sum2_acc(si, ei, r.im);
+        }
+        double4* w = wtot + hh * Hr + t;
+        const double4 v = *w;
+        const ddv re = dd_add_sum2(ddv{v.x, v.y}, dd_add_d(ddv{sr, 0.0}, er));
+        const ddv im = dd_add_sum2(ddv{v.z, v.w}, dd_add_d(ddv{si, 0.0}, ei));
+        *w = make_double4(re.hi, re.lo, im.hi, im.lo);
     }
+    __syncwarp();
 }
 
 // ---------------------------------------------------------------- one task: minors, FP64
@@ -427,22 +442,25 @@ __device__ __forceinline__ void minors_fold_fp64(cx<double>* __restrict__ sm_acc
 //   3. runs the prefix pass from X = (+-W) Q_partner:
 //          acc[l] += X * prefix_l * suffix_l,
 // with the per-column accumulators in shared memory, [col][thread]: plain
-// double runs of FOLD addends, folded into double-double totals (a second
-// [col][thread] array of {re hi, re lo, im hi, im lo}) that the lanes then
-// combine in Sum2 form (below).  Each
-// lane holds half the column sums and suffixes of the one-lane form, so twice
-// as many warps fit on an SM and the dependent product chains are half as
-// long, for the same FP64 work plus one real-by-complex product per lane and
-// addend.  All lanes run the warp's longest chunk length (a finished or
-// absent chunk continues with weight 0), so the shuffle has the full warp.  A
-// warp task covers 16 chunks.
+// double runs of FOLD addends, which the warp folds, column by column and
+// transposed across lanes, into one double-double total per column of the
+// warp (minors_fold_fp64).  Each lane holds half the column sums and
+// suffixes of the one-lane form, so more warps fit on an SM and the
+// dependent product chains are half as long, for the same FP64 work plus
+// one real-by-complex product per lane and addend; with the totals per warp
+// rather than per thread, shared memory (16 bytes per owned column and
+// thread) no longer limits the CTAs per SM before registers do.  All lanes
+// run the warp's longest chunk length (a finished or absent chunk continues
+// with weight 0), so the shuffle has the full warp.  A warp task covers 16
+// chunks; its last fold leaves the task's sums in the warp's totals, which
+// lanes 16 h + u write as the task's double-double partials.
 template <int KB>
 __device__ void walk_task_minors_fp64(const bs_job& jb, const cx<double>* __restrict__ data,
                                       const int* __restrict__ radix, bs_zdd* __restrict__ partials, uint32_t local,
-                                      int lane, cx<double>* __restrict__ sm_acc, double4* __restrict__ sm_tot,
+                                      int lane, cx<double>* __restrict__ sm_acc, double4* __restrict__ wtot,
                                       int stride) {
     // fold interval: each lane spends about 7 FP64 operations per column and
-    // addend, a fold about 20 per column, so folds every 256 addends cost
+    // addend, a fold about 16 per column, so folds every 256 addends cost
     // about 1 % (every 64: 4.8 %, measured on the 29 x 30 minors)
     constexpr uint32_t FOLD = 256;
     constexpr int H = KB / 2;  // most columns a lane can own
@@ -454,13 +472,12 @@ __device__ void walk_task_minors_fp64(const bs_job& jb, const cx<double>* __rest
     const int KH = half ? K - Hr : Hr;  // own columns, >= 1 for K >= 2
     const cx<double>* c0 = data + jb.data_off;
     const cx<double>* a2 = c0 + KP;
+    cx<double>* wacc = sm_acc - lane;  // this warp's thread 0
 #define BS_OWN(t) ((t) < H - 2 || (t) < KH)
 #pragma unroll
     for (int t = 0; t < H; ++t)
-        if (BS_OWN(t)) {
-            sm_acc[t * stride] = cx<double>{0.0, 0.0};
-            sm_tot[t * stride] = make_double4(0.0, 0.0, 0.0, 0.0);
-        }
+        if (BS_OWN(t)) sm_acc[t * stride] = cx<double>{0.0, 0.0};
+    for (int t = lane; t < K; t += 32) wtot[t] = make_double4(0.0, 0.0, 0.0, 0.0);
     const uint64_t i0_own = ((uint64_t)local * 16u + (uint64_t)(lane >> 1)) << jb.log2L;
     const bool has = i0_own < jb.C;
     const uint64_t i0 = has ? i0_own : 0ull;
@@ -534,7 +551,7 @@ __device__ void walk_task_minors_fp64(const bs_job& jb, const cx<double>* __rest
                 sm_acc[t * stride] = a;
                 if (BS_OWN(t + 1)) pre = cmul(pre, c[t]);
             }
-        if (((s + 1u) & (FOLD - 1u)) == 0) minors_fold_fp64<H>(sm_acc, sm_tot, stride, KH);
+        if (((s + 1u) & (FOLD - 1u)) == 0) minors_fold_fp64(wacc, wtot, stride, lane, K, Hr, H);
         if (s + 1 >= len) {  // this lane's chunk is done: weight 0 from here on
             ws = 0.0;
             continue;
@@ -553,37 +570,14 @@ __device__ void walk_task_minors_fp64(const bs_job& jb, const cx<double>* __rest
                 c[t].im = bfma(cf, v.im, c[t].im);
             }
     }
-    // Combine the 16 chunks of each column in Sum2 form: lane 16 h + u sums
-    // column t = u + 16 r of half h (rounds r) over lanes 2p + h, reading
-    // their double-double totals and their last plain runs from shared
-    // memory; the reduce kernel sums the task partials the same way.  The
-    // warp spends about 32 x 15 FP64 operations per 16 columns here, where a
-    // final fold and a shuffle tree of double-double additions took about
-    // 200 per column (a small job's latency is its FP64 instruction count).
-    __syncwarp();
-    const cx<double>* wacc = sm_acc - lane;  // this warp's thread 0
-    const double4* wtot = sm_tot - lane;
-    const int hh = lane >> 4;
-    const int Kh = hh ? K - Hr : Hr;
-#pragma unroll 1
-    for (int t = lane & 15; t < Kh; t += 16) {
-        double sr = 0.0, er = 0.0, si = 0.0, ei = 0.0;
-#pragma unroll 4
-        for (int p = 0; p < 16; ++p) {
-            const int th = 2 * p + hh;
-            const double4 v = wtot[t * stride + th];
-            const cx<double> r = wacc[t * stride + th];
-            sum2_acc(sr, er, v.x);
-            sum2_acc(sr, er, r.re);
-            er = __dadd_rn(er, v.y);
-            sum2_acc(si, ei, v.z);
-            sum2_acc(si, ei, r.im);
-            ei = __dadd_rn(ei, v.w);
-        }
-        const ddv re = dd_add_d(ddv{sr, 0.0}, er), im = dd_add_d(ddv{si, 0.0}, ei);
-        store_partial(partials + jb.partial_off + (int64_t)local * K + hh * Hr + t, re, im);
+    // the last runs into the totals, then the task's partials (the reduce
+    // kernel sums the partials of all tasks in Sum2 form)
+    minors_fold_fp64(wacc, wtot, stride, lane, K, Hr, H);
+    for (int t = lane; t < K; t += 32) {
+        const double4 v = wtot[t];
+        store_partial(partials + jb.partial_off + (int64_t)local * K + t, ddv{v.x, v.y}, ddv{v.z, v.w});
     }
-    __syncwarp();  // the next task's initialisation overwrites the arrays
+    __syncwarp();  // the next task's initialisation overwrites the totals
 #undef BS_OWN
 }
 
