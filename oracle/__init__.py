@@ -30,10 +30,10 @@ def lib():
         ip = C.POINTER(C.c_int)
         for name in ("orc_perm_bruteforce", "orc_ryser_gray"):
             getattr(L, name).argtypes = [C.c_int, dp, C.c_int, dp]
-        for name in ("orc_bbfg_gray", "orc_bbfg_direct"):
+        for name in ("orc_bbfg_gray", "orc_bbfg_direct", "orc_bbfg_gray_fp64"):
             getattr(L, name).argtypes = [C.c_int, C.c_int, dp, C.c_int, dp]
         for name in ("orc_perm_mult", "orc_perm_expanded", "orc_minors", "orc_bbfg_mult_extremes",
-                     "orc_perm_mult_abs", "orc_perm_mult_fp64"):
+                     "orc_perm_mult_abs", "orc_perm_mult_fp64", "orc_minors_fp64"):
             getattr(L, name).argtypes = [C.c_int, C.c_int, dp, C.c_int, ip, ip, dp]
         L.orc_gray_sequence.argtypes = [C.c_int, C.POINTER(C.c_uint64)]
         L.orc_ryser_exact_gauss.argtypes = [C.c_int, C.POINTER(C.c_int64), C.POINTER(C.c_int64)]
@@ -95,6 +95,16 @@ def bbfg_gray(a):
     out = np.zeros(4)
     _chk(lib().orc_bbfg_gray(r, c, _dp(a.view(np.float64)), c, _dp(out)), "bbfg_gray")
     return _dd_value(out)
+
+
+def bbfg_gray_fp64(a):
+    """The bbfg_gray walk in plain double arithmetic (the plain-FP64 CPU
+    form of Eq. (bbfg), a timing baseline)."""
+    a = _mat(a)
+    r, c = a.shape
+    out = np.zeros(2)
+    _chk(lib().orc_bbfg_gray_fp64(r, c, _dp(a.view(np.float64)), c, _dp(out)), "bbfg_gray_fp64")
+    return complex(out[0], out[1])
 
 
 def gray_sequence(bits):
@@ -199,6 +209,14 @@ def minors(a, row_mult, col_mult):
     val = out[:, 0] + 1j * out[:, 2]
     tail = out[:, 1] + 1j * out[:, 3]
     return val, tail
+
+
+def minors_fp64(a, row_mult, col_mult):
+    """Laplace minors as minors(), each by the plain-double Gray walk
+    (timing baseline)."""
+    K = np.asarray(a).shape[1]
+    out = _mult_call("orc_minors_fp64", a, row_mult, col_mult, 2 * K).reshape(K, 2)
+    return out[:, 0] + 1j * out[:, 1]
 
 
 def perm_mult_fp64(a, row_mult, col_mult):

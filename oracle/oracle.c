@@ -192,6 +192,50 @@ int orc_bbfg_gray(int r, int c, const double* A, int ld, double* out) {
     return 0;
 }
 
+/* The same Gray walk in plain double arithmetic (no compensation, no
+ * double-double): the plain-FP64 CPU form of Eq. (bbfg), a timing baseline
+ * beside the double-double walk above.  out = {re, im}. */
+int orc_bbfg_gray_fp64(int r, int c, const double* A, int ld, double* out) {
+    if (r < 0 || c < 0 || r > 40 || c > 64) return -1;
+    if (r == 0) {
+        out[0] = (c == 0) ? 1.0 : 0.0;
+        out[1] = 0.0;
+        return 0;
+    }
+    double sr[64], si[64];
+    for (int j = 0; j < c; ++j) {
+        sr[j] = 0.0; si[j] = 0.0;
+        for (int i = 0; i < r; ++i) { sr[j] += A[2 * ((size_t)i * ld + j)]; si[j] += A[2 * ((size_t)i * ld + j) + 1]; }
+    }
+    double ar = 0.0, ai = 0.0;
+    uint64_t count = (uint64_t)1 << (r - 1);
+    uint64_t gray_prev = 0;
+    int sign = 1;
+    for (uint64_t g = 0; g < count; ++g) {
+        if (g > 0) {
+            int t = __builtin_ctzll(g);
+            int row = t + 1;
+            double coef = ((gray_prev >> t) & 1u) ? 2.0 : -2.0;
+            for (int j = 0; j < c; ++j) {
+                sr[j] += coef * A[2 * ((size_t)row * ld + j)];
+                si[j] += coef * A[2 * ((size_t)row * ld + j) + 1];
+            }
+            gray_prev ^= (uint64_t)1 << t;
+            sign = -sign;
+        }
+        double pr = 1.0, pi = 0.0;
+        for (int j = 0; j < c; ++j) {
+            const double t = pr * sr[j] - pi * si[j];
+            pi = pr * si[j] + pi * sr[j];
+            pr = t;
+        }
+        if (sign > 0) { ar += pr; ai += pi; } else { ar -= pr; ai -= pi; }
+    }
+    out[0] = ldexp(ar, 1 - r);
+    out[1] = ldexp(ai, 1 - r);
+    return 0;
+}
+
 /* The sequence of Gray codes visited by orc_bbfg_gray's walk over `bits`
  * delta bits (bit t <-> row t+1; 1 means delta = -1), reconstructed from the
  * same flip rule: at index g the bit at the lowest set bit of g changes. */
@@ -646,6 +690,26 @@ int orc_minors(int R, int K, const double* A, int ld, const int* M, const int* N
         int n = 0;
         rc = expand(R, K, A, ld, M, N, l, E, &n);
         if (rc == 0) rc = orc_bbfg_gray(n, n, E, n, out + 4 * l);
+    }
+    free(E);
+    return rc;
+}
+
+/* Laplace minors as orc_minors, each by the plain-double walk
+ * orc_bbfg_gray_fp64 (timing baseline).  out: K x {re, im}. */
+int orc_minors_fp64(int R, int K, const double* A, int ld, const int* M, const int* N, double* out) {
+    int sm = 0, sn = 0;
+    for (int k = 0; k < R; ++k) { if (M[k] < 0) return -1; sm += M[k]; }
+    for (int j = 0; j < K; ++j) { if (N[j] < 0) return -1; sn += N[j]; }
+    if (sm != sn - 1) return -2;
+    double* E = (double*)malloc(sizeof(double) * 2 * 60 * 60);
+    if (!E) return -3;
+    int rc = 0;
+    for (int l = 0; l < K && rc == 0; ++l) {
+        if (N[l] == 0) { out[2 * l] = 0.0; out[2 * l + 1] = 0.0; continue; }
+        int n = 0;
+        rc = expand(R, K, A, ld, M, N, l, E, &n);
+        if (rc == 0) rc = orc_bbfg_gray_fp64(n, n, E, n, out + 2 * l);
     }
     free(E);
     return rc;

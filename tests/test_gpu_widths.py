@@ -259,6 +259,48 @@ def test_sampler_rows_match_oracle_at_workload_size(ctx, oracle_trace, mode):
     assert departures <= 1, departures
 
 
+def _check_rows(rows, ref_rows, ref_margin, steps, margin, max_departures):
+    departures = 0
+    for s in range(len(ref_rows)):
+        diff = np.nonzero(rows[s, :steps] != ref_rows[s, :steps])[0]
+        if len(diff) == 0:
+            continue
+        k = int(diff[0])
+        assert ref_margin[s, k] < margin, (s, k, rows[s, :k + 1], ref_rows[s, :k + 1], ref_margin[s, k])
+        departures += 1
+    assert departures <= max_departures, departures
+
+
+@pytest.mark.parametrize("mode", [0, 1, 2])
+def test_sampler_rows_match_oracle_in_the_bench_launch(ctx, oracle_trace, mode):
+    """The benchmark's launch configuration: 200 chains of the n = 30, m = 60
+    workload advance together (one walk launch per precision and step for
+    all of them).  A chain's random numbers depend only on (seed, sample
+    index), so chains 0..7 of the 200 are the oracle's chains 0..7: their
+    first 18 rows match, with the same departure rule."""
+    u, occ, ref_rows, ref_margin = oracle_trace
+    counts, rows = ctx.sample_trace(u, occ, 200, seed=7, mode=mode)
+    assert rows.shape == (200, 30) and np.all(counts.sum(axis=1) == 30)
+    _check_rows(rows[:TRACE_SAMPLES], ref_rows, ref_margin, TRACE_STEPS, MARGIN[mode], 1)
+
+
+def test_lossy_sampler_rows_match_oracle_at_workload_size(ctx):
+    """The lossy workload at full size (n = 40 photons, m = 60 modes,
+    eta = 0.5, the 100 x 40 isometry, MIXED as the lossy benchmark runs it):
+    the first 16 rows of four chains equal the oracle's lossy chains (loss
+    modes included), with the same departure rule."""
+    v, mdet = S.config_lossy()
+    occ = np.ones(v.shape[1], dtype=np.int32)
+    steps, ns = 16, 4
+    _, _, _, ref_rows, ref_margin = oracle.cc_sample(v, occ, ns, seed=41, m_detected=mdet, max_steps=steps,
+                                                     trace=True)
+    counts, rows = ctx.sample_trace(v, occ, ns, seed=41, m_detected=mdet, mode=1)
+    assert rows.shape == (ns, 40) and counts.shape == (ns, mdet)
+    for s in range(ns):
+        assert np.array_equal(np.bincount(rows[s][rows[s] < mdet], minlength=mdet), counts[s])
+    _check_rows(rows, ref_rows, ref_margin, steps, MARGIN[1], 0)
+
+
 def test_sampler_trace_equals_plain_sampler(ctx):
     """bs_sample_trace draws exactly what bs_sample_ex draws."""
     u, occ = S.config_cc(n=10, m=20, seed=8)

@@ -314,6 +314,44 @@ def test_plain_fp64_walk_against_exact_and_double_double():
     assert oracle.perm_mult_fp64(np.zeros((2, 2)), [0, 0], [0, 0]) == 1
 
 
+def test_plain_fp64_gray_walk_and_minors():
+    """The plain-double Gray walk and minors (the sampling workload's CPU
+    timing baseline): exact on Gaussian-integer matrices (every column sum,
+    product and partial sum is an exact double at these sizes), within
+    plain FP64 rounding of the double-double oracle on Haar matrices, per(J_n)
+    = n! exactly, the Laplace identity sum_l v_l minor_l = per([A; v]), and
+    the empty cases."""
+    for trial in range(8):
+        n = 3 + trial
+        a = S.gaussian_integer_matrix(n, 1400 + trial, bound=2)
+        re, im = oracle.ryser_exact_gauss(a)
+        got = oracle.bbfg_gray_fp64(a)
+        assert (Fraction(got.real), Fraction(got.imag)) == (re, im), trial
+    for n in range(1, 11):
+        assert oracle.bbfg_gray_fp64(np.ones((n, n))) == math.factorial(n)
+    for n in (8, 12, 16):
+        a = S.haar_unitary(n + 4, 1500 + n)[:n, :n]
+        v, t = oracle.bbfg_gray(a)
+        scale = float(np.prod(np.sqrt((np.abs(a) ** 2).sum(axis=0))))  # Hadamard bound
+        assert abs(oracle.bbfg_gray_fp64(a) - (v + t)) <= 1e-13 * scale, n
+    assert oracle.bbfg_gray_fp64(np.zeros((0, 0))) == 1
+    # minors: against the double-double minors and the Laplace identity
+    u = S.haar_unitary(12, 1600)
+    a = u[:6, :7]
+    M = np.ones(6, dtype=np.int32)
+    N = np.ones(7, dtype=np.int32)
+    got = oracle.minors_fp64(a, M, N)
+    mv, mt = oracle.minors(a, M, N)
+    assert np.all(np.abs(got - (mv + mt)) <= 1e-14), np.abs(got - (mv + mt)).max()
+    v = u[6, :7]
+    pv, pt = oracle.bbfg_gray(np.vstack([a, v[None, :]]))
+    assert abs(np.sum(v * got) - (pv + pt)) <= 1e-14
+    M2 = np.array([2, 1, 1, 1, 1, 0], dtype=np.int32)   # a repeated row: expanded
+    got2 = oracle.minors_fp64(a, M2, N)
+    mv2, mt2 = oracle.minors(a, M2, N)
+    assert np.all(np.abs(got2 - (mv2 + mt2)) <= 1e-14)
+
+
 def test_mult_no_photons_and_bad_input():
     assert oracle.perm_mult(np.zeros((2, 2)), [0, 0], [0, 0])[0] == 1
     with pytest.raises(oracle.OracleError):
