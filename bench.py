@@ -154,12 +154,35 @@ def _oracle_chain_prefix(job):
     return ops, time.perf_counter() - t0
 
 
-def calibrate_prefix(target_s):
+def _oracle_fp64_prefix(job):
+    """The plain-FP64 CPU form on the same work (pool worker): steps 2..s of
+    a chain, each step's k minors computed separately by the oracle's
+    plain-double Gray walk over the (k-1) x (k-1) matrices.  The oracle's
+    sampler expands repeated rows, so a step's cost does not depend on the
+    rows drawn: they are drawn uniformly here (seeded).  Returns
+    (addend-column ops, seconds)."""
+    steps, seed = job
+    import numpy as np
+    import oracle
+    import synthetic as S
+    u, occ = S.config_cc(N_PHOTONS, M_MODES, SEED)
+    cols = np.repeat(np.arange(M_MODES), occ)
+    rows = S.rng(seed).integers(0, M_MODES, size=N_PHOTONS)
+    ops = 0.0
+    t0 = time.perf_counter()
+    for k in range(2, steps + 1):
+        a = u[np.ix_(rows[:k - 1], cols[:k])]
+        oracle.minors_fp64(a, np.ones(k - 1, np.int32), np.ones(k, np.int32))
+        ops += k * (k - 1) * 2.0 ** (k - 2)
+    return ops, time.perf_counter() - t0
+
+
+def calibrate_prefix(target_s, fn=_oracle_chain_prefix):
     """Longest chain prefix (steps 1..s, s >= 12) whose single-threaded
     oracle run stays under about target_s; returns (s, ops, seconds)."""
     steps, last = 12, None
     while steps <= N_PHOTONS:
-        ops, dt = _oracle_chain_prefix((steps, 7))
+        ops, dt = fn((steps, 7))
         last = (steps, ops, dt)
         if dt > target_s:
             break
@@ -180,9 +203,9 @@ class OraclePool:
         self.pool.map_async(_oracle_chain_prefix, [(2, 7 + i) for i in range(procs)],
                             chunksize=1).get(timeout=POOL_TIMEOUT_S)  # imports
 
-    def run(self, steps):
+    def run(self, steps, fn=_oracle_chain_prefix):
         t0 = time.perf_counter()
-        res = self.pool.map_async(_oracle_chain_prefix, [(steps, 7 + i) for i in range(self.procs)],
+        res = self.pool.map_async(fn, [(steps, 7 + i) for i in range(self.procs)],
                                   chunksize=1).get(timeout=POOL_TIMEOUT_S)
         return sum(r[0] for r in res), time.perf_counter() - t0
 
@@ -198,14 +221,21 @@ def oracle_baseline(budget_s):
     steps, ops1, dt1 = calibrate_prefix(budget_s / 3)
     full = full_sample_ops(N_PHOTONS)
     one = {"value": ops1 / dt1 / full, "cores": 1}
+    fsteps, fops1, fdt1 = calibrate_prefix(budget_s / 6, _oracle_fp64_prefix)
     procs = host_cores()
     pool = OraclePool(procs)
     try:
         ops, wall = pool.run(steps)
+        fops, fwall = pool.run(fsteps, _oracle_fp64_prefix)
     finally:
         pool.close()
+    plain = {"value": fops / fwall / full, "cores": procs, "one_core": {"value": fops1 / fdt1 / full, "cores": 1},
+             "what": ("the oracle's plain-double Gray walk (no compensation), each of a step's k minors computed "
+                      "separately, on the same matrix sizes"),
+             "sample": f"steps 2..{fsteps} of one chain per core, {procs} cores in parallel: {fops:.3g} ops in "
+                       f"{fwall:.2f} s"}
     return {"value": ops / wall / full, "unit": UNIT, "cores": procs, "kind": "oracle",
-            "one_core": one,
+            "one_core": one, "plain_fp64": plain,
             "what": ("the double-double oracle, each of a step's k minors computed separately as its own "
                      "(k-1) x (k-1) Gray BB/FG permanent (k times the work of the fused walk), not a tuned CPU "
                      "code"),

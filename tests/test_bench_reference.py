@@ -53,3 +53,18 @@ def test_bench_addend_count_matches_the_planner():
         assert not plan["transposed"]
         assert bench.addend_count(M) == plan["C"], (M, plan)
     assert bench.addend_count([3, 2, 2, 1, 1, 1, 1, 1]) == 576
+
+
+def test_headline_cpu_baseline_has_the_plain_fp64_row():
+    """The headline line's cpu_baseline (host cores, no GPU): the
+    double-double oracle's rate with its one-core figure, and beside it the
+    plain-FP64 row (the oracle's plain-double Gray walk on the same
+    matrix sizes), which must be the faster of the two."""
+    sys.path.insert(0, ROOT)
+    import bench
+    cb = bench.oracle_baseline(1.0)
+    assert cb["kind"] == "oracle" and cb["unit"] == "samples/s" and cb["cores"] >= 1
+    assert cb["value"] > 0 and cb["one_core"]["value"] > 0
+    p = cb["plain_fp64"]
+    assert p["value"] > 0 and p["one_core"]["value"] > cb["one_core"]["value"]
+    assert "what" in p and "sample" in p

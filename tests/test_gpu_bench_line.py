@@ -17,7 +17,7 @@ ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 
 def test_bench_line_has_the_contract_keys():
     cmd = [sys.executable, os.path.join(ROOT, "bench.py"), "--samples", "16", "--steps", "3", "--warmup", "3",
-           "--no-cpu-baseline", "--side-steps", "1"]
+           "--no-cpu-baseline", "--side-steps", "1", "--serving-chains", "8"]
     r = subprocess.run(cmd, cwd=ROOT, capture_output=True, text=True, timeout=600)
     assert r.returncode == 0, r.stderr[-3000:]
     lines = [l for l in r.stdout.splitlines() if l.strip()]
@@ -35,6 +35,11 @@ def test_bench_line_has_the_contract_keys():
     for name, f in side.items():
         assert f["samples_per_s"] > 0 and 0 <= f["samples_equal_to_headline_run"] <= 1, name
     assert d["df_kernels_k30"]["minors"]["speedup_over_fp64"] > 1
+    srv = d["serving"]
+    for name in ("served_fp64", "served_mixed", "one_call_per_sample_fp64"):
+        assert srv[name]["requests"] == 8 and srv[name]["samples_per_s"] > 0, name
+        assert srv[name]["p99_ms"] >= srv[name]["p50_ms"] > 0, name
+    assert srv["served_fp64_equal_to_calls"] == 1.0
     assert d["latency_ms"]["max"] >= d["latency_ms"]["p50"] > 0
     assert d["config"]["workload"] == "cc_sampling_n30_m60" and d["config"]["samples_per_step"] == 16
     assert abs(d["value"] - 16 / (d["ms_per_step"] / 1000.0)) <= 1e-6 * d["value"]
