@@ -66,6 +66,8 @@ def parse():
     ap.add_argument("--workload", default="cc", choices=["cc", "single", "batch", "serving", "lossy", "formulas"],
                     help="cc: the headline line; the others print their own line for the other configs")
     ap.add_argument("--chains", type=int, default=64)
+    ap.add_argument("--serving-rates", default="50,200,1000,inf",
+                    help="Poisson arrival rates (Hz) of --workload serving, comma-separated (inf: all at once)")
     ap.add_argument("--serving-chains", type=int, default=64,
                     help="chains of the serving side measurement on the headline line (0: skip)")
     ap.add_argument("--lossy-samples", type=int, default=20, help="samples of the lossy workload")
@@ -738,20 +740,22 @@ def run_batch(args):
     return 0
 
 
-def serving_measure(chains, modes=("fp64", "mixed")):
+def serving_measure(chains, modes=("fp64", "mixed"), rate_hz=200.0, baseline=True):
     """Serving workload (C4): ``chains`` C&C samples, each with its own Haar
-    60 x 60 unitary and n ~ U[16, 34], Poisson arrivals at 200 Hz, served by
-    the continuous-batching engine (every chain on the device) in each of
-    ``modes``, and the same requests answered by one sample_ex call each in
-    FP64.  Samples/s over the wall time and per-request latency (arrival to
+    60 x 60 unitary and n ~ U[16, 34], Poisson arrivals at ``rate_hz``
+    (inf: all at once), served by the continuous-batching engine (every
+    chain on the device) in each of ``modes``, and the same requests
+    answered by one sample_ex call each in FP64 (one walk launch per minors
+    job).  Samples/s over the wall time and per-request latency (arrival to
     counts)."""
     import numpy as np
     import paper_2309_07027_gb300 as bs
     from paper_2309_07027_gb300 import serving
     import synthetic as S
-    cfg = S.config_serving(chains=chains)
+    cfg = S.config_serving(chains=chains, rate_hz=rate_hz)
     mode_of = {"fp64": bs.BS_FP64, "mixed": bs.BS_MIXED, "df": bs.BS_DF64}
-    out = {"workload": f"serving_{chains}_chains_n16_34_m60_poisson200hz",
+    rate_name = "all_at_once" if rate_hz == float("inf") else f"poisson{rate_hz:g}hz"
+    out = {"workload": f"serving_{chains}_chains_n16_34_m60_{rate_name}",
            "latency_what": "per request: arrival (submission) to counts available"}
     ref = None
     for name in modes:
@@ -763,18 +767,21 @@ def serving_measure(chains, modes=("fp64", "mixed")):
         out[f"served_{name}"] = r
         if name == "fp64":
             ref = counts
-    ctx = bs.Context(0)
-    ctx.sample_ex(cfg[0]["unitary"], cfg[0]["occupation"], 1, 1)  # load and warm the kernels
-    wall, lat, counts = serving.run_one_call_per_sample(cfg, ctx, mode=bs.BS_FP64)
-    ctx.close()
-    out["one_call_per_sample_fp64"] = serving.summarize(wall, lat, len(cfg))
-    if ref is not None:
-        out["served_fp64_equal_to_calls"] = float(np.mean([np.array_equal(a, b) for a, b in zip(ref, counts)]))
+    if baseline:
+        ctx = bs.Context(0)
+        ctx.sample_ex(cfg[0]["unitary"], cfg[0]["occupation"], 1, 1)  # load and warm the kernels
+        wall, lat, counts = serving.run_one_call_per_sample(cfg, ctx, mode=bs.BS_FP64)
+        ctx.close()
+        out["one_call_per_sample_fp64"] = serving.summarize(wall, lat, len(cfg))
+        if ref is not None:
+            out["served_fp64_equal_to_calls"] = float(np.mean([np.array_equal(a, b) for a, b in zip(ref, counts)]))
     return out
 
 
 def run_serving(args):
-    print(json.dumps(serving_measure(args.chains, ("fp64", "mixed", "df"))), flush=True)
+    """C4 with the arrival rate swept to saturation: one JSON line per rate."""
+    for rate in (float(x) for x in args.serving_rates.split(",")):
+        print(json.dumps(serving_measure(args.chains, ("fp64", "mixed", "df"), rate_hz=rate)), flush=True)
     return 0
 
 

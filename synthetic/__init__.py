@@ -113,13 +113,14 @@ def config_serving(chains: int = 64, nmin: int = 16, nmax: int = 34, m: int = 60
                    seed: int = 4, rate_hz: float = 200.0):
     """Serving workload: ``chains`` sampling chains, each with its own Haar
     m x m unitary and photon number n ~ U[nmin, nmax] (one photon in modes
-    0..n-1); Poisson arrival offsets (seconds) at ``rate_hz``."""
+    0..n-1); Poisson arrival offsets (seconds) at ``rate_hz`` (inf: all at
+    time 0).  The unitaries and photon numbers do not depend on the rate."""
     g = rng(seed)
     out = []
     t = 0.0
     for c in range(chains):
         n = int(g.integers(nmin, nmax + 1))
-        t += float(g.exponential(1.0 / rate_hz))
+        t += float(g.exponential(1.0)) / rate_hz  # inf: 0
         occ = np.zeros(m, dtype=np.int32)
         occ[:n] = 1
         out.append(dict(unitary=haar_unitary(m, seed * 7919 + c), occupation=occ,
