@@ -160,3 +160,19 @@ def test_server_cancel(ctx, bslib):
         with pytest.raises(bslib.BsError) as e:
             srv.cancel(done)                                # released: unknown ticket
         assert e.value.code == bslib.BS_EINVAL
+
+
+def test_served_mixed_chains_switch_precision_as_the_sampler_does(ctx, bslib):
+    """MIXED at a size where the rule sends some steps to FP32 and others to
+    the double-float kernels (n = 24 photons in 10 modes, two or three per
+    input mode, so late steps have heavily repeated rows): the served
+    samples equal the direct sampler's, so every step took the same
+    precision in both."""
+    u = S.haar_unitary(10, 19)
+    occ = np.array([3, 3, 3, 3, 2, 2, 2, 2, 2, 2], dtype=np.int32)
+    ctx.reset_stats()
+    ref = ctx.sample(u, occ, 12, seed=9, mode=1)
+    st = ctx.stats()
+    assert st["addends"][1] > 0 and st["addends"][2] > 0, st["addends"]
+    got, _, _ = _serve(bslib, 1, u, occ, 9, range(12), tick_tasks=2048)
+    assert np.array_equal(got, ref)
