@@ -278,8 +278,8 @@ int launch_walk(bs_ctx* c, const bs::WalkArgs& a, int prec, int kind) {
 // The MIXED mode's kernels for jobs that fail the FP32 rule.
 constexpr int kMixedFallback = BS_MIXED_FALLBACK_PREC;
 
-// Precision of a job planned under `mode` (rule_fp32: the MIXED rule's
-// verdict).
+// Precision of a job planned under `mode` (rule_fp32: whether the MIXED
+// rule admits FP32).
 int job_prec(bs_mode mode, int rule_fp32) {
     if (mode == BS_DF64) return BS_PREC_DF;
     if (mode == BS_MIXED) return rule_fp32 ? BS_PREC_FP32 : kMixedFallback;
