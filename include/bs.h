@@ -389,13 +389,16 @@ int bs_debug_gray_walk(int ndigits, int nbin, const int* radix, uint64_t start, 
 int bs_debug_plan(int rows, int cols, const int* row_mult, const int* col_mult, int kind, int64_t* info);
 
 /* Host-only view of the BS_MIXED precision rule for a permanent (kind 0) or
- * minors (kind 1) problem planned alone: *log2_err receives the predicted
- * log2 of the FP32 walk's error relative to prod_j ||a_j||^{N_j}, *log2L
- * (nullable) the FP32 chunk length it assumed.  The job runs in FP32 when
- * *log2_err <= log2 of the MIXED tolerance (bs_ctx_set_mixed_tolerance,
- * default 1e-6).  Returns BS_EINVAL on invalid multiplicities. */
-int bs_debug_mixed_error(int rows, int cols, const int* row_mult, const int* col_mult, int kind, double* log2_err,
-                         int* log2L);
+ * minors (kind 1) problem: *log2_err receives the predicted log2 of the
+ * FP32 walk's error relative to prod_j ||a_j||^{N_j} for FP32 chunks of
+ * 2^chunk_log2 addends (chunk_log2 <= 0: the chunk length of the problem
+ * planned alone), *log2L (nullable) that chunk exponent, *plan (nullable)
+ * the decision at the default tolerance 1e-6: 1 FP32, 2 FP32 with the column
+ * sums re-seeded from the matrix every 2^8 steps inside each chunk (the
+ * prediction without its drift term meets the tolerance), 0 the fallback
+ * kernels.  Returns BS_EINVAL on invalid multiplicities. */
+int bs_debug_mixed_error(int rows, int cols, const int* row_mult, const int* col_mult, int kind, int chunk_log2,
+                         double* log2_err, int* log2L, int* plan);
 
 #ifdef __cplusplus
 }

@@ -111,7 +111,7 @@ def load():
         "bs_debug_gray_walk": ([C.c_int, C.c_int, ip, C.c_uint64, C.c_int, ip, ip, C.POINTER(C.c_uint64)],
                                C.c_int),
         "bs_debug_plan": ([C.c_int, C.c_int, ip, ip, C.c_int, i64p], C.c_int),
-        "bs_debug_mixed_error": ([C.c_int, C.c_int, ip, ip, C.c_int, dp, ip], C.c_int),
+        "bs_debug_mixed_error": ([C.c_int, C.c_int, ip, ip, C.c_int, C.c_int, dp, ip, ip], C.c_int),
         "bs_perm_noalloc": ([vp, C.c_int, C.c_int, C.c_int, ip, ip, C.c_int, vp, vp, vp], C.c_int),
         "bs_server_create": ([C.POINTER(C.c_void_p), C.c_int, C.c_size_t, C.c_int, C.c_int, C.c_int], C.c_int),
         "bs_server_destroy": ([vp], None),
@@ -527,17 +527,20 @@ def debug_gray_walk(radix, nbin, start, steps):
     return deltas[:, :nd], moved[:steps], w[:steps]
 
 
-def debug_mixed_error(row_mult, col_mult, kind=0):
-    """MIXED precision rule for the problem planned alone: (predicted log2 of
-    the FP32 error relative to prod ||a_j||, FP32 chunk log2, runs in FP32 at
-    the default tolerance 1e-6)."""
+def debug_mixed_error(row_mult, col_mult, kind=0, chunk_log2=0):
+    """MIXED precision rule: (predicted log2 of the FP32 error relative to
+    prod ||a_j||, FP32 chunk log2, decision at the default tolerance 1e-6:
+    1 FP32, 2 FP32 re-seeded every 2^8 steps, 0 the fallback kernels).
+    chunk_log2 <= 0: the chunk length of the problem planned alone."""
     L = load()
     M = _i32(row_mult)
     N = _i32(col_mult)
     e = C.c_double(0.0)
     l = C.c_int(0)
-    _check(L.bs_debug_mixed_error(len(M), len(N), _ip(M), _ip(N), int(kind), C.byref(e), C.byref(l)))
-    return float(e.value), int(l.value), float(e.value) <= float(np.float32(-19.93))
+    plan = C.c_int(0)
+    _check(L.bs_debug_mixed_error(len(M), len(N), _ip(M), _ip(N), int(kind), int(chunk_log2), C.byref(e),
+                                  C.byref(l), C.byref(plan)))
+    return float(e.value), int(l.value), int(plan.value)
 
 
 def debug_plan(row_mult, col_mult, kind=0):

@@ -312,7 +312,7 @@ struct Prepared {
 int plan_upload(bs_ctx* c, std::vector<JobIn>& ins, bs_mode mode, Prepared& P) {
     struct Row {
         JobIn in;
-        int prec, kind, bucket, log2L, cpt, ncols;
+        int prec, kind, bucket, log2L, cpt, ncols, reseed;
         uint32_t ntasks;
     };
     std::vector<Row> rows;
@@ -326,10 +326,11 @@ int plan_upload(bs_ctx* c, std::vector<JobIn>& ins, bs_mode mode, Prepared& P) {
             // the rule needs the chunk length the FP32 kernel would use
             const int cpt32 = bs_chunks_per_task(in.p->kind, BS_PREC_FP32, in.p->K);
             const int l32 = bs_choose_log2L_single(in.p->C, cpt32, c->log2max[BS_PREC_FP32], BS_TARGET_TASKS_SINGLE_FP32);
-            rule = bs_mixed_uses_fp32(in.p->radix, in.p->nrows, in.p->pinned_m, in.p->K, in.p->n, l32,
+            rule = bs_mixed_fp32_plan(in.p->radix, in.p->nrows, in.p->pinned_m, in.p->K, in.p->n, l32,
                                       c->mixed_log2_tol, q_work.data());
         }
-        r.prec = job_prec(mode, rule);
+        r.prec = job_prec(mode, rule != 0);
+        r.reseed = r.prec == BS_PREC_FP32 && rule == 2 ? BS_FP32_RESEED_LOG2 : 0;
         r.kind = in.p->kind;
         r.bucket = r.prec == BS_PREC_DF ? (in.p->K + 7) >> 3 : (in.p->K + 3) >> 2;
         r.cpt = bs_chunks_per_task(r.kind, r.prec, in.p->K);
@@ -391,6 +392,7 @@ int plan_upload(bs_ctx* c, std::vector<JobIn>& ins, bs_mode mode, Prepared& P) {
             jb.src_ld = r.in.src_ld;
             jb.src_trans = p.trans ? 1 : 0;
             jb.formula = p.formula;
+            jb.reseed_log2 = r.reseed;
             meta.insert(meta.end(), p.radix, p.radix + p.nrows);
             meta.insert(meta.end(), p.digit_src, p.digit_src + p.nrows);
             meta.insert(meta.end(), p.col_src, p.col_src + p.K);
@@ -1505,8 +1507,8 @@ int bs_debug_gray_walk(int ndigits, int nbin, const int* radix, uint64_t start, 
     return BS_OK;
 }
 
-int bs_debug_mixed_error(int rows, int cols, const int* row_mult, const int* col_mult, int kind, double* log2_err,
-                         int* log2L) {
+int bs_debug_mixed_error(int rows, int cols, const int* row_mult, const int* col_mult, int kind, int chunk_log2,
+                         double* log2_err, int* log2L, int* plan) {
     if (!log2_err) return fail(BS_EINVAL, "log2_err is NULL");
     IntPlan p;
     int rc = plan_job(rows, cols, row_mult, col_mult, kind == 1 ? BS_KIND_MINORS : BS_KIND_PERM, p);
@@ -1514,12 +1516,18 @@ int bs_debug_mixed_error(int rows, int cols, const int* row_mult, const int* col
     if (p.trivial) {
         *log2_err = -1000.0;
         if (log2L) *log2L = 0;
+        if (plan) *plan = 1;
         return BS_OK;
     }
-    const int l32 = bs_choose_log2L_single(p.C, bs_chunks_per_task(p.kind, 1, p.K), 12, BS_TARGET_TASKS_SINGLE_FP32);
+    const int l32 = chunk_log2 > 0
+                        ? chunk_log2
+                        : bs_choose_log2L_single(p.C, bs_chunks_per_task(p.kind, 1, p.K), 12, BS_TARGET_TASKS_SINGLE_FP32);
     std::vector<double> q_work(BS_MIXED_QMAX + 1);
     *log2_err = bs_mixed_log2_error(p.radix, p.nrows, p.pinned_m, p.K, p.n, l32, q_work.data());
     if (log2L) *log2L = l32;
+    if (plan)
+        *plan = bs_mixed_fp32_plan(p.radix, p.nrows, p.pinned_m, p.K, p.n, l32, BS_MIXED_LOG2_TOL_DEFAULT,
+                                   q_work.data());
     return BS_OK;
 }
 

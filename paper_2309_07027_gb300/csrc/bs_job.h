@@ -48,7 +48,8 @@ struct bs_job {
     int32_t src_ld;        // source leading dimension (complex elements)
     int32_t src_trans;     // 1: formula row r / column c read source (c, r)
     int32_t formula;       // BS_JOB_BBFG (0), BS_JOB_RYSER or BS_JOB_NW (plain permanents, FP64)
-    int32_t reserved;
+    int32_t reseed_log2;   // FP32 jobs: > 0 re-seeds the column sums from the matrix every 2^reseed_log2
+                           // steps inside a chunk as well (0: at chunk starts only)
 };
 
 // Formula of a job (see bs_perm_formula).  Ryser and Nijenhuis-Wilf jobs

@@ -120,13 +120,15 @@ extern "C" int bs_perm_noalloc(const bs_c128* A, int rows, int cols, int ld, con
     if (!A) return bs::fail(BS_EINVAL, "matrix pointer is NULL");
     if (ld < cols) return bs::fail(BS_EINVAL, "leading dimension %d < columns %d", ld, cols);
     int prec = mode == BS_DF64 ? BS_PREC_DF : BS_PREC_FP64;
+    int reseed = 0;
     if (mode == BS_MIXED) {
         double q_work[BS_MIXED_QMAX + 1];  // the rule's scratch, on the stack
         const int l32 = bs_choose_log2L_single(p.C, bs_chunks_per_task(BS_KIND_PERM, BS_PREC_FP32, p.K), 12,
                                                BS_TARGET_TASKS_SINGLE_FP32);
-        prec = bs_mixed_uses_fp32(p.radix, p.nrows, p.pinned_m, p.K, p.n, l32, BS_MIXED_LOG2_TOL_DEFAULT, q_work)
-                   ? BS_PREC_FP32
-                   : BS_MIXED_FALLBACK_PREC;
+        const int plan = bs_mixed_fp32_plan(p.radix, p.nrows, p.pinned_m, p.K, p.n, l32, BS_MIXED_LOG2_TOL_DEFAULT,
+                                            q_work);
+        prec = plan ? BS_PREC_FP32 : BS_MIXED_FALLBACK_PREC;
+        reseed = plan == 2 ? BS_FP32_RESEED_LOG2 : 0;
     }
     const int cpt = bs_chunks_per_task(BS_KIND_PERM, prec, p.K);
     const int log2L = bs_choose_log2L_single(p.C, cpt, 12,
@@ -155,6 +157,7 @@ extern "C" int bs_perm_noalloc(const bs_c128* A, int rows, int cols, int ld, con
     jb.n = p.n;
     jb.normalize = prec != BS_PREC_FP64 ? 1 : 0;
     jb.prec = prec;
+    jb.reseed_log2 = reseed;
     jb.src_ld = nc;
     jb.src_trans = p.trans ? 1 : 0;
     int meta[BS_META_SIZE(BS_MAX_DIGITS, BS_MAX_COLS, BS_MAX_N)];

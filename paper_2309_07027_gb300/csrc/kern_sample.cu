@@ -153,12 +153,13 @@ __device__ int plan_minors_step(const int* __restrict__ rows, const int* __restr
     uint64_t C = 1;
     for (int j = 0; j < nrows; ++j) C *= (uint64_t)drad[j];
     int prec = rule.mode == 2 ? BS_PREC_DF : BS_PREC_FP64;
+    jb.reseed_log2 = 0;
     if (rule.mode == 1) {
         const int l32 = bs_choose_log2L(C, bs_chunks_per_task(BS_KIND_MINORS, BS_PREC_FP32, k), BS_LOG2L_MIN_MANY,
                                         rule.log2max[BS_PREC_FP32], BS_TARGET_TASKS_MANY);
-        prec = bs_mixed_uses_fp32(drad, nrows, ucnt[p], k, k - 1, l32, rule.mixed_log2_tol, q_work)
-                   ? BS_PREC_FP32
-                   : rule.mixed_fallback;
+        const int plan = bs_mixed_fp32_plan(drad, nrows, ucnt[p], k, k - 1, l32, rule.mixed_log2_tol, q_work);
+        prec = plan ? BS_PREC_FP32 : rule.mixed_fallback;
+        jb.reseed_log2 = plan == 2 ? BS_FP32_RESEED_LOG2 : 0;
     }
     jb.prec = prec;
     jb.normalize = prec != BS_PREC_FP64 ? 1 : 0;

@@ -13,8 +13,16 @@ constexpr int kPermBlock = 128;
 constexpr int kMinorsBlock = 128;
 
 
+// CTAs per SM the permanent kernel is compiled for, by bucket width (the
+// register budgets the measured kernels ran at: 96 registers at widths 20
+// and 24, 128 at 28..40, 168 above; 80 and less below 20).
 template <int KB>
-__global__ void __launch_bounds__(kPermBlock) walk_fp32_perm_kernel(WalkArgs a) {
+struct PermMinBlocks {
+    static constexpr int value = KB <= 8 ? 8 : KB <= 12 ? 7 : KB <= 16 ? 6 : KB <= 24 ? 5 : KB <= 40 ? 4 : 3;
+};
+
+template <int KB>
+__global__ void __launch_bounds__(kPermBlock, PermMinBlocks<KB>::value) walk_fp32_perm_kernel(WalkArgs a) {
     const int lane = threadIdx.x & 31;
     const bs_job* __restrict__ jobs = a.jobs;
     const unsigned long long total = task_total(a);

@@ -123,6 +123,10 @@ BS_HD int64_t bs_flops_per_addend(int K, int kind) {
 #define BS_MIXED_FALLBACK_PREC BS_PREC_DF
 #define BS_MIXED_QMAX (BS_MAX_PHOTONS * BS_MAX_PHOTONS)  // Q <= sum M_k^2 <= n^2
 #define BS_MIXED_RESIDUAL (-21.02)
+// Chunks up to 2^8 addends show no drift term in the measured errors; FP32
+// jobs that need it re-seed their column sums from the matrix every 2^8
+// steps inside a chunk, which keeps them within that length.
+#define BS_FP32_RESEED_LOG2 8
 
 // q_work: BS_MIXED_QMAX + 1 doubles of scratch.  radix / nrows: the job's
 // digits; pinned_m: multiplicity of the pinned row (its other pinned_m - 1
@@ -167,18 +171,28 @@ BS_HD float bs_mixed_log2_error(const int* radix, int nrows, int pinned_m, int K
         if (f[q] != 0.0) total += f[q] * pow((double)(q + off + nb) * inv_n, (double)K);
     if (!(total > 0.0)) return -1000.0f;
     const double lrss = (1.0 - (double)n) + 0.5 * (log2(total) + (double)nb);
-    const double drift = log2L > 8 ? 0.5 * (double)(log2L - 8) : 0.0;
+    const double drift = log2L > BS_FP32_RESEED_LOG2 ? 0.5 * (double)(log2L - BS_FP32_RESEED_LOG2) : 0.0;
     return (float)(lrss + 0.5 * log2((double)(K > 1 ? K : 1)) + drift + BS_MIXED_RESIDUAL);
 }
 
-// The job runs in FP32 when the predicted error is <= log2_tol (default
-// log2(1e-6)), else in FP64-class arithmetic (BS_MIXED_FALLBACK_PREC: where
-// cancellation demands it, the column sums, products and sums keep about 48
-// bits).  Depends only on the multiplicities, K, n and the FP32 chunk
-// length, so every planner with the same chunk rule decides alike.
-BS_HD int bs_mixed_uses_fp32(const int* radix, int nrows, int pinned_m, int K, int n, int log2L, float log2_tol,
+// The MIXED decision for a job the FP32 kernels would walk in chunks of
+// 2^log2L addends, against log2_tol (default log2(1e-6)):
+//   1  FP32 (predicted error <= log2_tol), column sums seeded at chunk starts;
+//   2  FP32 with the column sums also re-seeded every 2^BS_FP32_RESEED_LOG2
+//      steps (the prediction without the drift term is <= log2_tol) -- the
+//      re-seeding bounds the drift of the incremental FP32 sums, at the cost
+//      of one seed (about half the rows) per 2^8 steps;
+//   0  neither: FP64-class arithmetic (BS_MIXED_FALLBACK_PREC: where
+//      cancellation demands it, the column sums, products and sums keep
+//      about 48 bits).
+// Depends only on the multiplicities, K, n and the FP32 chunk length, so
+// every planner with the same chunk rule decides alike.
+BS_HD int bs_mixed_fp32_plan(const int* radix, int nrows, int pinned_m, int K, int n, int log2L, float log2_tol,
                              double* q_work) {
-    return bs_mixed_log2_error(radix, nrows, pinned_m, K, n, log2L, q_work) <= log2_tol;
+    const float e = bs_mixed_log2_error(radix, nrows, pinned_m, K, n, log2L, q_work);
+    if (e <= log2_tol) return 1;
+    if (log2L > BS_FP32_RESEED_LOG2 && e - 0.5f * (float)(log2L - BS_FP32_RESEED_LOG2) <= log2_tol) return 2;
+    return 0;
 }
 
 namespace bs {

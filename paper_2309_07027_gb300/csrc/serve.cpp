@@ -112,7 +112,7 @@ struct Request {
     size_t off = 0, bytes = 0;
     int64_t src_off = 0, data_off = 0, meta_off = 0, part_off = 0;
     int slot = -1;                     // result slot (BS_MAX_COLS values)
-    int prec = BS_PREC_FP64, cpt = 32, log2L = 6, ncols = 1;
+    int prec = BS_PREC_FP64, cpt = 32, log2L = 6, ncols = 1, reseed = 0;
     uint32_t ntasks = 0, done = 0;
     int status = 0;                    // 0 pending, 1 done, <0 error code
     std::vector<bs_c128> result;
@@ -285,6 +285,7 @@ int run_tick(bs_server* s, std::vector<Request*>& admit, std::vector<Request*>& 
         jb.n = p.n;
         jb.normalize = r->prec != BS_PREC_FP64 ? 1 : 0;
         jb.prec = r->prec;
+        jb.reseed_log2 = r->reseed;
         jb.data_off = r->data_off;
         jb.meta_off = r->meta_off;
         jb.partial_off = r->part_off;
@@ -316,6 +317,7 @@ int run_tick(bs_server* s, std::vector<Request*>& admit, std::vector<Request*>& 
             jb.log2L = r->log2L;
             jb.n = p.n;
             jb.prec = r->prec;
+            jb.reseed_log2 = r->reseed;
             jb.data_off = r->data_off;
             jb.meta_off = r->meta_off;
             jb.partial_off = r->part_off;
@@ -727,10 +729,10 @@ int64_t bs_server_submit(bs_server* s, int kind, const bs_c128* A, int rows, int
         double q_work[BS_MIXED_QMAX + 1];
         const int l32 = bs_choose_log2L(r->plan.C, bs_chunks_per_task(r->kind, BS_PREC_FP32, r->plan.K),
                                         BS_LOG2L_MIN_MANY, 12, BS_TARGET_TASKS_MANY);
-        r->prec = bs_mixed_uses_fp32(r->plan.radix, r->plan.nrows, r->plan.pinned_m, r->plan.K, r->plan.n, l32,
-                                     BS_MIXED_LOG2_TOL_DEFAULT, q_work)
-                      ? BS_PREC_FP32
-                      : BS_MIXED_FALLBACK_PREC;
+        const int plan = bs_mixed_fp32_plan(r->plan.radix, r->plan.nrows, r->plan.pinned_m, r->plan.K,
+                                            r->plan.n, l32, BS_MIXED_LOG2_TOL_DEFAULT, q_work);
+        r->prec = plan ? BS_PREC_FP32 : BS_MIXED_FALLBACK_PREC;
+        r->reseed = plan == 2 ? BS_FP32_RESEED_LOG2 : 0;
     }
     r->cpt = bs_chunks_per_task(r->kind, r->prec, r->plan.K);
     r->log2L = bs_choose_log2L(r->plan.C, r->cpt, BS_LOG2L_MIN_MANY, 12, BS_TARGET_TASKS_MANY);

@@ -112,6 +112,16 @@ __device__ __forceinline__ void seed_pairs(colsum (&c)[NP], const bs_gray& g, co
     }
 }
 
+// Re-seeding inside a chunk (jobs with reseed_log2 > 0, set by the MIXED
+// rule): at the steps s + 1 that are multiples of 2^reseed_log2 the column
+// sums are computed afresh from the matrix for the current Gray state
+// instead of updated, so the incremental FP32 sums drift no further than in
+// a chunk of that length.  The stepper's binary Delta bits are written back
+// to the Gray state first (between general steps it holds them alone).
+__device__ __forceinline__ bool reseed_due(const bs_job& jb, uint32_t s1) {
+    return jb.reseed_log2 > 0 && (s1 & ((1u << jb.reseed_log2) - 1u)) == 0;
+}
+
 // ---------------------------------------------------------------- one task: permanent
 // One lane = one chunk; all KB columns as KB/2 packed pairs (pad columns are
 // neutral).  Per addend: the packed update, one packed product chain (even
@@ -135,29 +145,42 @@ __device__ void walk_task_perm_fp32(const bs_job& jb, const void* __restrict__ d
         ChunkStepper st;
         st.init(g, i0, jb.nbin, jb.nrows, radix, reinterpret_cast<const uint64_t*>(radix + (BS_META_BINOM(jb) - jb.meta_off)));
         colsum c[NP];
-        seed_pairs<NP>(c, g, c0, a2, KP2, 0, jb.nbin, jb.nrows);
         float ws = signed_weight<float>(g.w, g.parity);
         cx<float> acc = {0.f, 0.f};
         uint32_t run = 0;
+        // segments of 2^reseed_log2 steps (the whole chunk without
+        // re-seeding), each starting from column sums seeded afresh
+        const uint32_t seg_mask = jb.reseed_log2 > 0 ? (1u << jb.reseed_log2) - 1u : 0xffffffffu;
         for (uint32_t s = 0;; ++s) {
-            cx2 pr = as_cx2(c[0]);
+            seed_pairs<NP>(c, g, c0, a2, KP2, 0, jb.nbin, jb.nrows);
+            const uint32_t s_last = min(len - 1u, s | seg_mask);
+            for (;; ++s) {
+                cx2 pr = as_cx2(c[0]);
 #pragma unroll
-            for (int p = 1; p < NP; ++p) pr = cmul2(pr, c[p]);
-            const cx<float> prod = halves_product(pr);
-            acc.re = bfma(ws, prod.re, acc.re);
-            acc.im = bfma(ws, prod.im, acc.im);
-            if (++run == FOLD) {
-                run = 0;
-                fre = ff_add_f(fre, acc.re);
-                fim = ff_add_f(fim, acc.im);
-                acc = cx<float>{0.f, 0.f};
+                for (int p = 1; p < NP; ++p) pr = cmul2(pr, c[p]);
+                const cx<float> prod = halves_product(pr);
+                acc.re = bfma(ws, prod.re, acc.re);
+                acc.im = bfma(ws, prod.im, acc.im);
+                if (++run == FOLD) {
+                    run = 0;
+                    fre = ff_add_f(fre, acc.re);
+                    fim = ff_add_f(fim, acc.im);
+                    acc = cx<float>{0.f, 0.f};
+                }
+                if (s == s_last) break;
+                uint32_t neg;
+                int wch;
+                const int row = st.step(g, s, radix, &neg, &wch);
+                ws = wch ? signed_weight<float>(g.w, g.parity) : flip_sign(ws);
+                update_pairs<NP>(c, a2 + (size_t)row * KP2, 0, unit_sign_f(neg));
             }
-            if (s + 1 == len) break;
+            if (s + 1u == len) break;
+            // into the next segment: its column sums are seeded at the top
             uint32_t neg;
             int wch;
-            const int row = st.step(g, s, radix, &neg, &wch);
+            (void)st.step(g, s, radix, &neg, &wch);
             ws = wch ? signed_weight<float>(g.w, g.parity) : flip_sign(ws);
-            update_pairs<NP>(c, a2 + (size_t)row * KP2, 0, unit_sign_f(neg));
+            g.dbin = (g.dbin & ~0xffffffffull) | (uint64_t)st.dlo;
         }
         fre = ff_add_f(fre, acc.re);
         fim = ff_add_f(fim, acc.im);
@@ -275,6 +298,7 @@ __device__ void walk_task_minors_fp32(const bs_job& jb, const void* __restrict__
     constexpr int CPT = 32 / G;
     static_assert(KB % (2 * G) == 0, "bucket must split into G groups of column pairs");
     static_assert(FOLD == 1u << LOG2_FOLD, "fold length is a power of two");
+    static_assert(BS_FP32_RESEED_LOG2 >= LOG2_FOLD, "re-seed points must be block ends");
     const int K = jb.K;
     constexpr int KP2 = KB / 2;  // pairs per row: BS_ROW_STRIDE(K) = KB in the bucket
     const int q = lane & (G - 1);
@@ -326,7 +350,13 @@ __device__ void walk_task_minors_fp32(const bs_job& jb, const void* __restrict__
             int wch;
             const int row = st.step(g, s, radix, &neg, &wch);
             ws = wch ? signed_weight<float>(g.w, g.parity) : flip_sign(ws);
-            update_pairs<NP>(c, a2 + (size_t)row * KP2, p0, unit_sign_f(neg));
+            // re-seed points (multiples of 2^reseed_log2 >= 2^8) are block ends
+            if (reseed_due(jb, s + 1u)) {
+                g.dbin = (g.dbin & ~0xffffffffull) | (uint64_t)st.dlo;
+                seed_pairs<NP>(c, g, c0, a2, KP2, p0, jb.nbin, jb.nrows);
+            } else {
+                update_pairs<NP>(c, a2 + (size_t)row * KP2, p0, unit_sign_f(neg));
+            }
         } else {
             ws = 0.f;
         }

@@ -201,3 +201,29 @@ def test_mixed_rule_closed_form_for_distinct_rows(bslib):
         got, l32, _ = bslib.debug_mixed_error(np.ones(n, np.int32), np.ones(n, np.int32), 0)
         want = (1 - n) / 2 + 0.5 * log2(n) + 0.5 * max(0, l32 - 8) - 21.02
         assert abs(got - want) < 1e-4, (n, got, want)
+
+
+def test_mixed_plan_reseeds_where_only_the_drift_term_fails(bslib):
+    """The three-way MIXED decision: FP32 when the prediction at the job's
+    chunk length meets 1e-6; FP32 with the column sums re-seeded every 2^8
+    steps when only the prediction without its drift term does (the drift
+    term is (log2 L - 8) / 2 for chunks of 2^log2L addends); else the
+    fallback kernels.  Checked over chunk lengths 2^3..2^12 on random
+    multiplicity patterns, against the prediction itself."""
+    tol = float(np.float32(-19.93))
+    g = np.random.default_rng(404)
+    seen = set()
+    for trial in range(300):
+        K = int(g.integers(8, 41))
+        hits = g.integers(0, int(g.integers(K // 3 + 1, 3 * K)), size=K - 1)
+        _, M = np.unique(hits, return_counts=True)
+        M = M.astype(np.int32)
+        for L in (3, 8, 10, 12):
+            e, l, plan = bslib.debug_mixed_error(M, np.ones(K, np.int32), 1, chunk_log2=L)
+            assert l == L
+            e8, _, _ = bslib.debug_mixed_error(M, np.ones(K, np.int32), 1, chunk_log2=8)
+            assert abs((e - e8) - 0.5 * max(0, L - 8)) < 1e-4
+            want = 1 if e <= tol else (2 if L > 8 and e8 <= tol else 0)
+            assert plan == want, (M.tolist(), L, e, e8, plan)
+            seen.add(plan)
+    assert seen == {0, 1, 2}

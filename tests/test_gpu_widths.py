@@ -180,6 +180,32 @@ def test_perm_block_diagonal_every_width(ctx, mode, K):
     assert abs(got - ref) <= TOL[mode] * scale(a, M, N), (K, got, ref)
 
 
+# ---------------------------------------------------------------- FP32 re-seeding inside chunks
+def test_mixed_reseeded_fp32_meets_the_drift_free_prediction(ctx, bslib):
+    """A 29 x 30 minors job (2^28 addends) is walked by the FP32 kernel in
+    chunks of 2^11 addends.  With the MIXED tolerance set between the rule's
+    prediction without and with its drift term, the rule keeps the job in
+    FP32 and has the kernel re-seed its column sums every 2^8 steps; the
+    error (against the FP64 kernel, itself checked against the oracle at
+    this width) then stays below the drift-free prediction, the bound of
+    chunks of 2^8 addends."""
+    K = 30
+    a = S.haar_unitary(64, 4900)[:K - 1, :K]
+    M = np.ones(K - 1, dtype=np.int32)
+    N = np.ones(K, dtype=np.int32)
+    e, L, _ = bslib.debug_mixed_error(M, N, 1)
+    e8, _, _ = bslib.debug_mixed_error(M, N, 1, chunk_log2=8)
+    assert L > 8 and e - e8 == pytest.approx(0.5 * (L - 8), abs=1e-4)
+    ref = ctx.laplace_minors(a, M, N, mode=0)
+    try:
+        ctx.set_mixed_tolerance(2.0 ** ((e + e8) / 2))
+        got = run_checked(ctx, lambda: ctx.laplace_minors(a, M, N, mode=1), 1, True)
+    finally:
+        ctx.set_mixed_tolerance(1e-6)
+    err = max(abs(got[l] - ref[l]) / minor_scale(a, M, N, l) for l in range(K))
+    assert 0 < err <= 2.0 ** e8, (err, 2.0 ** e8)
+
+
 # ---------------------------------------------------------------- power-of-two column normalisation
 @pytest.mark.parametrize("kind", ["pow2", "decimal"])
 def test_mixed_column_normalisation_extreme_ranges(ctx, bslib, kind):
