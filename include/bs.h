@@ -271,19 +271,22 @@ int bs_sample_dev(bs_ctx* ctx, const bs_c128* U_dev, int m_rows, int m_cols, int
 
 /* A server owns one device memory block of mem_budget_bytes (the admission
  * budget), a stream and a scheduler thread.  Requests (permanents or Laplace
- * minors, as bs_perm / bs_laplace_minors) are admitted in arrival order while
+ * minors, as bs_perm / bs_laplace_minors, and whole Clifford & Clifford
+ * samples, bs_server_submit_sample) are admitted in arrival order while
  * one of max_active slots is free and their device memory fits the budget;
  * every scheduling tick walks a share of tick_tasks warp tasks of every
  * resident request in one launch per kernel group, so requests arriving
  * while others run are admitted at the next tick and their work overlaps on
  * the device (iteration-level scheduling).  Results are bit-identical to
- * running each request alone.  mode: BS_FP64 or BS_MIXED (per-request
- * precision rule as for bs_perm).  Errors: BS_EINVAL, BS_ENODEV, BS_ENOMEM. */
+ * running each request alone.  mode: BS_FP64, BS_DF64 or BS_MIXED (per-job
+ * precision rule as for bs_perm).  Every entry point may be called from any
+ * host thread.  Errors: BS_EINVAL, BS_ENODEV, BS_ENOMEM. */
 typedef struct bs_server bs_server;
 int bs_server_create(bs_server** out, int device, size_t mem_budget_bytes, int max_active, int tick_tasks,
                      bs_mode mode);
 /* Stops the scheduler (after its current tick) and frees everything; pending
- * requests are dropped. */
+ * requests are dropped.  No other call on this server may be in progress or
+ * follow (a thread blocked in a wait must have returned). */
 void bs_server_destroy(bs_server* server);
 
 /* Submits a request (kind 0: permanent, 1: minors; host arrays, copied
