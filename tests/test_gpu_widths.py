@@ -400,3 +400,19 @@ def test_lossy_sampler_matches_binomial_thinning(ctx):
     table = table[:, table.sum(axis=0) > 0]
     _, pval, _, _ = st.chi2_contingency(table)
     assert pval > 1e-3, pval
+
+
+def test_mixed_sampler_agrees_with_fp64_at_workload_size(ctx):
+    """The sampling workload in full (n = 30, m = 60, 200 samples, all 30
+    steps, including the late steps whose FP32 jobs are re-seeded inside
+    their chunks and those the rule sends to the double-float kernels): a
+    MIXED chain leaves the FP64 chain's rows only at a draw that falls within
+    MIXED's error of a CDF boundary, so almost every sample is identical."""
+    u, occ = S.config_cc(n=30, m=60, seed=3)
+    _, r64 = ctx.sample_trace(u, occ, 200, seed=61, mode=0)
+    ctx.reset_stats()
+    _, rmx = ctx.sample_trace(u, occ, 200, seed=61, mode=1)
+    st = ctx.stats()
+    assert st["addends"][1] > 0 and st["addends"][2] > 0, st["addends"]
+    same = float(np.mean(np.all(r64 == rmx, axis=1)))
+    assert same >= 0.9, same
