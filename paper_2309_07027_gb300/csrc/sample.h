@@ -128,6 +128,18 @@ BS_HD int64_t bs_flops_per_addend(int K, int kind) {
 // steps inside a chunk, which keeps them within that length.
 #define BS_FP32_RESEED_LOG2 8
 
+// x^K by repeated squaring (K >= 0): plain multiplications, so host and
+// device compute the same value, far cheaper than pow() on the FP64 pipe.
+BS_HD double bs_ipow(double x, int K) {
+    double r = 1.0;
+    while (K > 0) {
+        if (K & 1) r *= x;
+        x *= x;
+        K >>= 1;
+    }
+    return r;
+}
+
 // q_work: BS_MIXED_QMAX + 1 doubles of scratch.  radix / nrows: the job's
 // digits; pinned_m: multiplicity of the pinned row (its other pinned_m - 1
 // copies are the digit of radix pinned_m when pinned_m > 1); log2L: the
@@ -152,14 +164,22 @@ BS_HD float bs_mixed_log2_error(const int* radix, int nrows, int pinned_m, int K
         const int dmax = pin ? pinned_m - 1 : M;
         const int add = top * top;
         if (qmax + add > BS_MIXED_QMAX) return 1000.0f;  // outside the model: FP64
+        // the row's squared weights C(dmax, d)^2 and squared coefficients,
+        // once per row (dmax <= 48; exact integers below 2^53)
+        double w2[BS_MAX_PHOTONS + 1];
+        int sq[BS_MAX_PHOTONS + 1];
+        uint64_t b = 1;
+        for (int d = 0; d <= dmax; ++d) {
+            if (d > 0) b = b * (uint64_t)(dmax - d + 1) / (uint64_t)d;
+            w2[d] = (double)b * (double)b;
+            sq[d] = (top - 2 * d) * (top - 2 * d);
+        }
         for (int q = qmax + add; q >= 0; --q) {
             double acc = 0.0;
             for (int d = 0; d <= dmax; ++d) {
-                const int sq = (top - 2 * d) * (top - 2 * d);
-                const int src = q - sq;
+                const int src = q - sq[d];
                 if (src < 0 || src > qmax) continue;
-                const double w = (double)bs_binom(dmax, d);
-                acc += f[src] * w * w;
+                acc += f[src] * w2[d];
             }
             f[q] = acc;
         }
@@ -168,7 +188,7 @@ BS_HD float bs_mixed_log2_error(const int* radix, int nrows, int pinned_m, int K
     double total = 0.0;
     const double inv_n = 1.0 / (double)n;
     for (int q = 0; q <= qmax; ++q)
-        if (f[q] != 0.0) total += f[q] * pow((double)(q + off + nb) * inv_n, (double)K);
+        if (f[q] != 0.0) total += f[q] * bs_ipow((double)(q + off + nb) * inv_n, K);
     if (!(total > 0.0)) return -1000.0f;
     const double lrss = (1.0 - (double)n) + 0.5 * (log2(total) + (double)nb);
     const double drift = log2L > BS_FP32_RESEED_LOG2 ? 0.5 * (double)(log2L - BS_FP32_RESEED_LOG2) : 0.0;
