@@ -176,3 +176,14 @@ def test_served_mixed_chains_switch_precision_as_the_sampler_does(ctx, bslib):
     assert st["addends"][1] > 0 and st["addends"][2] > 0, st["addends"]
     got, _, _ = _serve(bslib, 1, u, occ, 9, range(12), tick_tasks=2048)
     assert np.array_equal(got, ref)
+
+
+def test_served_mixed_chains_with_reseeded_fp32_steps(ctx, bslib):
+    """Late steps of n = 28 chains in m = 40 modes are long FP32 walks (chunks
+    of 2^12) that the MIXED rule may keep in FP32 only with in-chunk
+    re-seeding, or send to double-float: served samples still equal the
+    direct sampler's, step for step."""
+    u, occ = S.config_cc(n=28, m=40, seed=23)
+    ref = ctx.sample(u, occ, 16, seed=12, mode=1)
+    got, _, _ = _serve(bslib, 1, u, occ, 12, range(16), tick_tasks=4096)
+    assert np.array_equal(got, ref)
