@@ -206,6 +206,27 @@ def test_mixed_reseeded_fp32_meets_the_drift_free_prediction(ctx, bslib):
     assert 0 < err <= 2.0 ** e8, (err, 2.0 ** e8)
 
 
+def test_mixed_reseeded_fp32_permanent(ctx, bslib):
+    """The permanent kernel's re-seed segments: a 30 x 30 permanent (2^29
+    addends, FP32 chunks of 2^11) with the tolerance between the rule's two
+    predictions runs in FP32 re-seeded every 2^8 steps and stays below the
+    drift-free prediction (against the FP64 kernel)."""
+    n = 30
+    a = S.haar_unitary(64, 4950)[:n, :n]
+    ones = np.ones(n, dtype=np.int32)
+    e, L, _ = bslib.debug_mixed_error(ones, ones, 0)
+    e8, _, _ = bslib.debug_mixed_error(ones, ones, 0, chunk_log2=8)
+    assert L > 8
+    ref = ctx.perm(a, ones, ones, mode=0)
+    try:
+        ctx.set_mixed_tolerance(2.0 ** ((e + e8) / 2))
+        got = run_checked(ctx, lambda: ctx.perm(a, ones, ones, mode=1), 1, True)
+    finally:
+        ctx.set_mixed_tolerance(1e-6)
+    err = abs(got - ref) / scale(a, ones, ones)
+    assert 0 < err <= 2.0 ** e8, (err, 2.0 ** e8)
+
+
 # ---------------------------------------------------------------- power-of-two column normalisation
 @pytest.mark.parametrize("kind", ["pow2", "decimal"])
 def test_mixed_column_normalisation_extreme_ranges(ctx, bslib, kind):
