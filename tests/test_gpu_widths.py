@@ -437,3 +437,19 @@ def test_mixed_sampler_agrees_with_fp64_at_workload_size(ctx):
     assert st["addends"][1] > 0 and st["addends"][2] > 0, st["addends"]
     same = float(np.mean(np.all(r64 == rmx, axis=1)))
     assert same >= 0.9, same
+
+
+@pytest.mark.parametrize("mode", [0, 1, 2])
+def test_sampler_under_a_small_budget_runs_in_passes(ctx, bslib, mode):
+    """A context with a 16 MiB device budget cannot hold the partial slots of
+    200 chains of n = 20 photons at once (about 80 KB each), so bs_sample
+    runs them in passes of a few dozen chains: every sample equals the one
+    drawn by an unbounded context (chains depend only on seed and index)."""
+    u, occ = S.config_cc(n=20, m=40, seed=13)
+    ref = ctx.sample(u, occ, 200, seed=31, mode=mode)
+    small = bslib.Context(0, mem_budget_bytes=16 << 20)
+    try:
+        got = small.sample(u, occ, 200, seed=31, mode=mode)
+    finally:
+        small.close()
+    assert np.array_equal(got, ref)
