@@ -206,6 +206,48 @@ def test_mixed_reseeded_fp32_meets_the_drift_free_prediction(ctx, bslib):
     assert 0 < err <= 2.0 ** e8, (err, 2.0 ** e8)
 
 
+def test_mixed_reseeded_fp32_sweep(ctx, bslib):
+    """Ten long-chunk FP32 jobs (K = 27..32, up to three repeated rows,
+    permanents and minors), each run with the MIXED tolerance between its
+    two predictions: every one runs in FP32 with in-chunk re-seeding and
+    stays below its drift-free prediction (errors against the FP64
+    kernels)."""
+    g = np.random.default_rng(2719)
+    done = 0
+    for trial in range(40):
+        if done == 10:
+            break
+        kind = trial % 2
+        K = int(g.integers(27, 33))
+        n = K - kind
+        nrep = int(g.integers(0, 4))
+        M = np.ones(n - nrep, np.int32)
+        for _ in range(nrep):
+            M[int(g.integers(0, len(M)))] += 1
+        N = np.ones(K, np.int32)
+        e, L, _ = bslib.debug_mixed_error(M, N, kind)
+        e8, _, _ = bslib.debug_mixed_error(M, N, kind, chunk_log2=8)
+        if L <= 8:
+            continue
+        u = S.haar_unitary(80, 9100 + trial)
+        a = u[g.permutation(80)[:len(M)]][:, g.permutation(80)[:K]]
+        call = (lambda md: ctx.perm(a, M, N, mode=md)) if kind == 0 else \
+            (lambda md: ctx.laplace_minors(a, M, N, mode=md))
+        ref = np.atleast_1d(call(0))
+        try:
+            ctx.set_mixed_tolerance(2.0 ** ((e + e8) / 2))
+            got = np.atleast_1d(run_checked(ctx, lambda: call(1), 1, True))
+        finally:
+            ctx.set_mixed_tolerance(1e-6)
+        if kind == 0:
+            err = abs(got[0] - ref[0]) / scale(a, M, N)
+        else:
+            err = max(abs(got[l] - ref[l]) / minor_scale(a, M, N, l) for l in range(K))
+        assert err <= 2.0 ** e8, (K, M.tolist(), L, err, 2.0 ** e8)
+        done += 1
+    assert done == 10
+
+
 def test_mixed_reseeded_fp32_permanent(ctx, bslib):
     """The permanent kernel's re-seed segments: a 30 x 30 permanent (2^29
     addends, FP32 chunks of 2^11) with the tolerance between the rule's two
