@@ -204,7 +204,7 @@ int bs_perm_formula(bs_ctx* ctx, const bs_c128* A, int n, int ld, bs_formula for
  * device budget and forbids allocations outside it, and real-time loops that
  * must not enter the CUDA allocator (cudaMalloc / cudaFree may synchronise the
  * device and have no latency bound).  Computes the same permanent as bs_perm
- * (same kernels; FP64 or MIXED) without any device or host heap allocation:
+ * (same kernels, any mode) without any device or host heap allocation:
  * all device scratch is one file-scope __device__ array of 8 MiB that every
  * GPU loading the library holds until the process exits.  The paper has no
  * counterpart of this call.
