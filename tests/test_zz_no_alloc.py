@@ -18,7 +18,7 @@ import synthetic as S
 
 pytestmark = pytest.mark.gpu
 
-TOL = {0: 1e-10, 1: 1e-6}
+TOL = {0: 1e-10, 1: 1e-6, 2: 1e-10}  # FP64, MIXED, double-float
 
 
 def scale(a, M, N):
@@ -53,7 +53,7 @@ def problems():
     return [big, (a1, M1, N1)]
 
 
-@pytest.mark.parametrize("mode", [0, 1])
+@pytest.mark.parametrize("mode", [0, 1, 2])
 def test_noalloc_matches_bs_perm_on_two_calls(ctx, bslib, mode):
     lib = ctypes.CDLL(bslib.library_path())
     for a, M, N in problems():
