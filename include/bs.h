@@ -56,10 +56,12 @@ typedef struct {
  *   BS_FP64:  column sums, products, weights and sums in double precision;
  *             partial sums combined in double-double.
  *   BS_MIXED: column sums and products in single precision (column sums
- *             re-seeded from the matrix every chunk, columns scaled by powers
- *             of two), addends summed in float-float runs, partial sums in
- *             double-double (Sec. 3.2 discusses the accuracy trade-off), for
- *             every job whose predicted FP32 error meets the MIXED tolerance
+ *             re-seeded from the matrix every chunk, and every 2^8 steps
+ *             inside it for jobs whose error would otherwise drift past the
+ *             tolerance; columns scaled by powers of two), addends summed in
+ *             float-float runs, partial sums in double-double (Sec. 3.2
+ *             discusses the accuracy trade-off), for every job whose
+ *             predicted FP32 error meets the MIXED tolerance
  *             (bs_ctx_set_mixed_tolerance); other jobs run in the double-float
  *             kernels of BS_DF64 (FP64-class, the cancellation-prone jobs).
  *   BS_DF64:  double-float: every quantity an unevaluated pair of floats
@@ -109,8 +111,9 @@ int bs_ctx_get_chunk_log2(const bs_ctx* ctx, bs_mode mode);
 
 /* Accuracy target of BS_MIXED: a job runs in the FP32 kernels when the
  * precision rule predicts an FP32 error of at most tol * prod_j ||a_j||^{N_j}
- * (column norms over the rows repeated by their multiplicities), else in the
- * FP64 kernels.  Default 1e-6.  Larger values keep more jobs in FP32; a value
+ * (column norms over the rows repeated by their multiplicities) -- with its
+ * column sums re-seeded every 2^8 steps when only their drift over longer
+ * chunks breaks that -- else in the double-float kernels.  Default 1e-6.  Larger values keep more jobs in FP32; a value
  * >= 1e300 sends every MIXED job to FP32 (to measure the FP32 error itself).
  * Errors: BS_EINVAL (tol <= 0 or NaN). */
 int bs_ctx_set_mixed_tolerance(bs_ctx* ctx, double tol);
