@@ -339,6 +339,10 @@ DTYPE_DETAIL = {
 # precision [FP64, FP32, double-float].  None where the kernel changed since
 # the capture.
 TRAFFIC_K30 = [{"bytes": 1.090e6, "chains": 8}, {"bytes": 0.993e6, "chains": 32}, {"bytes": 0.4562e6, "chains": 8}]
+# The bounding pipe's busy fraction in the same captures
+# (sm__pipe_fp64_cycles_active / sm__pipe_fma_cycles_active, pct of peak
+# sustained active): FP64 pipe for the FP64 kernel, FMA pipe for the others.
+PIPE_K30 = [{"pipe": "fp64", "active": 0.919}, {"pipe": "fma", "active": 0.709}, {"pipe": "fma", "active": 0.788}]
 
 def run_mine(args):
     import numpy as np
@@ -452,6 +456,7 @@ def run_mine(args):
             "frac": achieved / peak if peak else None, "traffic": traffic,
             "traffic_launch": (f"the k = 30 launch (ncu capture of {TRAFFIC_K30[p]['chains']} chains, scaled)"
                                if TRAFFIC_K30[p] else None),
+            "ncu_pipe_active_k30": PIPE_K30[p],
             "kernel": ("walk_fp64_minors_kernel", "walk_fp32_minors_kernel", "walk_df_minors_kernel")[p],
             "peak_source": ("measured on this GPU by bs_measure_fma_rates (2 flops per lane-FMA), "
                             + ("FP32 FMA pipe" if p == 1 else "FP64 pipe")),
