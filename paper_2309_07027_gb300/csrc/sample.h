@@ -26,6 +26,17 @@
 #define BS_TARGET_TASKS_MANY 64
 #define BS_LOG2L_MIN_SINGLE 6
 #define BS_LOG2L_MIN_MANY 3
+// Floor for the tiniest jobs planned alone (at most BS_FILL_TINY_C
+// addends): chunks of 2 addends.  Such a job's walk time is one warp's FP64
+// instruction stream (one instruction per 64 cycles per scheduler on this
+// part), and more, shorter chunks spread it over more warps; a chunk start
+// decodes its index and seeds the column sums (about the work of one or two
+// addends), so shorter chunks would only add work.  Larger small jobs keep
+// the 2^3 floor: batches of them are throughput-bound, and there the extra
+// seeding of 2-addend chunks cost more than it saved (a 64-item batch of
+// k = 10..16 ran 19 % slower with the lower floor for every job).
+#define BS_LOG2L_MIN_FILL 1
+#define BS_FILL_TINY_C 1024
 // Warp tasks below which a job planned alone is latency-bound (its walk
 // time is one lane's chunk); see bs_choose_log2L_single.
 #define BS_TARGET_TASKS_FILL 256
@@ -43,8 +54,9 @@ BS_HD int bs_choose_log2L(uint64_t C, int cpt, int log2min, int log2max, int tar
 }
 // The rule for jobs planned one call at a time: bs_choose_log2L with the
 // single-call target and floor 2^6, except that a job too small to give
-// BS_TARGET_TASKS_FILL tasks at that floor gets shorter chunks (down to the
-// 2^3 floor of the sampler) until it does: such a job is latency-bound, and
+// BS_TARGET_TASKS_FILL tasks at that floor gets shorter chunks (down to 2^3,
+// or 2^BS_LOG2L_MIN_FILL for the tiniest) until it does: such a job is
+// latency-bound, and
 // its walk time is one lane's chunk, not the total work (a 576-addend FP64
 // job in one warp of 9 chunks of 64 runs at one scheduler's FP64 rate).
 // 256 tasks keeps the re-seeding of mid-size jobs as it was: with 2048 (one
@@ -55,7 +67,8 @@ BS_HD int bs_choose_log2L_single(uint64_t C, int cpt, int log2max, int target) {
     if (big > BS_LOG2L_MIN_SINGLE) return big;
     int fill = bs_floor_log2(C / ((uint64_t)cpt * (uint64_t)BS_TARGET_TASKS_FILL));
     if (fill > BS_LOG2L_MIN_SINGLE) fill = BS_LOG2L_MIN_SINGLE;
-    if (fill < BS_LOG2L_MIN_MANY) fill = BS_LOG2L_MIN_MANY;
+    const int floor = C <= BS_FILL_TINY_C ? BS_LOG2L_MIN_FILL : BS_LOG2L_MIN_MANY;
+    if (fill < floor) fill = floor;
     return fill > log2max ? log2max : fill;
 }
 

@@ -119,14 +119,15 @@ def test_planner_addend_counts_and_orientation(bslib):
 def test_single_call_chunking(bslib):
     """Jobs planned one call at a time: chunks of 2^6 to 2^12 addends aimed
     at 32768 warp tasks of 32 chunks; a job too small to give 256 tasks at
-    2^6 gets chunks down to 2^3 until it does (latency-bound jobs spread
-    over more warps); jobs large enough keep 2^6 or longer."""
+    2^6 gets chunks down to 2^3 until it does, or 2^1 for jobs of at most
+    1024 addends (latency-bound jobs spread over more warps); jobs large
+    enough keep 2^6 or longer."""
     def plan(n):
         return bslib.debug_plan([1] * n, [1] * n)
     for n in (3, 8, 11, 14, 17, 20, 23, 26, 29, 32, 36):
         p = plan(n)
         C, l, tasks = p["C"], p["log2L"], p["tasks"]
-        assert C == 2 ** (n - 1) and 3 <= l <= 12
+        assert C == 2 ** (n - 1) and 1 <= l <= 12
         assert tasks == -(-C // (32 << l))
         if l == 12:  # the re-seed interval caps the chunk
             assert tasks >= 32768
@@ -135,10 +136,10 @@ def test_single_call_chunking(bslib):
         elif l == 6:
             assert tasks >= 256
         else:        # shortened only as far as needed to reach 256 tasks
-            assert l == 3 or 256 <= tasks < 2 * 256
+            assert l == (1 if C <= 1024 else 3) or 256 <= tasks < 2 * 256
     assert [plan(n)["log2L"] for n in (17, 18, 19, 20, 23, 26, 29, 33)] == [3, 4, 5, 6, 6, 6, 8, 12]
     c1 = bslib.debug_plan([3, 2, 2, 1, 1, 1, 1, 1], [1] * 12)
-    assert c1["log2L"] == 3 and c1["tasks"] == 3
+    assert c1["log2L"] == 1 and c1["tasks"] == 9
 
 
 def test_planner_rejects_invalid(bslib):

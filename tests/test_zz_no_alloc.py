@@ -49,7 +49,7 @@ def noalloc_c_abi(lib, a, M, N, mode, stream=None):
 def problems():
     u = S.haar_unitary(40, 11)
     big = (u[:22, :22], np.ones(22, np.int32), np.ones(22, np.int32))      # 2^21 addends, many tasks
-    a1, M1, N1, _, _ = S.config_single(seed=1)                              # 576 addends, 3 tasks
+    a1, M1, N1, _, _ = S.config_single(seed=1)                              # 576 addends, 9 tasks
     return [big, (a1, M1, N1)]
 
 
