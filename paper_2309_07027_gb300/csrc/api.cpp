@@ -107,7 +107,8 @@ struct bs_ctx {
     size_t h_back_n = 0;
     cudaEvent_t stage_ev[2] = {nullptr, nullptr};
     double deadline_s = 0.0;
-    int log2max[BS_NPREC] = {12, 12, 12};  // chunk-length caps, indexed by precision (= bs_mode)
+    int log2max[BS_NPREC] = {bs_default_log2max(BS_PREC_FP64), bs_default_log2max(BS_PREC_FP32),
+                             bs_default_log2max(BS_PREC_DF)};  // chunk-length caps, indexed by precision (= bs_mode)
     float mixed_log2_tol = BS_MIXED_LOG2_TOL_DEFAULT;  // MIXED precision rule threshold
     bool profiling = false;
     std::vector<Timed> timed;
@@ -1521,7 +1522,8 @@ int bs_debug_mixed_error(int rows, int cols, const int* row_mult, const int* col
     }
     const int l32 = chunk_log2 > 0
                         ? chunk_log2
-                        : bs_choose_log2L_single(p.C, bs_chunks_per_task(p.kind, 1, p.K), 12, BS_TARGET_TASKS_SINGLE_FP32);
+                        : bs_choose_log2L_single(p.C, bs_chunks_per_task(p.kind, 1, p.K), bs_default_log2max(BS_PREC_FP32),
+                                                 BS_TARGET_TASKS_SINGLE_FP32);
     std::vector<double> q_work(BS_MIXED_QMAX + 1);
     *log2_err = bs_mixed_log2_error(p.radix, p.nrows, p.pinned_m, p.K, p.n, l32, q_work.data());
     if (log2L) *log2L = l32;
@@ -1545,7 +1547,7 @@ int bs_debug_plan(int rows, int cols, const int* row_mult, const int* col_mult, 
     // chunking of this job planned alone in FP64 mode (default maximum 2^12)
     const int kd = kind == 1 ? BS_KIND_MINORS : BS_KIND_PERM;
     const int cpt = bs_chunks_per_task(kd, 0, p.K);
-    const int l = p.trivial ? 0 : bs_choose_log2L_single(p.C, cpt, 12, BS_TARGET_TASKS_SINGLE);
+    const int l = p.trivial ? 0 : bs_choose_log2L_single(p.C, cpt, bs_default_log2max(BS_PREC_FP64), BS_TARGET_TASKS_SINGLE);
     const uint64_t per = (uint64_t)cpt << l;
     info[6] = l;
     info[7] = p.trivial ? 0 : (int64_t)((p.C + per - 1) / per);

@@ -123,7 +123,8 @@ extern "C" int bs_perm_noalloc(const bs_c128* A, int rows, int cols, int ld, con
     int reseed = 0;
     if (mode == BS_MIXED) {
         double q_work[BS_MIXED_QMAX + 1];  // the rule's scratch, on the stack
-        const int l32 = bs_choose_log2L_single(p.C, bs_chunks_per_task(BS_KIND_PERM, BS_PREC_FP32, p.K), 12,
+        const int l32 = bs_choose_log2L_single(p.C, bs_chunks_per_task(BS_KIND_PERM, BS_PREC_FP32, p.K),
+                                               bs_default_log2max(BS_PREC_FP32),
                                                BS_TARGET_TASKS_SINGLE_FP32);
         const int plan = bs_mixed_fp32_plan(p.radix, p.nrows, p.pinned_m, p.K, p.n, l32, BS_MIXED_LOG2_TOL_DEFAULT,
                                             q_work);
@@ -131,7 +132,7 @@ extern "C" int bs_perm_noalloc(const bs_c128* A, int rows, int cols, int ld, con
         reseed = plan == 2 ? BS_FP32_RESEED_LOG2 : 0;
     }
     const int cpt = bs_chunks_per_task(BS_KIND_PERM, prec, p.K);
-    const int log2L = bs_choose_log2L_single(p.C, cpt, 12,
+    const int log2L = bs_choose_log2L_single(p.C, cpt, bs_default_log2max(prec),
                                              prec == BS_PREC_FP32 ? BS_TARGET_TASKS_SINGLE_FP32 : BS_TARGET_TASKS_SINGLE);
     const uint64_t per = (uint64_t)cpt << log2L;
     const uint64_t ntasks = (p.C + per - 1) / per;

@@ -44,9 +44,8 @@ namespace {
 
 using clock_type = std::chrono::steady_clock;
 constexpr size_t kAlign = 256;
-// chunk-length cap of served chains' step jobs: the default of a context, so
+// chunk-length caps (by precision) of served jobs: a context's defaults, so
 // that a served sample plans every step as bs_sample does
-constexpr int kChainLog2Max = 12;
 
 // First-fit allocator over [0, size) with coalescing free ranges.
 class Arena {
@@ -406,7 +405,7 @@ int run_tick(bs_server* s, std::vector<Request*>& admit, std::vector<Request*>& 
         d.rule.mode = (int)s->mode;
         d.rule.mixed_log2_tol = BS_MIXED_LOG2_TOL_DEFAULT;
         d.rule.mixed_fallback = BS_MIXED_FALLBACK_PREC;
-        for (int q = 0; q < BS_NPREC; ++q) d.rule.log2max[q] = kChainLog2Max;
+        for (int q = 0; q < BS_NPREC; ++q) d.rule.log2max[q] = bs_default_log2max(q);
         descs.push_back(d);
         max_m_rows = std::max(max_m_rows, r->m_rows);
         back_bytes += r->k < r->n ? sizeof(bs_job) : (size_t)r->m_det * 4;
@@ -728,14 +727,14 @@ int64_t bs_server_submit(bs_server* s, int kind, const bs_c128* A, int rows, int
     if (s->mode == BS_MIXED) {
         double q_work[BS_MIXED_QMAX + 1];
         const int l32 = bs_choose_log2L(r->plan.C, bs_chunks_per_task(r->kind, BS_PREC_FP32, r->plan.K),
-                                        BS_LOG2L_MIN_MANY, 12, BS_TARGET_TASKS_MANY);
+                                        BS_LOG2L_MIN_MANY, bs_default_log2max(BS_PREC_FP32), BS_TARGET_TASKS_MANY);
         const int plan = bs_mixed_fp32_plan(r->plan.radix, r->plan.nrows, r->plan.pinned_m, r->plan.K,
                                             r->plan.n, l32, BS_MIXED_LOG2_TOL_DEFAULT, q_work);
         r->prec = plan ? BS_PREC_FP32 : BS_MIXED_FALLBACK_PREC;
         r->reseed = plan == 2 ? BS_FP32_RESEED_LOG2 : 0;
     }
     r->cpt = bs_chunks_per_task(r->kind, r->prec, r->plan.K);
-    r->log2L = bs_choose_log2L(r->plan.C, r->cpt, BS_LOG2L_MIN_MANY, 12, BS_TARGET_TASKS_MANY);
+    r->log2L = bs_choose_log2L(r->plan.C, r->cpt, BS_LOG2L_MIN_MANY, bs_default_log2max(r->prec), BS_TARGET_TASKS_MANY);
     const uint64_t per = (uint64_t)r->cpt << r->log2L;
     r->ntasks = (uint32_t)((r->plan.C + per - 1) / per);
     r->ncols = r->kind == BS_KIND_PERM ? 1 : r->plan.K;
@@ -839,7 +838,7 @@ int64_t bs_server_submit_sample(bs_server* s, const bs_c128* U, int m_rows, int 
         for (int i = 0; i < np; ++i) {
             const int q = s->mode == BS_MIXED ? precs_mixed[i] : prec_one;
             const uint64_t cpt_min = q == BS_PREC_FP64 ? 16 : q == BS_PREC_FP32 ? 8 : 4;
-            ts = std::max<uint64_t>(ts, cmax / (cpt_min << kChainLog2Max) + 2);
+            ts = std::max<uint64_t>(ts, cmax / (cpt_min << bs_default_log2max(q)) + 2);
         }
         r->tasks_stride = ts;
         r->bytes = chain_layout(*r);

@@ -117,7 +117,8 @@ def test_planner_addend_counts_and_orientation(bslib):
 
 
 def test_single_call_chunking(bslib):
-    """Jobs planned one call at a time: chunks of 2^6 to 2^12 addends aimed
+    """Jobs planned one call at a time (FP64, chunk cap 2^11 by default):
+    chunks of 2^6 to 2^11 addends aimed
     at 32768 warp tasks of 32 chunks; a job too small to give 256 tasks at
     2^6 gets chunks down to 2^3 until it does, or 2^1 for jobs of at most
     1024 addends (latency-bound jobs spread over more warps); jobs large
@@ -127,9 +128,9 @@ def test_single_call_chunking(bslib):
     for n in (3, 8, 11, 14, 17, 20, 23, 26, 29, 32, 36):
         p = plan(n)
         C, l, tasks = p["C"], p["log2L"], p["tasks"]
-        assert C == 2 ** (n - 1) and 1 <= l <= 12
+        assert C == 2 ** (n - 1) and 1 <= l <= 11
         assert tasks == -(-C // (32 << l))
-        if l == 12:  # the re-seed interval caps the chunk
+        if l == 11:  # the re-seed interval caps the chunk
             assert tasks >= 32768
         elif l > 6:  # the large-job rule: about 32768 tasks
             assert 32768 <= tasks < 2 * 32768
@@ -137,7 +138,7 @@ def test_single_call_chunking(bslib):
             assert tasks >= 256
         else:        # shortened only as far as needed to reach 256 tasks
             assert l == (1 if C <= 1024 else 3) or 256 <= tasks < 2 * 256
-    assert [plan(n)["log2L"] for n in (17, 18, 19, 20, 23, 26, 29, 33)] == [3, 4, 5, 6, 6, 6, 8, 12]
+    assert [plan(n)["log2L"] for n in (17, 18, 19, 20, 23, 26, 29, 33)] == [3, 4, 5, 6, 6, 6, 8, 11]
     c1 = bslib.debug_plan([3, 2, 2, 1, 1, 1, 1, 1], [1] * 12)
     assert c1["log2L"] == 1 and c1["tasks"] == 9
 
