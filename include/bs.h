@@ -104,8 +104,8 @@ int bs_ctx_sync(bs_ctx* ctx);
 int bs_ctx_set_deadline(bs_ctx* ctx, double seconds);
 
 /* Chunk-length knob: log2_chunk_max caps the chunk length (= the re-seed
- * interval of the column sums) of the given mode (default 11 for BS_FP64, 12
- * for the others); values
+ * interval of the column sums) of the given mode (default 11, 12 for
+ * BS_DF64); values
  * outside [4, 20] are rejected with BS_EINVAL. */
 int bs_ctx_set_chunk_log2(bs_ctx* ctx, bs_mode mode, int log2_chunk_max);
 int bs_ctx_get_chunk_log2(const bs_ctx* ctx, bs_mode mode);

@@ -53,6 +53,10 @@ constexpr size_t kSrc = 2560;                                     // compacted m
 constexpr size_t kData = kSrc + (size_t)BS_MAX_N * BS_MAX_N * 16;  // packed c0 / 2a
 constexpr size_t kPart = kData + (size_t)(1 + BS_MAX_N) * BS_ROW_STRIDE_DF(BS_MAX_N) * 16;
 constexpr size_t kPartSlots = (BS_NOALLOC_SCRATCH_BYTES - kPart) / sizeof(bs_zdd);
+// Chunk-length cap of this call's planner: 2^12 in every mode (the task
+// count of a job falls with the cap, and this one sets the size limit the
+// header states); only jobs beyond about 2^31 addends reach it.
+constexpr int kLog2Max = 12;
 static_assert(kPart % 256 == 0 && kData % 256 == 0, "scratch regions must stay aligned");
 static_assert(kMeta + BS_META_SIZE(BS_MAX_DIGITS, BS_MAX_COLS, BS_MAX_N) * 4 <= kOut, "metadata region too small");
 
@@ -123,8 +127,7 @@ extern "C" int bs_perm_noalloc(const bs_c128* A, int rows, int cols, int ld, con
     int reseed = 0;
     if (mode == BS_MIXED) {
         double q_work[BS_MIXED_QMAX + 1];  // the rule's scratch, on the stack
-        const int l32 = bs_choose_log2L_single(p.C, bs_chunks_per_task(BS_KIND_PERM, BS_PREC_FP32, p.K),
-                                               bs_default_log2max(BS_PREC_FP32),
+        const int l32 = bs_choose_log2L_single(p.C, bs_chunks_per_task(BS_KIND_PERM, BS_PREC_FP32, p.K), kLog2Max,
                                                BS_TARGET_TASKS_SINGLE_FP32);
         const int plan = bs_mixed_fp32_plan(p.radix, p.nrows, p.pinned_m, p.K, p.n, l32, BS_MIXED_LOG2_TOL_DEFAULT,
                                             q_work);
@@ -132,7 +135,7 @@ extern "C" int bs_perm_noalloc(const bs_c128* A, int rows, int cols, int ld, con
         reseed = plan == 2 ? BS_FP32_RESEED_LOG2 : 0;
     }
     const int cpt = bs_chunks_per_task(BS_KIND_PERM, prec, p.K);
-    const int log2L = bs_choose_log2L_single(p.C, cpt, bs_default_log2max(prec),
+    const int log2L = bs_choose_log2L_single(p.C, cpt, kLog2Max,
                                              prec == BS_PREC_FP32 ? BS_TARGET_TASKS_SINGLE_FP32 : BS_TARGET_TASKS_SINGLE);
     const uint64_t per = (uint64_t)cpt << log2L;
     const uint64_t ntasks = (p.C + per - 1) / per;

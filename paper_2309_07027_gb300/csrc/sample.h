@@ -41,11 +41,13 @@
 // time is one lane's chunk); see bs_choose_log2L_single.
 #define BS_TARGET_TASKS_FILL 256
 // Default cap of the chunk length (the re-seed interval) by precision:
-// 2^11 addends for the FP64 kernels, 2^12 for the others.  The sampler's
-// FP64 steps run about 1 % faster with 2^11 (twice the tasks of its largest
-// jobs, a shorter last wave per launch; 2^9..2^11 measured alike), while
-// its double-float steps showed no difference between 2^11 and 2^13.
-BS_HD int bs_default_log2max(int prec) { return prec == BS_PREC_FP64 ? 11 : 12; }
+// 2^11 addends for the FP64 and FP32 kernels, 2^12 for double-float.  The
+// sampler's FP64 steps run about 1 % faster with 2^11 than with 2^12 (twice
+// the tasks of its largest jobs, a shorter last wave per launch; 2^9..2^11
+// measured alike), its MIXED steps 1.4 % (2^10: 7 % slower), while its
+// double-float steps showed no difference between 2^11 and 2^13.  Jobs
+// planned one call at a time rarely reach the cap.
+BS_HD int bs_default_log2max(int prec) { return prec == BS_PREC_DF ? 12 : 11; }
 BS_HD int bs_floor_log2(uint64_t x) {  // floor(log2(x)) for x >= 1, 0 for x = 0
     int l = 0;
     while ((2ull << l) <= x) ++l;
