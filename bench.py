@@ -326,8 +326,9 @@ DTYPE_DETAIL = {
     "fp64": ("f64 column sums, products and weights; per-lane double runs folded into double-double, "
              "double-double task partials (Sum2 reduce)"),
     "mixed": ("f32 column sums and products where the MIXED rule predicts an error below 1e-6 prod ||a_j|| "
-              "(the rule is oracle-checked in tests/test_gpu_widths.py), double-float otherwise; float-float runs "
-              "folded into double-double partials"),
+              "(column sums re-seeded every 2^8 steps where only their drift would exceed it; the rule is "
+              "oracle-checked in tests/test_gpu_widths.py), double-float otherwise; float-float runs folded into "
+              "double-double partials"),
     "df": ("double-float: each value a pair of f32 (about 48 significant bits) on the FP32 pipe; exact "
            "fixed-point column sums, FMA-based exact products, Sum2 runs, double-double partials; within the FP64 "
            "tolerance 1e-10 prod ||a_j||, with errors against the oracle about 100x the FP64 kernels' "
