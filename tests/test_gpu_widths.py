@@ -495,3 +495,23 @@ def test_sampler_under_a_small_budget_runs_in_passes(ctx, bslib, mode):
     finally:
         small.close()
     assert np.array_equal(got, ref)
+
+
+@pytest.mark.parametrize("mode", [0, 1, 2])
+def test_sampler_at_the_largest_output_mode_count(ctx, bslib, mode):
+    """m = 8192 output modes (the largest supported; the draw's weights then
+    need more than 48 KB of shared memory): an isometry with 6 input columns,
+    sampled by bs_sample_ex and by a server, equals the oracle's chains seed
+    for seed (up to a draw within the mode's margin of a CDF boundary)."""
+    g = S.rng(8192)
+    q, _ = np.linalg.qr(g.standard_normal((8192, 6)) + 1j * g.standard_normal((8192, 6)))
+    v = np.ascontiguousarray(q)
+    occ = np.ones(6, dtype=np.int32)
+    ns = 16
+    ref, margin, _ = oracle.cc_sample(v, occ, ns, seed=88)
+    got = ctx.sample_ex(v, occ, ns, seed=88, mode=mode)
+    bad = [s for s in range(ns) if not np.array_equal(got[s], ref[s])]
+    assert all(margin[s] < MARGIN[mode] for s in bad) and len(bad) <= 1, (bad, margin[bad])
+    with bslib.Server(0, mem_budget_bytes=512 << 20, max_active=8, tick_tasks=256, mode=mode) as srv:
+        served = np.array([srv.wait_sample(t)[0] for t in [srv.submit_sample(v, occ, 88, s) for s in range(4)]])
+    assert np.array_equal(served, got[:4])
