@@ -220,9 +220,8 @@ int bs_perm_formula(bs_ctx* ctx, const bs_c128* A, int n, int ld, bs_formula for
  * Limit: the job's warp tasks must fit the fixed scratch (about 2.6e5 tasks,
  * e.g. every permanent with up to 2^34 addends); larger jobs return
  * BS_EINVAL with a message naming the limit.  The first call on a device looks
- * up the array's device address; make that first call before any stream
- * capture.  Calls share the array: calls that overlap on the GPU race and
- * must be serialised by the caller. */
+ * up the array's device address.  Calls share the array: calls that overlap
+ * on the GPU race and must be serialised by the caller. */
 int bs_perm_noalloc(const bs_c128* A, int rows, int cols, int ld, const int* row_mult, const int* col_mult,
                     bs_mode mode, void* stream, bs_c128* out, bs_c128* out_lo);
 

@@ -20,8 +20,7 @@
 // In host code the array's name is only a host-side handle, not a device
 // address: the first call on each device (with that device current) asks the
 // runtime for the array's device address with cudaGetSymbolAddress, checks
-// the result and caches it; kernels only ever receive that address.  That
-// first call should therefore happen before any stream capture.
+// the result and caches it; kernels only ever receive that address.
 //
 // All calls share the one array and leave their data in it; the counter and
 // status words are cleared on every call.  Calls whose work overlaps on the
