@@ -1,7 +1,9 @@
 // FP64 walk kernels: permanents and fused Laplace minors, every step in
 // double precision (column sums, products, weights; compensated sums).
-// One instantiation per column bucket KB (K in (KB-4, KB]); the host groups
-// jobs by bucket, so each kernel keeps its own register allocation.
+// One kernel per column bucket KB (K in (KB-4, KB]); the host groups jobs by
+// bucket, so each kernel keeps its own register allocation.  Inside, each
+// task runs the walk instance for its job's exact column count (permanents)
+// or owned-column count (minors), so no dead bucket column costs FP64 slots.
 #include "kernels.h"
 #include "walk.cuh"
 
@@ -26,13 +28,29 @@ __global__ void __launch_bounds__(kPermBlock) walk_fp64_perm_kernel(WalkArgs a) 
             if (lane == 0) atomicExch(a.status, BS_STATUS_BADJOB);
             continue;
         }
-        walk_task_perm_fp64<KB>(jb, data, a.meta + BS_META_RADIX(jb), a.partials,
-                                   (uint32_t)(t - jb.task_begin) + jb.task_offset, lane);
+        const uint32_t local = (uint32_t)(t - jb.task_begin) + jb.task_offset;
+        const int* radix = a.meta + BS_META_RADIX(jb);
+        // the instance with the job's exact column count (K in (KB-4, KB])
+        switch (jb.K - (KB - 4)) {
+            case 1: walk_task_perm_fp64<KB, KB - 3>(jb, data, radix, a.partials, local, lane); break;
+            case 2: walk_task_perm_fp64<KB, KB - 2>(jb, data, radix, a.partials, local, lane); break;
+            case 3: walk_task_perm_fp64<KB, KB - 1>(jb, data, radix, a.partials, local, lane); break;
+            default: walk_task_perm_fp64<KB, KB>(jb, data, radix, a.partials, local, lane); break;
+        }
     }
 }
 
+// Resident CTAs per SM the fused-minor kernel is compiled for (64 threads
+// each): the register budgets it measured fastest at -- 168 registers (6
+// CTAs) at widths 24 to 32, 128 (8) at 16 and 20, 96 (10) at 8 and 12, 72
+// (14) at 4, and the compiler's choice (at most 255, 4 CTAs) above 32.
 template <int KB>
-__global__ void __launch_bounds__(kMinorsBlock) walk_fp64_minors_kernel(WalkArgs a) {
+struct MinorsMinBlocks {
+    static constexpr int value = KB <= 4 ? 14 : KB <= 12 ? 10 : KB <= 20 ? 8 : KB <= 32 ? 6 : 4;
+};
+
+template <int KB>
+__global__ void __launch_bounds__(kMinorsBlock, MinorsMinBlocks<KB>::value) walk_fp64_minors_kernel(WalkArgs a) {
     extern __shared__ double2 smem_fp64[];
     const int lane = threadIdx.x & 31;
     const int stride = blockDim.x;
@@ -52,8 +70,13 @@ __global__ void __launch_bounds__(kMinorsBlock) walk_fp64_minors_kernel(WalkArgs
             if (lane == 0) atomicExch(a.status, BS_STATUS_BADJOB);
             continue;
         }
-        walk_task_minors_fp64<KB>(jb, data, a.meta + BS_META_RADIX(jb), a.partials, (uint32_t)(t - jb.task_begin) + jb.task_offset,
-                                  lane, sm_acc, wtot, stride);
+        const uint32_t local = (uint32_t)(t - jb.task_begin) + jb.task_offset;
+        const int* radix = a.meta + BS_META_RADIX(jb);
+        // the instance whose lanes own exactly Hr = ceil(K / 2) columns
+        if (((jb.K + 1) >> 1) == KB / 2)
+            walk_task_minors_fp64<KB, KB / 2>(jb, data, radix, a.partials, local, lane, sm_acc, wtot, stride);
+        else
+            walk_task_minors_fp64<KB, KB / 2 - 1>(jb, data, radix, a.partials, local, lane, sm_acc, wtot, stride);
     }
 }
 

@@ -305,33 +305,38 @@ __device__ __forceinline__ cx<double> ldg_cx(const cx<double>* p) {
     return cx<double>{v.x, v.y};
 }
 
-// c_col += cf * row_col for the live columns (one 16-byte load per column).
-template <int KB>
-__device__ __forceinline__ void update_columns(cx<double> (&c)[KB], const cx<double>* __restrict__ row, double cf,
-                                               int K) {
+// c_col += cf * row_col for the KX live columns (one 16-byte load per
+// column).  KX is the job's exact column count, a template parameter: a
+// runtime test on the bucket's last columns becomes predicated instructions
+// that occupy FP64 issue slots even where the column is dead.
+template <int KB, int KX>
+__device__ __forceinline__ void update_columns(cx<double> (&c)[KB], const cx<double>* __restrict__ row, double cf) {
+    static_assert(KX >= 1 && KX <= KB, "live columns lie in the bucket");
 #pragma unroll
-    for (int col = 0; col < KB; ++col)
-        if (BS_LIVE(col)) {
-            cx<double> a = ldg_cx(row + col);
-            c[col].re = bfma(cf, a.re, c[col].re);
-            c[col].im = bfma(cf, a.im, c[col].im);
-        }
+    for (int col = 0; col < KX; ++col) {
+        cx<double> a = ldg_cx(row + col);
+        c[col].re = bfma(cf, a.re, c[col].re);
+        c[col].im = bfma(cf, a.im, c[col].im);
+    }
 }
-// prod_col c_col with two interleaved chains (even / odd columns).
-template <typename T, int KB>
-__device__ __forceinline__ cx<T> product_columns(const cx<T> (&c)[KB], int K) {
-    if (KB == 4 && K == 1) return c[0];
-    cx<T> pe = c[0];
-    cx<T> po = c[1];
+// prod_col c_col over the KX live columns with two interleaved chains (even
+// / odd columns).
+template <typename T, int KB, int KX>
+__device__ __forceinline__ cx<T> product_columns(const cx<T> (&c)[KB]) {
+    if constexpr (KX == 1) {
+        return c[0];
+    } else {
+        cx<T> pe = c[0];
+        cx<T> po = c[1];
 #pragma unroll
-    for (int col = 2; col < KB; ++col)
-        if (BS_LIVE(col)) {
+        for (int col = 2; col < KX; ++col) {
             if (col & 1)
                 po = cmul(po, c[col]);
             else
                 pe = cmul(pe, c[col]);
         }
-    return cmul(pe, po);
+        return cmul(pe, po);
+    }
 }
 
 template <typename T>
@@ -352,14 +357,16 @@ __device__ __forceinline__ void store_partial(bs_zdd* p, ddv re, ddv im) {
 // ---------------------------------------------------------------- one task: permanent, FP64
 // Each lane: plain double runs of FOLD addends folded into a double-double
 // sum; the 32 lanes are combined in double-double in a fixed shuffle order
-// and lane 0 writes the task's partial.  (The FP32 permanent runs on packed
-// pairs, walk_fp32.cuh.)
-template <int KB>
+// and lane 0 writes the task's partial.  KX = K, the job's column count, is
+// compile-time (the kernel picks the instance per task), so the per-addend
+// update and product run exactly K columns.  (The FP32 permanent runs on
+// packed pairs, walk_fp32.cuh.)
+template <int KB, int KX>
 __device__ void walk_task_perm_fp64(const bs_job& jb, const cx<double>* __restrict__ data,
                                     const int* __restrict__ radix, bs_zdd* __restrict__ partials, uint32_t local,
                                     int lane) {
     constexpr uint32_t FOLD = 64;
-    const int K = jb.K;
+    constexpr int K = KX;
     constexpr int KP = KB;  // = BS_ROW_STRIDE(K) for every K of the bucket
     const cx<double>* c0 = data + jb.data_off;
     const cx<double>* a2 = c0 + KP;
@@ -377,7 +384,7 @@ __device__ void walk_task_perm_fp64(const bs_job& jb, const cx<double>* __restri
         cx<double> acc = {0.0, 0.0};
         uint32_t run = 0;
         for (uint32_t s = 0;; ++s) {
-            const cx<double> p = product_columns<double, KB>(c, K);
+            const cx<double> p = product_columns<double, KB, KX>(c);
             acc.re = bfma(ws, p.re, acc.re);
             acc.im = bfma(ws, p.im, acc.im);
             if (++run == FOLD) {
@@ -391,7 +398,7 @@ __device__ void walk_task_perm_fp64(const bs_job& jb, const cx<double>* __restri
             int wch;
             const int row = st.step(g, s, radix, &neg, &wch);
             ws = wch ? signed_weight<double>(g.w, g.parity) : flip_sign(ws);
-            update_columns<KB>(c, a2 + (size_t)row * KP, unit_sign_d(neg), K);
+            update_columns<KB, KX>(c, a2 + (size_t)row * KP, unit_sign_d(neg));
         }
         sre = dd_add_d(sre, acc.re);
         sim = dd_add_d(sim, acc.im);
@@ -454,7 +461,11 @@ __device__ __forceinline__ void minors_fold_fp64(cx<double>* __restrict__ wacc, 
 // with weight 0), so the shuffle has the full warp.  A warp task covers 16
 // chunks; its last fold leaves the task's sums in the warp's totals, which
 // lanes 16 h + u write as the task's double-double partials.
-template <int KB>
+//
+// HX = Hr, the most columns a lane owns, is compile-time (the kernel picks
+// the instance per task: KB / 2 or KB / 2 - 1), so the per-addend loops run
+// exactly Hr columns; only lane h = 1 of an odd K has one predicated column.
+template <int KB, int HX>
 __device__ void walk_task_minors_fp64(const bs_job& jb, const cx<double>* __restrict__ data,
                                       const int* __restrict__ radix, bs_zdd* __restrict__ partials, uint32_t local,
                                       int lane, cx<double>* __restrict__ sm_acc, double4* __restrict__ wtot,
@@ -463,7 +474,8 @@ __device__ void walk_task_minors_fp64(const bs_job& jb, const cx<double>* __rest
     // addend, a fold about 16 per column, so folds every 256 addends cost
     // about 1 % (every 64: 4.8 %, measured on the 29 x 30 minors)
     constexpr uint32_t FOLD = 256;
-    constexpr int H = KB / 2;  // most columns a lane can own
+    constexpr int H = HX;  // most columns a lane owns: Hr
+    static_assert(HX >= 1 && 2 * HX <= KB, "owned columns lie in the bucket");
     const int K = jb.K;
     constexpr int KP = KB;  // = BS_ROW_STRIDE(K) for every K of the bucket
     const int half = lane & 1;
@@ -473,7 +485,7 @@ __device__ void walk_task_minors_fp64(const bs_job& jb, const cx<double>* __rest
     const cx<double>* c0 = data + jb.data_off;
     const cx<double>* a2 = c0 + KP;
     cx<double>* wacc = sm_acc - lane;  // this warp's thread 0
-#define BS_OWN(t) ((t) < H - 2 || (t) < KH)
+#define BS_OWN(t) ((t) < H - 1 || (t) < KH)
 #pragma unroll
     for (int t = 0; t < H; ++t)
         if (BS_OWN(t)) sm_acc[t * stride] = cx<double>{0.0, 0.0};
