@@ -339,11 +339,11 @@ DTYPE_DETAIL = {
 # fused-minor launch of this workload under ncu, and the chains it ran; by
 # precision [FP64, FP32, double-float].  None where the kernel changed since
 # the capture.
-TRAFFIC_K30 = [{"bytes": 1.090e6, "chains": 8}, {"bytes": 0.993e6, "chains": 32}, {"bytes": 0.4562e6, "chains": 8}]
+TRAFFIC_K30 = [{"bytes": 0.6948e6, "chains": 8}, {"bytes": 0.993e6, "chains": 32}, {"bytes": 0.4562e6, "chains": 8}]
 # The bounding pipe's busy fraction in the same captures
 # (sm__pipe_fp64_cycles_active / sm__pipe_fma_cycles_active, pct of peak
 # sustained active): FP64 pipe for the FP64 kernel, FMA pipe for the others.
-PIPE_K30 = [{"pipe": "fp64", "active": 0.919}, {"pipe": "fma", "active": 0.709}, {"pipe": "fma", "active": 0.788}]
+PIPE_K30 = [{"pipe": "fp64", "active": 0.928}, {"pipe": "fma", "active": 0.709}, {"pipe": "fma", "active": 0.788}]
 
 def run_mine(args):
     import numpy as np
