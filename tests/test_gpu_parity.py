@@ -257,6 +257,44 @@ def test_fp64_minors_every_width_against_oracle(ctx, mode, K):
         assert abs(got[l] - ref) <= bound, (K, l, got[l], ref, bound)
 
 
+def _rows_for(total):
+    """Row multiplicities summing to `total`: two rows of multiplicity 1
+    (binary Gray digits, one of them pinned) and two of large multiplicity
+    (n-ary digits), so the oracle's term-by-term sum stays small."""
+    if total <= 2:
+        return np.ones(total, dtype=np.int32)
+    rest = total - 2
+    return np.array([1, 1, (rest + 1) // 2, rest // 2], dtype=np.int32)[: 4 if rest > 1 else 3]
+
+
+@pytest.mark.parametrize("K", range(1, 49))
+def test_fp64_every_column_count_against_oracle(ctx, K):
+    """The FP64 kernels run a separately compiled walk for each exact column
+    count (permanents) and each owned-column count of a lane pair (minors),
+    so every K from 1 to 48 is its own instance: the permanent of a K-column
+    problem and, for K >= 2, the K minors of a (K-1)-photon row set, each
+    against the oracle (Eq. bbfgrepeated term by term)."""
+    g = S.rng(7000 + K)
+    u = S.haar_unitary(64, 700 + K)
+    N = np.ones(K, dtype=np.int32)
+    M = _rows_for(K)
+    a = u[g.permutation(64)[: len(M)]][:, g.permutation(64)[:K]]
+    got = ctx.perm(a, M, N, mode=0)
+    ref = ref_perm(a, M, N)
+    bound = TOL[0] * scale(a, M, N) + TOL_L1 * oracle.perm_mult_abs(a, M, N)
+    assert abs(got - ref) <= bound, (K, got, ref, bound)
+    if K < 2:
+        return
+    M = _rows_for(K - 1)
+    a = u[g.permutation(64)[: len(M)]][:, g.permutation(64)[:K]]
+    got = ctx.laplace_minors(a, M, N, mode=0)
+    for l in range(K):
+        keep = [j for j in range(K) if j != l]
+        ref = ref_perm(a[:, keep], M, N[keep])
+        bound = TOL[0] * minor_scale(a, M, N, l) + TOL_L1 * oracle.perm_mult_abs(a[:, keep], M, N[keep])
+        assert abs(got[l] - ref) <= bound, (K, l, got[l], ref, bound)
+
+
 @pytest.mark.parametrize("K", MINOR_WIDTHS)
 def test_fp32_minors_every_width(ctx, bslib, K):
     """The FP32 fused minors at every column width, forced to FP32 with the
