@@ -41,9 +41,11 @@ __global__ void __launch_bounds__(kPermBlock) walk_fp64_perm_kernel(WalkArgs a) 
 }
 
 // Resident CTAs per SM the fused-minor kernel is compiled for (64 threads
-// each): the register budgets it measured fastest at -- 168 registers (6
-// CTAs) at widths 24 to 32, 128 (8) at 16 and 20, 96 (10) at 8 and 12, 72
-// (14) at 4, and the compiler's choice (at most 255, 4 CTAs) above 32.
+// each).  Two walk instances inlined into one kernel raise the compiler's
+// register choice (width 32: 168 -> 216, 6 -> 4 CTAs per SM), so the kernel
+// keeps the budgets its one-instance form ran at, with no spills: 168
+// registers (6 CTAs) at widths 24 to 32, 128 (8) at 16 and 20, 96 (10) at 8
+// and 12, 72 (14) at 4, and the compiler's choice (4 CTAs) above 32.
 template <int KB>
 struct MinorsMinBlocks {
     static constexpr int value = KB <= 4 ? 14 : KB <= 12 ? 10 : KB <= 20 ? 8 : KB <= 32 ? 6 : 4;
