@@ -337,9 +337,12 @@ DTYPE_DETAIL = {
 
 # DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) of one k = 30
 # fused-minor launch of this workload under ncu, and the chains it ran; by
-# precision [FP64, FP32, double-float].  None where the kernel changed since
-# the capture.
-TRAFFIC_K30 = [{"bytes": 0.6948e6, "chains": 8}, {"bytes": 0.993e6, "chains": 32}, {"bytes": 0.4562e6, "chains": 8}]
+# precision [FP64, FP32, double-float].  The traffic does not grow in
+# proportion to the chains (the task partials stay in L2 for a few chains
+# and spill from it at 200: FP64 0.69 MB at 8 chains, 1.36 MB at 32, 80.1 MB
+# at 200), so only a capture of the full 200-chain launch is used; None where
+# there is none, or where the kernel changed since the capture.
+TRAFFIC_K30 = [{"bytes": 80.08e6, "chains": 200}, None, None]
 # The bounding pipe's busy fraction in the same captures
 # (sm__pipe_fp64_cycles_active / sm__pipe_fma_cycles_active, pct of peak
 # sustained active): FP64 pipe for the FP64 kernel, FMA pipe for the others.
@@ -442,11 +445,12 @@ def run_mine(args):
     peak = 2.0 * (fp32_rate if p == 1 else fp64_rate) / 1e12
     achieved = fl / walk_s / 1e12 if walk_s > 0 else 0.0
     # DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) of the k = 30
-    # fused-minor launch, from an ncu capture of a few chains of this
-    # workload, scaled to the step's chains (job data, metadata and task
-    # partials grow with the number of chains).  The kernels are
+    # fused-minor launch, from an ncu capture of that launch with the same
+    # number of chains (null for other chain counts: the task partials' share
+    # of the traffic depends on whether they fit L2).  The kernels are
     # compute-bound; the figure shows that they re-read nothing.
-    traffic = TRAFFIC_K30[p]["bytes"] * S_ / TRAFFIC_K30[p]["chains"] if TRAFFIC_K30[p] else None
+    cap = TRAFFIC_K30[p]
+    traffic = cap["bytes"] if cap and cap["chains"] == S_ else None
     # nominal peak from unit counts and clocks: FMA lanes per SM per clock
     # (128 FP32, 2 FP64 on this part) x SMs x maximum SM clock x 2 flops
     sms = torch.cuda.get_device_properties(local).multi_processor_count
@@ -455,8 +459,8 @@ def run_mine(args):
     peak_nominal = 2.0 * lanes * sms * max_mhz * 1e6 / 1e12
     roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
             "frac": achieved / peak if peak else None, "traffic": traffic,
-            "traffic_launch": (f"the k = 30 launch (ncu capture of {TRAFFIC_K30[p]['chains']} chains, scaled)"
-                               if TRAFFIC_K30[p] else None),
+            "traffic_launch": (f"the k = 30 launch of {S_} chains (ncu dram__bytes_read.sum + dram__bytes_write.sum)"
+                               if traffic is not None else None),
             "ncu_pipe_active_k30": PIPE_K30[p],
             "kernel": ("walk_fp64_minors_kernel", "walk_fp32_minors_kernel", "walk_df_minors_kernel")[p],
             "peak_source": ("measured on this GPU by bs_measure_fma_rates (2 flops per lane-FMA), "
